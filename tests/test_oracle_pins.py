@@ -1,0 +1,301 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Each test checks the oracle against a closed form, a library routine that
+computes the same quantity by another route, an invariant of the
+mathematics, or a number printed in the paper.  A dropped term, wrong sign,
+wrong index or transposed operand anywhere in the oracle fails at least one.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.fft
+import scipy.signal
+import torch
+
+from oracle import melt_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- Mel map
+def test_mel_map_textbook_points():
+    # Eq. 1 at f = 700 Hz is 2595 log10(2); HTK maps 1000 Hz to ~1000 mel.
+    assert O.mel_htk(700.0) == pytest.approx(2595.0 * math.log10(2.0), rel=1e-15)
+    assert O.mel_htk(1000.0) == pytest.approx(1000.0, abs=0.05)
+    assert O.mel_htk(0.0) == 0.0
+    f = np.linspace(0.0, 11025.0, 257)
+    np.testing.assert_allclose(O.mel_htk_inv(O.mel_htk(f)), f, rtol=1e-12, atol=1e-9)
+
+
+def test_analysis_frequencies_interior_and_mel_uniform():
+    f = O.melt_frequencies(80, 0.0, 8000.0)
+    assert f.shape == (80,)
+    assert 0.0 < f[0] and f[-1] < 8000.0           # interior points only
+    step = (O.mel_htk(8000.0) - O.mel_htk(0.0)) / 81.0
+    mu = O.mel_htk(f)
+    np.testing.assert_allclose(np.diff(mu), step, rtol=1e-10)
+    assert mu[0] == pytest.approx(step, rel=1e-10)
+
+
+# ------------------------------------------------------------------ window
+@pytest.mark.parametrize("n", [8, 400, 1024, 1200])
+def test_hann_matches_scipy(n):
+    np.testing.assert_allclose(O.hann(n, periodic=True),
+                               scipy.signal.get_window("hann", n, fftbins=True), atol=1e-15)
+    np.testing.assert_allclose(O.hann(n, periodic=False),
+                               scipy.signal.windows.hann(n, sym=True), atol=1e-15)
+
+
+def test_frame_count_rule():
+    # 1 s at 16 kHz with N=400, H=160 gives 98 frames (the 8 x 1 s workload's count)
+    assert O.num_frames(16000, 400, 160) == 98
+    assert O.num_frames(399, 400, 160) == 0
+    assert O.num_frames(400, 400, 160) == 1
+    assert O.num_frames(559, 400, 160) == 1
+    assert O.num_frames(560, 400, 160) == 2
+    assert O.num_frames(480000, 400, 160) == 2998
+
+
+# ------------------------------------------------------- tone closed form
+def _geom(omega, n):
+    """G(omega) = sum_{k<n} e^{-i omega k} in closed form."""
+    omega = np.asarray(omega, np.float64)
+    z = np.exp(-1j * omega)
+    near = np.abs(np.angle(z)) < 1e-12
+    out = np.where(near, n + 0j, (1 - z ** n) / np.where(near, 1, 1 - z))
+    return out
+
+
+def _hann_dtft(omega, n, periodic):
+    d = n if periodic else n - 1
+    s = 2 * math.pi / d
+    return 0.5 * _geom(omega, n) - 0.25 * _geom(omega - s, n) - 0.25 * _geom(omega + s, n)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_tone_closed_form_all_bins(periodic):
+    sr, N, M = 16000.0, 400, 80
+    spec = O.MelTSpec(sr=sr, n_fft=N, hop=160, n_mels=M, periodic=periodic)
+    rng = np.random.default_rng(7)
+    for m0 in [10, 33, 57, 70]:
+        A, phi = 0.37, rng.uniform(0, 2 * math.pi)
+        th0 = 2 * math.pi * spec.freqs[m0] / sr
+        x = A * np.cos(th0 * np.arange(N) + phi)
+        R, I = O.melt_components(x, spec)
+        S = O.dmp_energy(R, I)[0]
+        th = 2 * math.pi * spec.freqs / sr
+        Z = 0.5 * A * (np.exp(1j * phi) * _hann_dtft(th - th0, N, periodic)
+                       + np.exp(-1j * phi) * _hann_dtft(th + th0, N, periodic))
+        np.testing.assert_allclose(R[0] - 1j * I[0], Z, rtol=1e-9, atol=1e-9)
+        np.testing.assert_allclose(S, np.abs(Z) ** 2, rtol=1e-9, atol=1e-12)
+        assert int(np.argmax(S)) == m0
+
+
+def test_tone_peak_magnitude_at_own_bin():
+    # away from DC, |R - iI| at the tone's own bin is ~A/2 * sum(w) = A N / 4
+    sr, N = 16000.0, 400
+    spec = O.MelTSpec(sr=sr, n_fft=N, hop=160, n_mels=80)
+    m0 = 40
+    th0 = 2 * math.pi * spec.freqs[m0] / sr
+    x = 0.5 * np.cos(th0 * np.arange(N))
+    S = O.dmp_energy(*O.melt_components(x, spec))[0]
+    assert math.sqrt(S[m0]) == pytest.approx(0.5 * N / 4.0, rel=2e-3)
+
+
+# ------------------------------------------- uniform-frequency special case
+@pytest.mark.parametrize("periodic", [True, False])
+def test_uniform_frequencies_equal_rfft(periodic):
+    sr, N, H = 16000.0, 400, 160
+    freqs = np.arange(N // 2 + 1) * sr / N
+    spec = O.MelTSpec(sr=sr, n_fft=N, hop=H, periodic=periodic, freqs=freqs)
+    x = np.random.default_rng(3).standard_normal(N + 3 * H)
+    R, I = O.melt_components(x, spec)
+    X = O.frame_signal(x, N, H) * O.hann(N, periodic)[None, :]
+    F = np.fft.rfft(X, axis=1)
+    np.testing.assert_allclose(R, F.real, atol=1e-10)
+    np.testing.assert_allclose(I, -F.imag, atol=1e-10)
+    np.testing.assert_allclose(O.dft_power(X, N), np.abs(F) ** 2, rtol=1e-10, atol=1e-9)
+
+
+def test_parseval_full_uniform_set():
+    sr, N = 16000.0, 256
+    spec = O.MelTSpec(sr=sr, n_fft=N, hop=64, freqs=np.arange(N) * sr / N)
+    x = np.random.default_rng(5).standard_normal(N + 64)
+    S = O.dmp_energy(*O.melt_components(x, spec))
+    Xw = O.frame_signal(x, N, 64) * spec.window[None, :]
+    np.testing.assert_allclose(S.sum(axis=1), N * np.sum(Xw * Xw, axis=1), rtol=1e-11)
+
+
+# -------------------------------------------------------------- invariants
+def test_linearity_and_scale_law():
+    spec = O.MelTSpec()
+    g = np.random.default_rng(11)
+    x1, x2 = g.standard_normal(4000), g.standard_normal(4000)
+    a, b = 0.7, -1.9
+    R1, I1 = O.melt_components(x1, spec)
+    R2, I2 = O.melt_components(x2, spec)
+    R, I = O.melt_components(a * x1 + b * x2, spec)
+    np.testing.assert_allclose(R, a * R1 + b * R2, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(I, a * I1 + b * I2, rtol=1e-10, atol=1e-10)
+    S1 = O.dmp_energy(R1, I1)
+    S = O.dmp_energy(*O.melt_components(3.0 * x1, spec))
+    np.testing.assert_allclose(S, 9.0 * S1, rtol=1e-11)
+
+
+def test_hop_shift():
+    spec = O.MelTSpec()
+    x = np.random.default_rng(2).standard_normal(6000)
+    out = O.melt_clip(x, spec)
+    out2 = O.melt_clip(x[spec.hop:], spec)
+    np.testing.assert_allclose(out2, out[1:1 + out2.shape[0]], rtol=1e-12, atol=1e-12)
+    pre = np.concatenate([np.random.default_rng(3).standard_normal(spec.hop), x])
+    out3 = O.melt_clip(pre, spec)
+    np.testing.assert_allclose(out3[1:], out[:out3.shape[0] - 1], rtol=1e-12, atol=1e-12)
+
+
+def test_brute_force_tiny():
+    # tiny case summed with Python loops straight from Eq. 3
+    sr, N, H = 100.0, 8, 3
+    freqs = np.array([7.0, 19.0, 31.5])
+    spec = O.MelTSpec(sr=sr, n_fft=N, hop=H, freqs=freqs, periodic=False)
+    x = [math.sin(0.3 * k) + 0.1 * k for k in range(N + 2 * H + 1)]
+    R, I = O.melt_components(np.array(x), spec)
+    assert R.shape == (3, 3)
+    for t in range(3):
+        for m, f in enumerate(freqs):
+            r = i = 0.0
+            for n in range(N):
+                w = 0.5 - 0.5 * math.cos(2 * math.pi * n / (N - 1))
+                r += w * x[t * H + n] * math.cos(2 * math.pi * f * n / sr)
+                i += w * x[t * H + n] * math.sin(2 * math.pi * f * n / sr)
+            assert R[t, m] == pytest.approx(r, abs=1e-12)
+            assert I[t, m] == pytest.approx(i, abs=1e-12)
+
+
+# -------------------------------------------------------------------- DCT
+@pytest.mark.parametrize("K,M", [(40, 80), (40, 128), (13, 40)])
+def test_dct_matches_scipy(K, M):
+    D = O.dct2_ortho(K, M)
+    v = np.random.default_rng(1).standard_normal((5, M))
+    np.testing.assert_allclose(v @ D.T, scipy.fft.dct(v, type=2, norm="ortho", axis=1)[:, :K],
+                               atol=1e-12)
+
+
+def test_dct_orthonormal():
+    D = O.dct2_ortho(80, 80)
+    np.testing.assert_allclose(D @ D.T, np.eye(80), atol=1e-12)
+
+
+# ----------------------------------------------------- conventional pipeline
+def test_slaney_scale_textbook_points():
+    assert O.mel_slaney(1000.0) == pytest.approx(15.0)
+    assert O.mel_slaney(6400.0) == pytest.approx(42.0)
+    assert O.mel_slaney(200.0 / 3.0) == pytest.approx(1.0)
+    f = np.linspace(0, 8000, 101)
+    np.testing.assert_allclose(O.mel_slaney_inv(O.mel_slaney(f)), f, atol=1e-9)
+
+
+def test_htk_triangles_partition_of_unity():
+    N, sr = 1024, 16000.0
+    F = O.triangular_filterbank(40, N, sr, 0.0, 8000.0, "htk")
+    edges = O.mel_htk_inv(np.linspace(O.mel_htk(0.0), O.mel_htk(8000.0), 42))
+    fk = np.arange(N // 2 + 1) * sr / N
+    inside = (fk >= edges[1]) & (fk <= edges[-2])
+    np.testing.assert_allclose(F[:, inside].sum(axis=0), 1.0, atol=1e-12)
+    assert F.max() <= 1.0 + 1e-12
+
+
+def test_slaney_triangle_area_is_one():
+    N, sr = 4096, 16000.0
+    F = O.triangular_filterbank(40, N, sr, 0.0, 8000.0, "slaney")
+    # Riemann sum over bin spacing of a unit-area triangle spanning many bins
+    np.testing.assert_allclose(F.sum(axis=1) * sr / N, 1.0, rtol=2e-2)
+
+
+# ----------------------------------------------------------------- metrics
+def test_metrics_closed_forms():
+    a = np.array([1.0, 2.0, 3.0])
+    assert O.lin_ccc(a, a + 1.0) == pytest.approx(4.0 / 7.0)
+    A = np.random.default_rng(0).standard_normal((6, 9))
+    assert O.mean_row_cosine(A, A) == pytest.approx(1.0)
+    assert O.lin_ccc(A, A) == pytest.approx(1.0)
+    assert O.rmse_db(A, A) == 0.0
+
+
+def test_paper_delta_nat_to_db():
+    # Sec. IV-F: a 1% f_max retuning gives delta = 0.244 nat = 1.06 dB
+    assert O.rmse_db(np.full((3, 4), 0.244), np.zeros((3, 4))) == pytest.approx(1.06, abs=0.005)
+
+
+def test_paper_arithmetic_intensity():
+    # Sec. V, Fig. "roofline": MelT at ~57 FLOP/B for N=400, M=80
+    ai = O.gemm_flops_per_frame(400, 80) / O.materialised_bytes_per_frame(400, 80)
+    assert round(ai) == 57
+
+
+# ------------------------------------------------------- operand rounding
+def test_bf16_rounding_matches_torch():
+    g = np.random.default_rng(4)
+    v = np.concatenate([(g.standard_normal(20000) * 10.0 ** g.integers(-30, 30, 20000)).astype(np.float32),
+                        np.array([1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -(1.0 + 2 ** -8), 3e-39, -7e-40],
+                                 np.float32)])
+    assert v.dtype == np.float32
+    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(O.round_bf16(v.astype(np.float64)), ref)
+
+
+def test_e4m3_rounding_matches_torch():
+    g = np.random.default_rng(5)
+    v = (g.uniform(-460, 460, 20000) * 2.0 ** g.integers(-12, 1, 20000)).astype(np.float32)
+    v = np.concatenate([v, np.array([0.0, 2 ** -9, 1.5 * 2 ** -9, 2.5 * 2 ** -9, 448.0, -448.0, 17.0,
+                                     9.0, 11.0, 2 ** -10], np.float32)])
+    v = v[np.abs(v) <= 448.0]
+    ref = torch.from_numpy(v).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(O.round_e4m3(v.astype(np.float64)), ref)
+    assert O.round_e4m3(np.array([1000.0, -470.0]))[0] == 448.0
+    assert O.round_e4m3(np.array([1000.0, -470.0]))[1] == -448.0
+
+
+def test_rounded_forms_reduce_to_library_products():
+    spec = O.MelTSpec()
+    x = np.random.default_rng(9).standard_normal(3000).astype(np.float32)
+    X = O.frame_signal(x, 400, 160)
+    W = np.concatenate([spec.Wr, spec.Wi])
+    tb = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(torch.bfloat16).to(torch.float64)
+    Y = (tb(X) @ tb(W).T).numpy()
+    ref = np.log(Y[:, :80] ** 2 + Y[:, 80:] ** 2 + spec.eps)
+    np.testing.assert_allclose(O.melt_clip_rounded(x, spec, "bf16"), ref, rtol=1e-12, atol=1e-12)
+    # the split form is far closer to FP64 than plain bf16
+    exact = O.melt_clip(x, spec)
+    e_bf16 = np.abs(O.melt_clip_rounded(x, spec, "bf16") - exact).max()
+    e_x3 = np.abs(O.melt_clip_rounded(x, spec, "bf16x3") - exact).max()
+    assert e_x3 < e_bf16 / 50.0
+
+
+def test_fp8_form_power_of_two_scale_invariance():
+    # per-frame amax scaling makes x -> 2^k x change the output by exactly 2k ln 2
+    spec = O.MelTSpec(eps=0.0)
+    x = np.random.default_rng(8).standard_normal(2400).astype(np.float32)
+    a = O.melt_clip_rounded(x, spec, "fp8")
+    b = O.melt_clip_rounded(x * np.float32(8.0), spec, "fp8")
+    np.testing.assert_allclose(b - a, 2 * 3 * math.log(2.0), atol=1e-9)
+
+
+def test_zero_frame_is_log_eps():
+    spec = O.MelTSpec()
+    out = O.melt_clip(np.zeros(800), spec)
+    np.testing.assert_allclose(out, math.log(spec.eps))
+    np.testing.assert_allclose(O.melt_clip_rounded(np.zeros(800, np.float32), spec, "fp8"),
+                               math.log(spec.eps))
+
+
+# -------------------------------------------------------- golden fixtures
+def test_golden_paper_figures():
+    import json
+    with open(os.path.join(GOLDEN, "paper_figures.json")) as f:
+        g = json.load(f)
+    assert round(O.gemm_flops_per_frame(g["n_fft"], g["n_mels"])
+                 / O.materialised_bytes_per_frame(g["n_fft"], g["n_mels"])) == g["ai_melt_flop_per_byte"]
+    assert O.rmse_db(np.full(4, g["delta_nat"]), np.zeros(4)) == pytest.approx(g["delta_db"], abs=0.005)
