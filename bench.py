@@ -1,0 +1,455 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the MelT hot path on GB300.
+
+Workload (one "step"): MelT log-Mel of 64 synthetic clips of 30 s at 16 kHz
+(n_fft=400, hop=160, 80 Mel bins over 0-8000 Hz, periodic Hann, eps=1e-10),
+i.e. 64 x 2998 = 191,872 frames, through libmelt's C ABI (melt_forward).
+
+  value     frames/s with inputs resident in HBM (CUDA events, kernel stream)
+  e2e       frames/s through the public Python API with pinned HOST buffers:
+            H2D of the step's waveforms, the forward, D2H of its features
+  roofline  dominant kernel vs the measured HBM copy bandwidth
+            (bound "hbm" for the tensor-core forms, "alu" for FP32 SIMT)
+  cpu_baseline  the FP64 oracle on the host cores on a bounded sample
+
+Inputs larger than L2: the step's inputs and outputs rotate over several
+device copies (together well above the 129 MB L2).
+
+--impl reference times the FP64 CPU oracle on the same workload (bounded
+sample per step) and prints the same JSON line with "impl": "reference".
+Multi-GPU (torchrun): replicas only; every rank runs the same per-GPU
+workload (weak scaling), timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (generator workload, sr, n_fft, hop, n_mels, fmin, fmax)
+    "rich_64x30s": ("rich_64x30s", 16000.0, 400, 160, 80, 0.0, 8000.0),
+    "levels_1024x10s": ("levels_1024x10s", 16000.0, 400, 160, 80, 0.0, 8000.0),
+    "tones_8x1s": ("tones_8x1s", 16000.0, 400, 160, 80, 0.0, 8000.0),
+}
+L2_BYTES = 129e6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="melt", choices=["melt", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "bf16x3", "fp8"])
+    ap.add_argument("--workload", default="rich_64x30s", choices=sorted(WORKLOADS))
+    ap.add_argument("--n-mels", type=int, default=None)
+    ap.add_argument("--mfcc", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forms", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time every other operand form")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 100 ms in the background."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        self.t0 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ workload
+def make_inputs(args):
+    from paper_2606_01009_gb300 import inputs as G
+    gen, sr, n_fft, hop, n_mels, fmin, fmax = WORKLOADS[args.workload]
+    if args.n_mels:
+        n_mels = args.n_mels
+    clips, sr = G.workload(gen)
+    pk = G.pack_clips(clips)
+    return clips, pk, dict(sr=sr, n_fft=n_fft, hop=hop, n_mels=n_mels, fmin=fmin, fmax=fmax)
+
+
+def frames_of(lengths, n_fft, hop):
+    return int(sum((L - n_fft) // hop + 1 for L in lengths if L >= n_fft))
+
+
+def algorithmic_bytes(lengths, n_fft, hop, n_out):
+    """Bytes a perfect implementation moves: each needed sample read once,
+    each feature written once (FP32)."""
+    tot = 0
+    for L in lengths:
+        if L < n_fft:
+            continue
+        T = (L - n_fft) // hop + 1
+        tot += 4 * ((T - 1) * hop + n_fft) + 4 * T * n_out
+    return tot
+
+
+def cpu_oracle_baseline(clips, cfg, n_mfcc, seconds):
+    """Time the FP64 oracle as it stands on the host cores; bounded sample."""
+    from oracle import melt_oracle as O
+    spec = O.MelTSpec(sr=cfg["sr"], n_fft=cfg["n_fft"], hop=cfg["hop"], n_mels=cfg["n_mels"],
+                      fmin=cfg["fmin"], fmax=cfg["fmax"], n_mfcc=n_mfcc)
+    frames = 0
+    n_clips = 0
+    t0 = time.perf_counter()
+    i = 0
+    while True:
+        c = clips[i % len(clips)]
+        out = O.melt_clip(c, spec)
+        frames += out.shape[0]
+        n_clips += 1
+        i += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": frames / el, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_clips} clips ({frames} frames) of the workload, FP64 numpy oracle, {el:.1f} s"}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------- main arm
+class Workload:
+    """Device-resident copies of one batch, rotated so inputs+outputs exceed L2."""
+
+    def __init__(self, args, dev):
+        import torch
+        self.clips, self.pk, self.cfg = make_inputs(args)
+        self.lens = np.ascontiguousarray(self.pk.lengths, dtype=np.int64)
+        self.offs = np.ascontiguousarray(self.pk.offsets, dtype=np.int64)
+        self.wave_h = torch.from_numpy(self.pk.wave)
+        self.in_bytes = self.pk.wave.nbytes
+        self.dev = dev
+        self.waves = None
+
+    def device_copies(self, n_out, T):
+        import torch
+        out_bytes = T * n_out * 4
+        copies = max(2, math.ceil(2.5 * L2_BYTES / (self.in_bytes + out_bytes)))
+        if self.waves is None or len(self.waves) < copies:
+            self.waves = [self.wave_h.to(self.dev) for _ in range(copies)]
+        outs = [torch.empty((T, n_out), device=self.dev) for _ in range(copies)]
+        return self.waves[:copies], outs, copies
+
+
+def time_form(args, W, precision, steps, warmup, world, want_e2e):
+    """Time melt_forward for one operand form; returns a dict of measurements."""
+    import ctypes as C
+    import torch
+    from paper_2606_01009_gb300 import melt
+
+    cfg, dev = W.cfg, W.dev
+    fe = melt.Frontend(sr=cfg["sr"], n_fft=cfg["n_fft"], hop=cfg["hop"], n_mels=cfg["n_mels"],
+                       fmin=cfg["fmin"], fmax=cfg["fmax"], precision=precision, n_mfcc=args.mfcc)
+    n_out = fe.n_out
+    T = fe.total_frames(W.lens)
+    waves, outs, copies = W.device_copies(n_out, T)
+    stream = torch.cuda.current_stream(dev)
+    sp = C.c_void_p(stream.cuda_stream)
+    lp = W.lens.ctypes.data_as(C.POINTER(C.c_int64))
+    op = W.offs.ctypes.data_as(C.POINTER(C.c_int64))
+    wp = [C.c_void_p(w.data_ptr()) for w in waves]
+    outp = [C.c_void_p(o.data_ptr()) for o in outs]
+    fwd = melt.lib.melt_forward
+    B = int(W.lens.shape[0])
+
+    def step(i):
+        st = fwd(fe.handle, wp[i % copies], op, lp, B, outp[i % copies], sp)
+        if st != 0:
+            raise melt.MeltError(st, "melt_forward")
+
+    for i in range(warmup):
+        step(i)
+    fe.sync(stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(min(steps, 2000))]
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        if i < len(ev):
+            ev[i][0].record(stream)
+        step(i)
+        if i < len(ev):
+            ev[i][1].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    fe.sync(stream)
+    ms_total = e0.elapsed_time(e1)
+    launch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    res = {"precision": precision, "T": T, "n_out": n_out, "copies": copies, "steps": steps,
+           "ms_total": ms_total, "ms_per_step": ms_total / steps, "launch_ms": launch_ms,
+           "value": world * T * steps / (ms_total / 1e3), "clocks": ck,
+           "out_sample": outs[0], "fe": fe}
+
+    if want_e2e:
+        wave_pin = W.wave_h.pin_memory()
+        out_pin = torch.empty((T, n_out), dtype=torch.float32).pin_memory()
+        wave_d, out_d = waves[0], outs[0]
+
+        def e2e_step():
+            wave_d.copy_(wave_pin, non_blocking=True)
+            fe(wave_d, W.offs, W.lens, out=out_d, stream=stream)
+            out_pin.copy_(out_d, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        E = args.e2e_steps
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(E):
+            e2e_step()
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        fe.sync(stream)
+        e2e_ms = a0.elapsed_time(a1) / E
+        res["e2e"] = {"value": world * T / (e2e_ms / 1e3), "unit": "frames/s",
+                      "h2d_bytes_per_step": W.in_bytes, "d2h_bytes_per_step": T * n_out * 4,
+                      "ms_per_step": e2e_ms}
+    return res
+
+
+def roofline(cfg, W, r, peaks, peak_kind):
+    prec, T, n_out = r["precision"], r["T"], r["n_out"]
+    flops = 2 * cfg["n_fft"] * 2 * cfg["n_mels"] * T * (3 if prec == "bf16x3" else 1)
+    alg_bytes = algorithmic_bytes(W.lens, cfg["n_fft"], cfg["hop"], n_out)
+    sec = r["launch_ms"] / 1e3
+    if prec == "fp32":
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = flops / sec / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "peak_note": "FP32 FFMA peak derived: 152 SMs x 128 lanes x 2 FLOP x "
+                f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz max SM clock",
+                "algorithmic_flops_per_launch": flops, "launch_ms": r["launch_ms"]}
+    ach = alg_bytes / sec / 1e9
+    peak = peaks["hbm_gbs"]
+    out = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+           "traffic": None, "peak_note": f"hbm_gbs of {peak_kind} peaks (copy bandwidth)",
+           "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": r["launch_ms"],
+           "tensor_tflops": flops / sec / 1e12}
+    out["tensor_frac_of_bf16_peak"] = out["tensor_tflops"] / peaks.get("bf16_tflops", 1900.0)
+    return out
+
+
+def accuracy_vs_oracle(W, forms, cfg, mfcc, n_clips=2):
+    """dB error of each form's output vs the FP64 oracle on the first clips (CPU leg)."""
+    from oracle import melt_oracle as O
+    spec = O.MelTSpec(sr=cfg["sr"], n_fft=cfg["n_fft"], hop=cfg["hop"], n_mels=cfg["n_mels"],
+                      fmin=cfg["fmin"], fmax=cfg["fmax"], n_mfcc=mfcc)
+    ref = np.concatenate([O.melt_clip(c, spec) for c in W.clips[:n_clips]])
+    rows = ref.shape[0]
+    acc = {}
+    for name, r in forms.items():
+        got = r["out_sample"][:rows].cpu().numpy().astype(np.float64)
+        mx, rms = O.err_db(got, ref)
+        mask = O.within_db_of_frame_max(ref, 60.0) if not mfcc else None
+        mx60, rms60 = O.err_db(got, ref, mask) if mask is not None else (mx, rms)
+        acc[name] = {"max_db": mx, "rms_db": rms, "max_db_within_60dB": mx60, "rms_db_within_60dB": rms60}
+    return acc, f"first {n_clips} clips ({rows} frames) vs the FP64 oracle"
+
+
+def run_melt(args, rank, world):
+    import torch
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    W = Workload(args, dev)
+    cfg = W.cfg
+    peaks, peak_kind = load_peaks()
+    head = time_form(args, W, args.precision, args.steps, args.warmup, world, want_e2e=True)
+    forms = {args.precision: head}
+    if args.forms:
+        for prec in ["fp32", "bf16", "bf16x3", "fp8"]:
+            if prec == args.precision:
+                continue
+            # scale the step count so each form's timed region is ~1 s at most
+            k = max(10, min(args.steps, int(1000.0 / max(head["ms_per_step"], 1e-3) * 0.3)))
+            try:
+                forms[prec] = time_form(args, W, prec, k if prec != "fp32" else max(10, k // 20),
+                                        max(3, args.warmup // 10), world, want_e2e=False)
+            except Exception as e:  # a form this configuration cannot run
+                forms[prec] = {"error": str(e)}
+    T, n_out = head["T"], head["n_out"]
+    B = int(W.lens.shape[0])
+    res = {
+        "metric": "log-Mel frames/s on 1 GB300 (MelT, %s)" % args.precision,
+        "value": head["value"], "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "fp8": "fp8e4m3"}[args.precision],
+        "data": "synthetic (seeded chirps, harmonic stacks, pink noise, AM bursts; stands in for LibriSpeech)",
+        "config": {"workload": f"{args.workload}: {B} clips, {T} frames, sr={cfg['sr']:.0f}, n_fft={cfg['n_fft']}, "
+                               f"hop={cfg['hop']}, n_mels={cfg['n_mels']}, n_mfcc={args.mfcc}, periodic Hann, eps=1e-10",
+                   "precision": args.precision, "frames_per_step": T,
+                   "l2": f"inputs+outputs rotate over {head['copies']} device copies "
+                         f"({head['copies'] * (W.in_bytes + T * n_out * 4) / 1e6:.0f} MB > 129 MB L2)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": head["e2e"],
+        "gpu_launches": args.steps,
+        "roofline": roofline(cfg, W, head, peaks, peak_kind),
+        "clocks": {k: head["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples")},
+    }
+    if args.forms:
+        res["forms"] = {}
+        for name, r in forms.items():
+            if "error" in r:
+                res["forms"][name] = r
+                continue
+            rf = roofline(cfg, W, r, peaks, peak_kind)
+            res["forms"][name] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "steps": r["steps"],
+                                  "roofline_frac": rf["frac"], "bound": rf["bound"],
+                                  "achieved": rf["achieved"], "unit": rf["unit"],
+                                  "clocks_sm_mhz": r["clocks"]["sm_mhz"]}
+    return res, W, forms
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    clips, pk, cfg = make_inputs(args)
+    from oracle import melt_oracle as O
+    spec = O.MelTSpec(sr=cfg["sr"], n_fft=cfg["n_fft"], hop=cfg["hop"], n_mels=cfg["n_mels"],
+                      fmin=cfg["fmin"], fmax=cfg["fmax"], n_mfcc=args.mfcc)
+    T_all = frames_of(pk.lengths, cfg["n_fft"], cfg["hop"])
+    # bounded sample per step: a few clips of the workload
+    per_step = max(1, min(len(clips), 4))
+    for i in range(args.warmup):
+        O.melt_clip(clips[i % len(clips)], spec)
+    K = args.steps
+    frames = 0
+    t0 = time.perf_counter()
+    for s in range(K):
+        for j in range(per_step):
+            frames += O.melt_clip(clips[(s * per_step + j) % len(clips)], spec).shape[0]
+    el = time.perf_counter() - t0
+    value = frames / el
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {
+        "impl": "reference", "metric": "log-Mel frames/s on 1 GB300 (MelT, %s)" % args.precision,
+        "value": value, "unit": "frames/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": el * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {len(clips)} clips, {T_all} frames (each step: a {per_step}-clip sample)",
+                   "precision": "fp64 oracle", "parallelism": "host CPU"},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} clips per step, {K} steps, {frames} frames"},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def _jsonable(o):
+    if hasattr(o, "item"):
+        return o.item()
+    return str(o)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res, default=_jsonable), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    res, W, forms = run_melt(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_oracle_baseline(W.clips, W.cfg, args.mfcc, args.cpu_seconds)
+            ok = {k: v for k, v in forms.items() if "error" not in v}
+            res["accuracy_db"], res["accuracy_sample"] = accuracy_vs_oracle(W, ok, W.cfg, args.mfcc)
+        print(json.dumps(res, default=_jsonable), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

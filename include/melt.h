@@ -1,0 +1,172 @@
+/*
+ * melt.h - C ABI of libmelt, a GB300 (sm_103a) implementation of the MelT /
+ * MFCCT audio frontend of arXiv 2606.01009 ("Matmul-Native Mel Frontends").
+ *
+ * What is computed (paper Sec. III-A):
+ *   f_m      M analysis frequencies, uniform on the HTK Mel scale (Eq. 1-2):
+ *            the M interior points of M+2 Mel-uniform points on [fmin, fmax]
+ *   w[n]     Hann window of length N (periodic or symmetric)
+ *   W_r,W_i  window-folded basis  w[n] cos(2 pi f_m n / sr), w[n] sin(...)  (Eq. 5)
+ *   frame t  x[tH .. tH+N-1] of a clip, T = floor((L-N)/H)+1 frames (0 if L<N),
+ *            no centring or padding
+ *   R, I     R = X W_r^T, I = X W_i^T, one GEMM against [W_r; W_i] (Eq. 6)
+ *   S        R^2 + I^2 (Eq. 7)
+ *   MelT     log(S + eps), natural log, additive eps (Eq. 8)
+ *   MFCCT    log(S + eps) D^T, D = first K rows of the orthonormal DCT-II (Eq. 9)
+ *
+ * Conventions for every entry point:
+ *   - Pointers named "device" are CUDA device pointers of the current device;
+ *     "host" pointers are ordinary host memory.  The caller owns every buffer
+ *     it passes; the library owns what a melt_basis holds (device basis,
+ *     workspace, pinned staging, cached plans) and frees it in melt_destroy.
+ *   - A `stream` argument is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Forward calls are asynchronous on that stream and do
+ *     not allocate once a basis has seen a batch of the same or larger size.
+ *   - Errors are returned as negative melt_status values; nothing aborts.
+ *     Errors found by a kernel while it runs (a bounded wait that ran out)
+ *     are latched in the basis and reported by melt_sync().
+ *   - One melt_basis may be used by one host thread at a time.
+ */
+#ifndef MELT_H_
+#define MELT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct melt_basis melt_basis;
+
+typedef enum {
+  MELT_OK = 0,
+  MELT_ERR_ARG = -1,          /* invalid argument (null pointer, size, alignment) */
+  MELT_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+  MELT_ERR_OOM = -3,          /* device or pinned host allocation failed */
+  MELT_ERR_UNSUPPORTED = -4,  /* valid request this build or device cannot run */
+  MELT_ERR_TIMEOUT = -5,      /* a kernel's bounded wait ran out (pipeline stalled) */
+  MELT_ERR_NO_DEVICE = -6     /* no CUDA device, or not an sm_103 device */
+} melt_status;
+
+typedef enum { MELT_WIN_HANN_PERIODIC = 0, MELT_WIN_HANN_SYMMETRIC = 1 } melt_window;
+
+/*
+ * GEMM operand formats (the paper runs FP32/TF32 only; the reduced forms are
+ * this library's).  All accumulate in FP32 and take FP32 waveforms.
+ *   MELT_FP32    FP32 samples x FP32 basis on CUDA cores (FFMA).
+ *   MELT_BF16    BF16 samples x BF16 basis on tcgen05 tensor cores.
+ *   MELT_BF16X3  two-term BF16 splits of both operands, three products
+ *                (hi*hi + hi*lo + lo*hi) on tcgen05 tensor cores.
+ *   MELT_FP8E4M3 e4m3 samples with a per-frame scale amax(|x_t|)/448 and an
+ *                e4m3 basis scaled by 448, on tcgen05 tensor cores.
+ */
+typedef enum { MELT_FP32 = 0, MELT_BF16 = 1, MELT_BF16X3 = 2, MELT_FP8E4M3 = 3 } melt_precision;
+
+/*
+ * melt_basis_create - build the FP64 basis of Sec. III-A (Eq. 1, 2, 5) on the
+ * host, round it to the operand format and upload it to the current device.
+ *   sr          sample rate in Hz (> 0)
+ *   n_fft       frame length N (16..4096, multiple of 4)
+ *   hop         hop H (1..n_fft, multiple of 4)
+ *   n_mels      M (1..128)
+ *   fmin, fmax  0 <= fmin < fmax <= sr/2
+ *   window      melt_window
+ *   out         receives the new basis (host pointer to a handle)
+ * Defaults: MELT_FP32, log-Mel output (no MFCC), eps = 1e-10.
+ * Returns MELT_ERR_ARG on a bad parameter, MELT_ERR_NO_DEVICE without an
+ * sm_103 device, MELT_ERR_OOM/MELT_ERR_CUDA on allocation or copy failure.
+ */
+melt_status melt_basis_create(double sr, int n_fft, int hop, int n_mels, double fmin,
+                              double fmax, int window, melt_basis** out);
+
+/*
+ * melt_basis_create_ex - as melt_basis_create, plus:
+ *   precision   melt_precision of the projection GEMM
+ *   n_mfcc      K > 0 appends the DCT-II of Eq. 9 (K <= n_mels); 0 = log-Mel
+ *   eps         additive eps of Eq. 8 (>= 0)
+ */
+melt_status melt_basis_create_ex(double sr, int n_fft, int hop, int n_mels, double fmin,
+                                 double fmax, int window, int precision, int n_mfcc,
+                                 double eps, melt_basis** out);
+
+/*
+ * melt_basis_create_freqs - basis at caller-chosen analysis frequencies
+ * (host array freqs[n_freqs], Hz, each in [0, sr/2]) instead of the Mel
+ * centres; used to check the projection against a plain DFT (f_k = k sr/N).
+ * Other arguments as melt_basis_create_ex.
+ */
+melt_status melt_basis_create_freqs(double sr, int n_fft, int hop, const double* freqs,
+                                    int n_freqs, int window, int precision, int n_mfcc,
+                                    double eps, melt_basis** out);
+
+/* Frames of a clip of `length` samples: floor((L-N)/H)+1, or 0 if L < N (or basis NULL). */
+int64_t melt_num_frames(const melt_basis* basis, int64_t length);
+
+/* Values per output frame: n_mfcc if MFCC is on, else n_mels; 0 if basis is NULL. */
+int melt_num_outputs(const melt_basis* basis);
+
+/*
+ * melt_basis_info - copies basis parameters to host ints/doubles (any may be NULL):
+ *   ints[6]    = {n_fft, hop, n_mels, n_mfcc, precision, window}
+ *   doubles[4] = {sr, fmin, fmax, eps}
+ */
+melt_status melt_basis_info(const melt_basis* basis, int* ints, double* doubles);
+
+/*
+ * melt_basis_get_fp64 - copy the host FP64 basis before rounding (Eq. 5) to
+ *   freqs  host double[n_mels]            analysis frequencies f_m in Hz
+ *   w      host double[2*n_mels*n_fft]    rows 0..M-1 = W_r, rows M..2M-1 = W_i,
+ *                                         row-major (n fastest)
+ * Either pointer may be NULL.
+ */
+melt_status melt_basis_get_fp64(const melt_basis* basis, double* freqs, double* w);
+
+/*
+ * melt_forward - MelT (Eq. 8) or MFCCT (Eq. 9) features of a batch of clips.
+ *   wave     device float[]: clip b occupies wave[offsets[b] .. offsets[b]+lengths[b]);
+ *            the whole 4-float-aligned span [offsets[b], offsets[b]+round_up(lengths[b],4))
+ *            must be readable (its tail beyond lengths[b] is never used).
+ *            wave must be 16-byte aligned.
+ *   offsets  host int64[batch], each a multiple of 4 (NULL = clips packed back to
+ *            back at 4-float alignment: offsets[b] = sum_{c<b} round_up(lengths[c],4))
+ *   lengths  host int64[batch], each >= 0
+ *   batch    number of clips (>= 0; 0 is a no-op)
+ *   out      device float[sum_b T_b * n_out], 16-byte aligned: clip after clip,
+ *            frame-major, n_out = melt_num_outputs(basis) values per frame
+ *   stream   cudaStream_t as void*
+ * Asynchronous; the host arrays may be reused as soon as it returns.
+ * Returns MELT_ERR_ARG for a bad pointer, alignment or length.
+ */
+melt_status melt_forward(melt_basis* basis, const float* wave, const int64_t* offsets,
+                         const int64_t* lengths, int batch, float* out, void* stream);
+
+/*
+ * melt_forward_components - debug form: the raw projection (Eq. 6) for every
+ * frame, out = device float[sum_b T_b * 2M]: per frame M values of R then M of I.
+ * Only MELT_FP32 bases.  Arguments otherwise as melt_forward.
+ */
+melt_status melt_forward_components(melt_basis* basis, const float* wave,
+                                    const int64_t* offsets, const int64_t* lengths,
+                                    int batch, float* out, void* stream);
+
+/*
+ * melt_sync - wait for `stream`, then report (and clear) any error a kernel of
+ * this basis latched while running (MELT_ERR_TIMEOUT), else the stream's own
+ * CUDA status.
+ */
+melt_status melt_sync(melt_basis* basis, void* stream);
+
+/* melt_destroy - free everything the basis owns (NULL is a no-op). Synchronises the device. */
+melt_status melt_destroy(melt_basis* basis);
+
+/* Static English text for a status code. */
+const char* melt_status_string(int status);
+
+/* Library version string, e.g. "melt 0.1 sm_103a". */
+const char* melt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MELT_H_ */

@@ -1,0 +1,414 @@
+// Host side of libmelt: FP64 basis builder, tile planner and the C ABI.
+//
+// The basis (Sec. III-A, Eq. 1, 2, 5) is built once per configuration in
+// FP64 on the host: the phase 2 pi f_m n / sr, its cos/sin and the window
+// product are all double precision, and only the finished values are rounded
+// to the operand format of the chosen kernel and uploaded.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "melt_internal.h"
+#include "melt_tc.h"
+
+using namespace melt;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kStagingSlots = 4;
+
+// ---- Eq. 1 and Eq. 2: HTK Mel map and its inverse
+double hz_to_mel(double f) { return 2595.0 * std::log10(1.0 + f / 700.0); }
+double mel_to_hz(double mu) { return 700.0 * (std::pow(10.0, mu / 2595.0) - 1.0); }
+
+struct Staging {
+  TileDesc* host = nullptr;    // pinned
+  TileDesc* dev = nullptr;
+  size_t cap = 0;              // tiles
+  size_t n = 0;                // tiles currently held (valid when `key_batch >= 0`)
+  cudaEvent_t done = nullptr;  // recorded after the last kernel that read `dev`
+  // batch layout the tiles were planned for (plan cache key)
+  int key_batch = -1;
+  std::vector<int64_t> key_offsets, key_lengths;
+};
+
+}  // namespace
+
+struct melt_basis {
+  int device = 0;
+  int sm_count = 0;
+  double sr = 0, fmin = 0, fmax = 0, eps = 1e-10;
+  int n_fft = 0, hop = 0, n_mels = 0, n_mfcc = 0, precision = 0, window = 0;
+  std::vector<double> freqs;   // [M]
+  std::vector<double> w64;     // [2M][N]: W_r rows then W_i rows
+  // device data
+  int mj = 0, mp = 0;          // SIMT: 16*mj padded mels
+  float* d_w32 = nullptr;      // SIMT basis [N][2*mp]
+  float* d_dct = nullptr;      // [K][M]
+  int* d_err = nullptr;        // latched kernel errors
+  TcBasis tc;                  // tensor-core operand images (BF16/FP8 forms)
+  Staging staging[kStagingSlots];
+  int next_slot = 0;
+  std::vector<TileDesc> plan;  // host scratch for planning
+};
+
+namespace {
+
+melt_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return MELT_OK;
+  if (e == cudaErrorMemoryAllocation) return MELT_ERR_OOM;
+  return MELT_ERR_CUDA;
+}
+
+#define MELT_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_status(e_);        \
+  } while (0)
+
+void free_basis(melt_basis* b) {
+  if (!b) return;
+  cudaFree(b->d_w32);
+  cudaFree(b->d_dct);
+  cudaFree(b->d_err);
+  tc_free(&b->tc);
+  for (auto& s : b->staging) {
+    if (s.done) cudaEventSynchronize(s.done), cudaEventDestroy(s.done);
+    cudaFreeHost(s.host);
+    cudaFree(s.dev);
+  }
+  delete b;
+}
+
+// Build W_r, W_i (Eq. 5) in FP64.
+void build_fp64(melt_basis* b) {
+  const int N = b->n_fft, M = b->n_mels;
+  const double den = b->window == MELT_WIN_HANN_SYMMETRIC ? (double)(N - 1) : (double)N;
+  std::vector<double> w(N);
+  for (int n = 0; n < N; ++n) w[n] = 0.5 - 0.5 * std::cos(2.0 * kPi * n / den);
+  b->w64.assign((size_t)2 * M * N, 0.0);
+  for (int m = 0; m < M; ++m) {
+    for (int n = 0; n < N; ++n) {
+      const double theta = 2.0 * kPi * b->freqs[m] * (double)n / b->sr;
+      b->w64[(size_t)m * N + n] = w[n] * std::cos(theta);
+      b->w64[(size_t)(M + m) * N + n] = w[n] * std::sin(theta);
+    }
+  }
+}
+
+melt_status upload_fp32(melt_basis* b) {
+  const int N = b->n_fft, M = b->n_mels;
+  b->mj = (M + 15) / 16;
+  b->mp = 16 * b->mj;
+  std::vector<float> h((size_t)N * 2 * b->mp, 0.f);
+  for (int n = 0; n < N; ++n)
+    for (int m = 0; m < M; ++m) {
+      h[(size_t)n * 2 * b->mp + 2 * m] = (float)b->w64[(size_t)m * N + n];
+      h[(size_t)n * 2 * b->mp + 2 * m + 1] = (float)b->w64[(size_t)(M + m) * N + n];
+    }
+  MELT_CUDA(cudaMalloc(&b->d_w32, h.size() * sizeof(float)));
+  MELT_CUDA(cudaMemcpy(b->d_w32, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return MELT_OK;
+}
+
+melt_status upload_dct(melt_basis* b) {
+  if (b->n_mfcc == 0) return MELT_OK;
+  const int K = b->n_mfcc, M = b->n_mels;
+  std::vector<float> d((size_t)K * M);
+  for (int k = 0; k < K; ++k)
+    for (int m = 0; m < M; ++m) {
+      double v = std::cos(kPi * k * (2.0 * m + 1.0) / (2.0 * M)) * std::sqrt(2.0 / M);
+      if (k == 0) v *= std::sqrt(0.5);
+      d[(size_t)k * M + m] = (float)v;
+    }
+  MELT_CUDA(cudaMalloc(&b->d_dct, d.size() * sizeof(float)));
+  MELT_CUDA(cudaMemcpy(b->d_dct, d.data(), d.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return MELT_OK;
+}
+
+melt_status check_device(int* dev, int* sms) {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return MELT_ERR_NO_DEVICE;
+  MELT_CUDA(cudaGetDevice(dev));
+  cudaDeviceProp prop;
+  MELT_CUDA(cudaGetDeviceProperties(&prop, *dev));
+  if (prop.major != 10 || prop.minor != 3) return MELT_ERR_NO_DEVICE;
+  *sms = prop.multiProcessorCount;
+  return MELT_OK;
+}
+
+melt_status create_common(double sr, int n_fft, int hop, const double* freqs, int n_freqs,
+                          double fmin, double fmax, int window, int precision, int n_mfcc,
+                          double eps, melt_basis** out) {
+  if (!out) return MELT_ERR_ARG;
+  *out = nullptr;
+  if (!(sr > 0) || n_fft < 16 || n_fft > 4096 || (n_fft & 3) || hop < 1 || hop > n_fft ||
+      (hop & 3) || n_freqs < 1 || n_freqs > 128 || n_mfcc < 0 || n_mfcc > n_freqs ||
+      !(eps >= 0) || (window != MELT_WIN_HANN_PERIODIC && window != MELT_WIN_HANN_SYMMETRIC) ||
+      precision < MELT_FP32 || precision > MELT_FP8E4M3)
+    return MELT_ERR_ARG;
+  for (int m = 0; m < n_freqs; ++m)
+    if (!(freqs[m] >= 0.0) || !(freqs[m] <= sr / 2)) return MELT_ERR_ARG;
+  int dev = 0, sms = 0;
+  melt_status st = check_device(&dev, &sms);
+  if (st != MELT_OK) return st;
+  melt_basis* b = new (std::nothrow) melt_basis();
+  if (!b) return MELT_ERR_OOM;
+  b->device = dev;
+  b->sm_count = sms;
+  b->sr = sr; b->fmin = fmin; b->fmax = fmax; b->eps = eps;
+  b->n_fft = n_fft; b->hop = hop; b->n_mels = n_freqs; b->n_mfcc = n_mfcc;
+  b->precision = precision; b->window = window;
+  b->freqs.assign(freqs, freqs + n_freqs);
+  build_fp64(b);
+  st = upload_fp32(b);
+  if (st == MELT_OK) st = upload_dct(b);
+  if (st == MELT_OK && precision != MELT_FP32) {
+    TcConfig c{n_fft, hop, n_freqs, precision};
+    st = tc_build(&b->tc, c, b->w64.data());
+  }
+  if (st == MELT_OK) {
+    cudaError_t e = cudaMalloc(&b->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+    st = cuda_status(e);
+  }
+  for (int i = 0; st == MELT_OK && i < kStagingSlots; ++i)
+    st = cuda_status(cudaEventCreateWithFlags(&b->staging[i].done, cudaEventDisableTiming));
+  if (st != MELT_OK) {
+    free_basis(b);
+    return st;
+  }
+  *out = b;
+  return MELT_OK;
+}
+
+int64_t frames_of(const melt_basis* b, int64_t len) {
+  if (len < b->n_fft) return 0;
+  return (len - b->n_fft) / b->hop + 1;
+}
+
+// Build the tile list of a batch; returns MELT_ERR_ARG on bad offsets/lengths.
+melt_status plan_tiles(melt_basis* b, const int64_t* offsets, const int64_t* lengths, int batch) {
+  b->plan.clear();
+  int64_t row = 0, off = 0;
+  for (int c = 0; c < batch; ++c) {
+    const int64_t L = lengths[c];
+    if (L < 0) return MELT_ERR_ARG;
+    const int64_t o = offsets ? offsets[c] : off;
+    if (o < 0 || (o & 3)) return MELT_ERR_ARG;
+    off += (L + 3) & ~int64_t(3);
+    const int64_t T = frames_of(b, L);
+    for (int64_t t0 = 0; t0 < T; t0 += kTileFrames) {
+      TileDesc d;
+      d.in_off = o + t0 * b->hop;
+      d.out_row = row + t0;
+      d.n_frames = (int32_t)std::min<int64_t>(kTileFrames, T - t0);
+      d.n_samples = (int32_t)std::min<int64_t>(L - t0 * b->hop, INT32_MAX);
+      d.group = 0;
+      d.clip = c;
+      b->plan.push_back(d);
+    }
+    row += T;
+  }
+  return MELT_OK;
+}
+
+bool same_layout(const Staging& s, const int64_t* offsets, const int64_t* lengths, int batch) {
+  if (s.key_batch != batch) return false;
+  if ((offsets == nullptr) != s.key_offsets.empty()) return false;
+  if (std::memcmp(s.key_lengths.data(), lengths, sizeof(int64_t) * batch) != 0) return false;
+  return !offsets || std::memcmp(s.key_offsets.data(), offsets, sizeof(int64_t) * batch) == 0;
+}
+
+// A slot already holding the device tile list of this exact batch layout.
+Staging* cached_plan(melt_basis* b, const int64_t* offsets, const int64_t* lengths, int batch) {
+  for (auto& s : b->staging)
+    if (same_layout(s, offsets, lengths, batch)) return &s;
+  return nullptr;
+}
+
+// Copy the plan to the device through the next pinned staging slot.
+melt_status stage_plan(melt_basis* b, const int64_t* offsets, const int64_t* lengths, int batch,
+                       cudaStream_t stream, Staging** slot_out) {
+  Staging& s = b->staging[b->next_slot];
+  b->next_slot = (b->next_slot + 1) % kStagingSlots;
+  MELT_CUDA(cudaEventSynchronize(s.done));  // the previous user of this slot is finished
+  s.key_batch = -1;
+  const size_t n = std::max<size_t>(b->plan.size(), 1);
+  if (n > s.cap) {
+    cudaFreeHost(s.host);
+    cudaFree(s.dev);
+    s.host = nullptr; s.dev = nullptr; s.cap = 0;
+    const size_t cap = std::max<size_t>(n, 1024);
+    MELT_CUDA(cudaMallocHost(&s.host, cap * sizeof(TileDesc)));
+    MELT_CUDA(cudaMalloc(&s.dev, cap * sizeof(TileDesc)));
+    s.cap = cap;
+  }
+  std::memcpy(s.host, b->plan.data(), b->plan.size() * sizeof(TileDesc));
+  MELT_CUDA(cudaMemcpyAsync(s.dev, s.host, b->plan.size() * sizeof(TileDesc),
+                            cudaMemcpyHostToDevice, stream));
+  s.n = b->plan.size();
+  s.key_batch = batch;
+  s.key_lengths.assign(lengths, lengths + batch);
+  if (offsets) s.key_offsets.assign(offsets, offsets + batch); else s.key_offsets.clear();
+  *slot_out = &s;
+  return MELT_OK;
+}
+
+melt_status forward_impl(melt_basis* b, const float* wave, const int64_t* offsets,
+                         const int64_t* lengths, int batch, float* out, void* stream_v,
+                         int mode) {
+  if (!b || batch < 0 || (batch > 0 && (!lengths || !wave || !out))) return MELT_ERR_ARG;
+  if (((uintptr_t)wave & 15) || ((uintptr_t)out & 15)) return MELT_ERR_ARG;
+  if (batch == 0) return MELT_OK;
+  cudaStream_t stream = (cudaStream_t)stream_v;
+  Staging* slot = cached_plan(b, offsets, lengths, batch);
+  if (!slot) {
+    melt_status st = plan_tiles(b, offsets, lengths, batch);
+    if (st != MELT_OK) return st;
+    if (b->plan.empty()) return MELT_OK;
+    st = stage_plan(b, offsets, lengths, batch, stream, &slot);
+    if (st != MELT_OK) return st;
+  }
+  if (slot->n == 0) return MELT_OK;
+  const int n_tiles = (int)slot->n;
+  cudaError_t e;
+  if (b->precision == MELT_FP32 || mode == 1) {
+    SimtParams p;
+    p.wave = wave; p.tiles = slot->dev; p.n_tiles = n_tiles;
+    p.w32 = b->d_w32; p.dct = b->d_dct; p.out = out;
+    p.n_fft = b->n_fft; p.hop = b->hop; p.n_mels = b->n_mels; p.mp = b->mp;
+    p.n_mfcc = b->n_mfcc; p.n_out = b->n_mfcc ? b->n_mfcc : b->n_mels;
+    p.eps = (float)b->eps; p.mode = mode;
+    const int grid = std::min(n_tiles, b->sm_count * 1);
+    e = launch_simt(p, b->mj, grid, stream);
+  } else {
+    TcLaunch L;
+    L.wave = wave; L.tiles = slot->dev; L.n_tiles = n_tiles; L.out = out;
+    L.dct = b->d_dct; L.n_mfcc = b->n_mfcc; L.eps = (float)b->eps; L.err = b->d_err;
+    L.sm_count = b->sm_count;
+    e = tc_launch(&b->tc, L, stream);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  MELT_CUDA(cudaEventRecord(slot->done, stream));
+  return MELT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+melt_status melt_basis_create(double sr, int n_fft, int hop, int n_mels, double fmin,
+                              double fmax, int window, melt_basis** out) {
+  return melt_basis_create_ex(sr, n_fft, hop, n_mels, fmin, fmax, window, MELT_FP32, 0, 1e-10,
+                              out);
+}
+
+melt_status melt_basis_create_ex(double sr, int n_fft, int hop, int n_mels, double fmin,
+                                 double fmax, int window, int precision, int n_mfcc,
+                                 double eps, melt_basis** out) {
+  if (!out) return MELT_ERR_ARG;
+  *out = nullptr;
+  if (n_mels < 1 || n_mels > 128 || !(sr > 0) || !(fmin >= 0) || !(fmax > fmin) ||
+      !(fmax <= sr / 2))
+    return MELT_ERR_ARG;
+  // M interior points of M+2 points uniform on the Mel scale (Sec. III-A)
+  std::vector<double> f(n_mels);
+  const double lo = hz_to_mel(fmin), hi = hz_to_mel(fmax);
+  for (int m = 0; m < n_mels; ++m) f[m] = mel_to_hz(lo + (hi - lo) * (m + 1) / (n_mels + 1));
+  melt_status st = create_common(sr, n_fft, hop, f.data(), n_mels, fmin, fmax, window, precision,
+                                 n_mfcc, eps, out);
+  return st;
+}
+
+melt_status melt_basis_create_freqs(double sr, int n_fft, int hop, const double* freqs,
+                                    int n_freqs, int window, int precision, int n_mfcc,
+                                    double eps, melt_basis** out) {
+  if (!freqs) return MELT_ERR_ARG;
+  return create_common(sr, n_fft, hop, freqs, n_freqs, 0.0, sr / 2, window, precision, n_mfcc,
+                       eps, out);
+}
+
+int64_t melt_num_frames(const melt_basis* basis, int64_t length) {
+  if (!basis) return 0;
+  return frames_of(basis, length);
+}
+
+int melt_num_outputs(const melt_basis* basis) {
+  if (!basis) return 0;
+  return basis->n_mfcc ? basis->n_mfcc : basis->n_mels;
+}
+
+melt_status melt_basis_info(const melt_basis* b, int* ints, double* doubles) {
+  if (!b) return MELT_ERR_ARG;
+  if (ints) {
+    ints[0] = b->n_fft; ints[1] = b->hop; ints[2] = b->n_mels;
+    ints[3] = b->n_mfcc; ints[4] = b->precision; ints[5] = b->window;
+  }
+  if (doubles) {
+    doubles[0] = b->sr; doubles[1] = b->fmin; doubles[2] = b->fmax; doubles[3] = b->eps;
+  }
+  return MELT_OK;
+}
+
+melt_status melt_basis_get_fp64(const melt_basis* b, double* freqs, double* w) {
+  if (!b) return MELT_ERR_ARG;
+  if (freqs) std::memcpy(freqs, b->freqs.data(), b->freqs.size() * sizeof(double));
+  if (w) std::memcpy(w, b->w64.data(), b->w64.size() * sizeof(double));
+  return MELT_OK;
+}
+
+melt_status melt_forward(melt_basis* basis, const float* wave, const int64_t* offsets,
+                         const int64_t* lengths, int batch, float* out, void* stream) {
+  return forward_impl(basis, wave, offsets, lengths, batch, out, stream, 0);
+}
+
+melt_status melt_forward_components(melt_basis* basis, const float* wave,
+                                    const int64_t* offsets, const int64_t* lengths, int batch,
+                                    float* out, void* stream) {
+  if (basis && basis->precision != MELT_FP32) return MELT_ERR_UNSUPPORTED;
+  return forward_impl(basis, wave, offsets, lengths, batch, out, stream, 1);
+}
+
+melt_status melt_sync(melt_basis* b, void* stream) {
+  if (!b) return MELT_ERR_ARG;
+  MELT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  int err = 0;
+  MELT_CUDA(cudaMemcpy(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    MELT_CUDA(cudaMemset(b->d_err, 0, sizeof(int)));
+    return MELT_ERR_TIMEOUT;
+  }
+  return MELT_OK;
+}
+
+melt_status melt_destroy(melt_basis* b) {
+  if (!b) return MELT_OK;
+  cudaDeviceSynchronize();
+  free_basis(b);
+  return MELT_OK;
+}
+
+const char* melt_status_string(int s) {
+  switch (s) {
+    case MELT_OK: return "ok";
+    case MELT_ERR_ARG: return "invalid argument";
+    case MELT_ERR_CUDA: return "CUDA runtime error";
+    case MELT_ERR_OOM: return "out of memory";
+    case MELT_ERR_UNSUPPORTED: return "unsupported configuration";
+    case MELT_ERR_TIMEOUT: return "kernel wait timed out";
+    case MELT_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+    default: return "unknown status";
+  }
+}
+
+const char* melt_version(void) { return "melt 0.1 sm_103a"; }
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// Internal types shared by the host planner and the kernels of libmelt.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/melt.h"
+
+namespace melt {
+
+// Frames per tile.  Every kernel works on tiles of up to kTileFrames
+// consecutive frames of one clip; 128 is the M extent of one tcgen05 MMA
+// (cta_group::1) and of the SIMT kernel's CTA tile.
+constexpr int kTileFrames = 128;
+
+// One unit of work: up to kTileFrames consecutive frames of one clip.
+struct TileDesc {
+  int64_t in_off;     // float index in `wave` of sample 0 of the tile's first frame
+  int64_t out_row;    // row of the tile's first frame in the packed output
+  int32_t n_frames;   // valid frames in the tile, 1..kTileFrames
+  int32_t n_samples;  // samples of the clip from in_off to the clip end (clamped to int32)
+  int32_t group;      // basis group of the tile (grouped launch); 0 otherwise
+  int32_t clip;       // clip index
+};
+static_assert(sizeof(TileDesc) == 32, "TileDesc is 32 bytes");
+
+// Error bits latched by kernels in the per-basis device error word.
+enum : int { kErrTimeout = 1, kErrBadTile = 2 };
+
+// Parameters of the FP32 SIMT kernel.
+struct SimtParams {
+  const float* wave;
+  const TileDesc* tiles;
+  int n_tiles;
+  const float* w32;   // [n_fft][2*mp]: interleaved (W_r[m][n], W_i[m][n]) per mel, zero-padded to mp mels
+  const float* dct;   // [n_mfcc][n_mels] or nullptr
+  float* out;
+  int n_fft, hop, n_mels, mp, n_mfcc, n_out;
+  float eps;
+  int mode;           // 0: log-Mel / MFCC, 1: raw R|I components
+};
+
+// Launch the FP32 SIMT kernel for `p` (grid picked by the caller).
+cudaError_t launch_simt(const SimtParams& p, int mj, int grid, cudaStream_t stream);
+int simt_smem_bytes(int mj, int n_mels, int n_mfcc);
+
+}  // namespace melt

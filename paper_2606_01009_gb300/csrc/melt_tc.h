@@ -1,0 +1,45 @@
+// Tensor-core (tcgen05 / TMEM) MelT kernels: BF16, split-BF16 and FP8 forms.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "melt_internal.h"
+
+namespace melt {
+
+struct TcConfig {
+  int n_fft, hop, n_mels, precision;
+};
+
+// Device-resident operand images of one basis for the tensor-core kernels.
+struct TcBasis {
+  int precision = 0;
+  int n_fft = 0, hop = 0, n_mels = 0;
+  int J = 0;            // polyphase slices ceil(N / H)
+  int ksteps = 0;       // MMA K-steps over all slices
+  int kstep_k = 0;      // K per MMA instruction (16 for BF16, 32 for FP8)
+  int n_cols = 0;       // UMMA N = 2M rounded up to a multiple of 16
+  size_t kstep_bytes = 0;  // bytes of one K-step block of the B operand
+  void* d_b = nullptr;     // B operand blocks, one per K-step (hi part for BF16x3)
+  void* d_b_lo = nullptr;  // BF16x3: lo part blocks
+  uint32_t* d_kmap = nullptr;  // per K-step: (slice j << 16) | (first sample column r0)
+};
+
+struct TcLaunch {
+  const float* wave;
+  const TileDesc* tiles;
+  int n_tiles;
+  float* out;
+  const float* dct;   // [n_mfcc][n_mels] or nullptr
+  int n_mfcc;
+  float eps;
+  int* err;
+  int sm_count;
+};
+
+melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64);
+void tc_free(TcBasis* tb);
+cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream);
+
+}  // namespace melt

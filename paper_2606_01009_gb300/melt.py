@@ -1,0 +1,236 @@
+"""Thin ctypes binding of libmelt (include/melt.h), same names as the C ABI.
+
+Argument marshalling only: every step of the MelT path runs in libmelt's
+CUDA kernels.  torch is used for device memory and streams.  If libmelt.so
+has not been built, importing this module raises (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmelt.so")
+
+MELT_OK = 0
+MELT_ERR_ARG = -1
+MELT_ERR_CUDA = -2
+MELT_ERR_OOM = -3
+MELT_ERR_UNSUPPORTED = -4
+MELT_ERR_TIMEOUT = -5
+MELT_ERR_NO_DEVICE = -6
+
+MELT_WIN_HANN_PERIODIC = 0
+MELT_WIN_HANN_SYMMETRIC = 1
+
+MELT_FP32 = 0
+MELT_BF16 = 1
+MELT_BF16X3 = 2
+MELT_FP8E4M3 = 3
+PRECISIONS = {"fp32": MELT_FP32, "bf16": MELT_BF16, "bf16x3": MELT_BF16X3, "fp8": MELT_FP8E4M3}
+
+# Every symbol include/melt.h declares, with (restype, argtypes).
+_VP = C.c_void_p
+_I64P = C.POINTER(C.c_int64)
+SIGNATURES = {
+    "melt_basis_create": (C.c_int, [C.c_double, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                    C.c_int, C.POINTER(_VP)]),
+    "melt_basis_create_ex": (C.c_int, [C.c_double, C.c_int, C.c_int, C.c_int, C.c_double,
+                                       C.c_double, C.c_int, C.c_int, C.c_int, C.c_double,
+                                       C.POINTER(_VP)]),
+    "melt_basis_create_freqs": (C.c_int, [C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                          C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                          C.POINTER(_VP)]),
+    "melt_num_frames": (C.c_int64, [_VP, C.c_int64]),
+    "melt_num_outputs": (C.c_int, [_VP]),
+    "melt_basis_info": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "melt_basis_get_fp64": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "melt_forward": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
+    "melt_forward_components": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
+    "melt_sync": (C.c_int, [_VP, _VP]),
+    "melt_destroy": (C.c_int, [_VP]),
+    "melt_status_string": (C.c_char_p, [C.c_int]),
+    "melt_version": (C.c_char_p, []),
+}
+
+
+class MeltError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmelt.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def status_string(status: int) -> str:
+    return lib.melt_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != MELT_OK:
+        raise MeltError(status, what)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _i64(a):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+    return arr, arr.ctypes.data_as(_I64P)
+
+
+# ------------------------------------------------------------------ C names
+def melt_basis_create(sr, n_fft, hop, n_mels, fmin, fmax, window=MELT_WIN_HANN_PERIODIC):
+    h = C.c_void_p()
+    _check(lib.melt_basis_create(sr, n_fft, hop, n_mels, fmin, fmax, window, C.byref(h)),
+           "melt_basis_create")
+    return h
+
+
+def melt_basis_create_ex(sr, n_fft, hop, n_mels, fmin, fmax, window=MELT_WIN_HANN_PERIODIC,
+                         precision=MELT_FP32, n_mfcc=0, eps=1e-10):
+    h = C.c_void_p()
+    _check(lib.melt_basis_create_ex(sr, n_fft, hop, n_mels, fmin, fmax, window, precision, n_mfcc,
+                                    eps, C.byref(h)), "melt_basis_create_ex")
+    return h
+
+
+def melt_basis_create_freqs(sr, n_fft, hop, freqs, window=MELT_WIN_HANN_PERIODIC,
+                            precision=MELT_FP32, n_mfcc=0, eps=1e-10):
+    f = np.ascontiguousarray(np.asarray(freqs, dtype=np.float64))
+    h = C.c_void_p()
+    _check(lib.melt_basis_create_freqs(sr, n_fft, hop, f.ctypes.data_as(C.POINTER(C.c_double)),
+                                       int(f.shape[0]), window, precision, n_mfcc, eps,
+                                       C.byref(h)), "melt_basis_create_freqs")
+    return h
+
+
+def melt_num_frames(basis, length) -> int:
+    return int(lib.melt_num_frames(basis, int(length)))
+
+
+def melt_num_outputs(basis) -> int:
+    return int(lib.melt_num_outputs(basis))
+
+
+def melt_basis_info(basis):
+    ints = (C.c_int * 6)()
+    dbl = (C.c_double * 4)()
+    _check(lib.melt_basis_info(basis, ints, dbl), "melt_basis_info")
+    keys_i = ["n_fft", "hop", "n_mels", "n_mfcc", "precision", "window"]
+    keys_d = ["sr", "fmin", "fmax", "eps"]
+    out = {k: int(v) for k, v in zip(keys_i, ints)}
+    out.update({k: float(v) for k, v in zip(keys_d, dbl)})
+    return out
+
+
+def melt_basis_get_fp64(basis):
+    info = melt_basis_info(basis)
+    M, N = info["n_mels"], info["n_fft"]
+    freqs = np.zeros(M, np.float64)
+    w = np.zeros((2 * M, N), np.float64)
+    _check(lib.melt_basis_get_fp64(basis, freqs.ctypes.data_as(C.POINTER(C.c_double)),
+                                   w.ctypes.data_as(C.POINTER(C.c_double))), "melt_basis_get_fp64")
+    return freqs, w
+
+
+def melt_forward(basis, wave, offsets, lengths, out, stream=None, batch=None):
+    """wave/out: CUDA float32 tensors (or raw device pointers); offsets/lengths: host int64."""
+    lens, lp = _i64(lengths)
+    offs, op = _i64(offsets)
+    b = int(lens.shape[0]) if batch is None else int(batch)
+    wp = wave if isinstance(wave, int) else wave.data_ptr()
+    outp = out if isinstance(out, int) else out.data_ptr()
+    _check(lib.melt_forward(basis, C.c_void_p(wp), op, lp, b, C.c_void_p(outp), _stream_ptr(stream)),
+           "melt_forward")
+
+
+def melt_forward_components(basis, wave, offsets, lengths, out, stream=None):
+    lens, lp = _i64(lengths)
+    offs, op = _i64(offsets)
+    _check(lib.melt_forward_components(basis, C.c_void_p(wave.data_ptr()), op, lp, int(lens.shape[0]),
+                                       C.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+           "melt_forward_components")
+
+
+def melt_sync(basis, stream=None):
+    _check(lib.melt_sync(basis, _stream_ptr(stream)), "melt_sync")
+
+
+def melt_destroy(basis):
+    _check(lib.melt_destroy(basis), "melt_destroy")
+
+
+def melt_status_string(status: int) -> str:
+    return status_string(status)
+
+
+def melt_version() -> str:
+    return lib.melt_version().decode()
+
+
+# ------------------------------------------------------- convenience object
+class Frontend:
+    """Owns one melt_basis; calls melt_forward on torch tensors.
+
+    ``precision`` is one of "fp32", "bf16", "bf16x3", "fp8".
+    """
+
+    def __init__(self, sr=16000.0, n_fft=400, hop=160, n_mels=80, fmin=0.0, fmax=8000.0,
+                 window=MELT_WIN_HANN_PERIODIC, precision="fp32", n_mfcc=0, eps=1e-10, freqs=None):
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if freqs is None:
+            self.handle = melt_basis_create_ex(sr, n_fft, hop, n_mels, fmin, fmax, window, p, n_mfcc, eps)
+        else:
+            self.handle = melt_basis_create_freqs(sr, n_fft, hop, freqs, window, p, n_mfcc, eps)
+        self.n_out = melt_num_outputs(self.handle)
+
+    def num_frames(self, length) -> int:
+        return melt_num_frames(self.handle, length)
+
+    def total_frames(self, lengths) -> int:
+        return sum(self.num_frames(int(L)) for L in lengths)
+
+    def __call__(self, wave, offsets, lengths, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.total_frames(lengths), self.n_out), device=wave.device,
+                              dtype=torch.float32)
+        melt_forward(self.handle, wave, offsets, lengths, out, stream)
+        return out
+
+    def sync(self, stream=None):
+        melt_sync(self.handle, stream)
+
+    def close(self):
+        if self.handle is not None:
+            melt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

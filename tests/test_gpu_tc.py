@@ -1,0 +1,135 @@
+"""Parity of the tcgen05 tensor-core forms (BF16, split-BF16, FP8) with the oracle.
+
+Two comparisons per form:
+* element by element against the oracle evaluated on the same rounded
+  operands (products exact, only the FP32 accumulation may differ), within a
+  bound derived from the sum of |products|;
+* against the exact FP64 oracle: the form's real error in dB, printed and
+  held to a loose ceiling (bins within 60 dB of their frame's maximum).
+"""
+import numpy as np
+import pytest
+
+from oracle import melt_oracle as O
+from paper_2606_01009_gb300 import inputs as G
+from tests.helpers import db_report, fp32_sum_error, gpu_features, oracle_features, rounded_log_bound
+
+pytestmark = pytest.mark.gpu
+
+# accumulation error allowance per sum, relative to the sum of |products|
+ACC_REL = {"bf16": 4 * fp32_sum_error(400), "bf16x3": 4 * fp32_sum_error(1200),
+           "fp8": 4 * fp32_sum_error(416)}
+FORMS = ["bf16", "bf16x3", "fp8"]
+
+
+@pytest.fixture(scope="module")
+def melt():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_01009_gb300 import melt as m
+    return m
+
+
+def _spec(**kw):
+    base = dict(sr=16000.0, n_fft=400, hop=160, n_mels=80, fmin=0.0, fmax=8000.0)
+    base.update(kw)
+    return O.MelTSpec(**base)
+
+
+def _check(melt, prec, clips, n_scale=None, **kw):
+    spec = _spec(**kw)
+    fe = melt.Frontend(precision=prec, **kw)
+    got = gpu_features(fe, clips)
+    ref_r = oracle_features(spec, clips, rounded=prec)
+    assert got.shape == ref_r.shape
+    bound = rounded_log_bound(spec, clips, prec, ACC_REL[prec])
+    bad = np.abs(got - ref_r) > bound
+    assert not bad.any(), (prec, int(bad.sum()), np.argwhere(bad)[:5])
+    exact = oracle_features(spec, clips)
+    rep = db_report(got, exact)
+    # the form's error vs FP64 is the operand rounding's: the oracle predicts it
+    pred = db_report(ref_r, exact)
+    for key in rep:
+        assert rep[key][1] <= pred[key][1] * 1.02 + 2e-3, (key, rep[key], pred[key])
+        assert rep[key][0] <= pred[key][0] + 0.05, (key, rep[key], pred[key])
+    fe.close()
+    return rep
+
+
+@pytest.mark.parametrize("prec", FORMS)
+def test_tones_8x1s(melt, prec):
+    clips, _ = G.workload("tones_8x1s")
+    rep = _check(melt, prec, clips)
+    print(prec, "tones_8x1s vs FP64:", rep)
+
+
+@pytest.mark.parametrize("prec", FORMS)
+def test_ragged_and_multi_tile(melt, prec):
+    lens = [0, 399, 400, 401, 560, 128 * 160 + 240, 129 * 160 + 240, 300 * 160 + 397, 16000, 3]
+    clips = [G.rich_clip(21, i, L) if L >= 16 else np.ones(L, np.float32) for i, L in enumerate(lens)]
+    rep = _check(melt, prec, clips)
+    print(prec, "ragged vs FP64:", rep)
+
+
+@pytest.mark.parametrize("prec", FORMS)
+@pytest.mark.parametrize("n_mels", [128, 13, 40])
+def test_mel_counts(melt, prec, n_mels):
+    clips = [G.rich_clip(31, i, 30000) for i in range(3)]
+    _check(melt, prec, clips, n_mels=n_mels)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_22k_group(melt, prec):
+    clips = [G.rich_clip(41, i, 22050 * 3 + 5, sr=22050.0) for i in range(3)]
+    _check(melt, prec, clips, sr=22050.0, n_fft=1024, hop=256)
+
+
+def test_fp8_22k_reports_unsupported(melt):
+    with pytest.raises(melt.MeltError) as ei:
+        melt.Frontend(sr=22050.0, n_fft=1024, hop=256, precision="fp8")
+    assert ei.value.status == melt.MELT_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", FORMS)
+def test_mfcc(melt, prec):
+    clips = [G.rich_clip(51, i, 25000) for i in range(2)]
+    spec = _spec(n_mfcc=40)
+    fe = melt.Frontend(precision=prec, n_mfcc=40)
+    got = gpu_features(fe, clips)
+    spec_l = _spec()
+    lb = rounded_log_bound(spec_l, clips, prec, ACC_REL[prec])
+    D = O.dct2_ortho(40, 80)
+    logmel_r = oracle_features(spec_l, clips, rounded=prec)
+    ref = logmel_r @ D.T
+    bound = lb @ np.abs(D).T + 82 * 2 ** -24 * (np.abs(logmel_r) @ np.abs(D).T)
+    assert np.all(np.abs(got - ref) <= bound)
+    fe.close()
+
+
+def test_silent_and_tiny_inputs(melt):
+    clips = [np.zeros(3000, np.float32), np.full(1000, 1e-30, np.float32), np.ones(600, np.float32) * 0.5]
+    for prec in FORMS:
+        _check(melt, prec, clips)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", FORMS)
+def test_full_levels_1024x10s_sampled(melt, prec):
+    """The 1024 x 10 s precision-sweep workload in one launch; sampled frames vs the oracle."""
+    clips, sr = G.workload("levels_1024x10s")
+    spec = _spec()
+    fe = melt.Frontend(sr=sr, precision=prec)
+    got = gpu_features(fe, clips)
+    assert got.shape == (1024 * 998, 80)
+    rng = np.random.default_rng(1)
+    idx = rng.choice(1024, 12, replace=False)
+    sub = [clips[b] for b in idx]
+    rows = np.concatenate([np.arange(998) + b * 998 for b in idx])
+    bound = rounded_log_bound(spec, sub, prec, ACC_REL[prec])
+    ref_r = oracle_features(spec, sub, rounded=prec)
+    assert np.all(np.abs(got[rows] - ref_r) <= bound)
+    rep = db_report(got[rows], oracle_features(spec, sub))
+    print(prec, "levels_1024x10s (12 clips) vs FP64:", rep)
+    fe.close()
