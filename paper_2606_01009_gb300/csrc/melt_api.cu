@@ -170,8 +170,9 @@ melt_status create_common(double sr, int n_fft, int hop, const double* freqs, in
   build_fp64(b);
   st = upload_fp32(b);
   if (st == MELT_OK) st = upload_dct(b);
+  if (st == MELT_OK && precision != MELT_FP32 && n_mfcc > tc_max_mfcc()) st = MELT_ERR_UNSUPPORTED;
   if (st == MELT_OK && precision != MELT_FP32) {
-    TcConfig c{n_fft, hop, n_freqs, precision};
+    TcConfig c{n_fft, hop, n_freqs, precision, n_mfcc};
     st = tc_build(&b->tc, c, b->w64.data());
   }
   if (st == MELT_OK) {

@@ -9,7 +9,7 @@
 namespace melt {
 
 struct TcConfig {
-  int n_fft, hop, n_mels, precision;
+  int n_fft, hop, n_mels, precision, n_mfcc;
 };
 
 // Device-resident operand images of one basis for the tensor-core kernels.
@@ -39,6 +39,7 @@ struct TcLaunch {
 };
 
 melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64);
+int tc_max_mfcc();  // largest n_mfcc the tensor-core epilogue supports
 void tc_free(TcBasis* tb);
 cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream);
 
