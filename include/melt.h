@@ -141,6 +141,32 @@ melt_status melt_forward(melt_basis* basis, const float* wave, const int64_t* of
                          const int64_t* lengths, int batch, float* out, void* stream);
 
 /*
+ * melt_forward_noalloc - melt_forward without any allocation at call time.
+ *   The paper has no counterpart: this entry point exists for callers that
+ *   must not allocate device memory once running - a real-time audio thread
+ *   (cudaMalloc can block on driver locks and synchronise the device), a
+ *   process whose device memory is already reserved by another framework's
+ *   caching allocator, or a deployment that fixes its memory footprint at
+ *   start-up.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   Arguments, layouts and results are those of melt_forward.
+ *   Scratch: the per-call tile list lives in one file-scope device array of
+ *     16384 tiles (512 KiB; one tile = up to 128 frames of one clip, so each
+ *     clip needs ceil(T_b / 128) tiles), held by every device that loads the
+ *     library until the process exits.  A batch that needs more tiles is
+ *     rejected with MELT_ERR_ARG before anything is launched.
+ *   The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.  The basis must belong to the current device.
+ *   All calls share the array, which keeps the previous call's descriptors;
+ *     each call rewrites every entry it uses, so nothing needs clearing.
+ *     Calls whose work overlaps on the GPU (different streams without
+ *     ordering) race on the array: order them on one stream, or wait.
+ *   Host-side planning uses a file-scope host array guarded by a mutex.
+ */
+melt_status melt_forward_noalloc(melt_basis* basis, const float* wave, const int64_t* offsets,
+                                 const int64_t* lengths, int batch, float* out, void* stream);
+
+/*
  * melt_forward_components - debug form: the raw projection (Eq. 6) for every
  * frame, out = device float[sum_b T_b * 2M]: per frame M values of R then M of I.
  * Only MELT_FP32 bases.  Arguments otherwise as melt_forward.

@@ -304,6 +304,59 @@ melt_status forward_impl(melt_basis* b, const float* wave, const int64_t* offset
 
 }  // namespace
 
+namespace melt {
+
+long long plan_tiles_into(const melt_basis* b, const int64_t* offsets, const int64_t* lengths,
+                          int batch, TileDesc* dst, long long cap) {
+  long long n = 0;
+  int64_t row = 0, off = 0;
+  for (int c = 0; c < batch; ++c) {
+    const int64_t L = lengths[c];
+    if (L < 0) return -1;
+    const int64_t o = offsets ? offsets[c] : off;
+    if (o < 0 || (o & 3)) return -1;
+    off += (L + 3) & ~int64_t(3);
+    const int64_t T = frames_of(b, L);
+    for (int64_t t0 = 0; t0 < T; t0 += kTileFrames) {
+      if (n >= cap) return -2;
+      TileDesc& d = dst[n++];
+      d.in_off = o + t0 * b->hop;
+      d.out_row = row + t0;
+      d.n_frames = (int32_t)std::min<int64_t>(kTileFrames, T - t0);
+      d.n_samples = (int32_t)std::min<int64_t>(L - t0 * b->hop, INT32_MAX);
+      d.group = 0;
+      d.clip = c;
+    }
+    row += T;
+  }
+  return n;
+}
+
+melt_status launch_forward_tiles(melt_basis* b, const float* wave, const TileDesc* d_tiles,
+                                 int n_tiles, float* out, cudaStream_t stream) {
+  cudaError_t e;
+  if (b->precision == MELT_FP32) {
+    SimtParams p;
+    p.wave = wave; p.tiles = d_tiles; p.n_tiles = n_tiles;
+    p.w32 = b->d_w32; p.dct = b->d_dct; p.out = out;
+    p.n_fft = b->n_fft; p.hop = b->hop; p.n_mels = b->n_mels; p.mp = b->mp;
+    p.n_mfcc = b->n_mfcc; p.n_out = b->n_mfcc ? b->n_mfcc : b->n_mels;
+    p.eps = (float)b->eps; p.mode = 0;
+    e = launch_simt(p, b->mj, std::min(n_tiles, b->sm_count), stream);
+  } else {
+    TcLaunch L;
+    L.wave = wave; L.tiles = d_tiles; L.n_tiles = n_tiles; L.out = out;
+    L.dct = b->d_dct; L.n_mfcc = b->n_mfcc; L.eps = (float)b->eps; L.err = b->d_err;
+    L.sm_count = b->sm_count;
+    e = tc_launch(&b->tc, L, stream);
+  }
+  return cuda_status(e);
+}
+
+int basis_device(const melt_basis* b) { return b->device; }
+
+}  // namespace melt
+
 extern "C" {
 
 melt_status melt_basis_create(double sr, int n_fft, int hop, int n_mels, double fmin,

@@ -47,3 +47,20 @@ cudaError_t launch_simt(const SimtParams& p, int mj, int grid, cudaStream_t stre
 int simt_smem_bytes(int mj, int n_mels, int n_mfcc);
 
 }  // namespace melt
+
+// ---- helpers shared with the allocation-free entry point (melt_noalloc.cu)
+namespace melt {
+
+// Plans the tiles of a batch into dst[0..cap).  Returns the tile count,
+// -1 for an invalid offset/length, -2 if more than `cap` tiles are needed.
+long long plan_tiles_into(const melt_basis* b, const int64_t* offsets, const int64_t* lengths,
+                          int batch, TileDesc* dst, long long cap);
+
+// Launches the basis's forward kernel over `n_tiles` device tile descriptors.
+melt_status launch_forward_tiles(melt_basis* b, const float* wave, const TileDesc* d_tiles,
+                                 int n_tiles, float* out, cudaStream_t stream);
+
+// Device of the basis (the current device when it was created).
+int basis_device(const melt_basis* b);
+
+}  // namespace melt

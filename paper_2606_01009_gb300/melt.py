@@ -49,6 +49,7 @@ SIGNATURES = {
     "melt_basis_get_fp64": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "melt_forward": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
     "melt_forward_components": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
+    "melt_forward_noalloc": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
     "melt_sync": (C.c_int, [_VP, _VP]),
     "melt_destroy": (C.c_int, [_VP]),
     "melt_status_string": (C.c_char_p, [C.c_int]),
@@ -165,6 +166,16 @@ def melt_forward(basis, wave, offsets, lengths, out, stream=None, batch=None):
     outp = out if isinstance(out, int) else out.data_ptr()
     _check(lib.melt_forward(basis, C.c_void_p(wp), op, lp, b, C.c_void_p(outp), _stream_ptr(stream)),
            "melt_forward")
+
+
+def melt_forward_noalloc(basis, wave, offsets, lengths, out, stream=None):
+    """melt_forward with its tile list in a fixed device array: allocates nothing."""
+    lens, lp = _i64(lengths)
+    offs, op = _i64(offsets)
+    wp = wave if isinstance(wave, int) else wave.data_ptr()
+    outp = out if isinstance(out, int) else out.data_ptr()
+    _check(lib.melt_forward_noalloc(basis, C.c_void_p(wp), op, lp, int(lens.shape[0]), C.c_void_p(outp),
+                                    _stream_ptr(stream)), "melt_forward_noalloc")
 
 
 def melt_forward_components(basis, wave, offsets, lengths, out, stream=None):
