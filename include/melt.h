@@ -122,6 +122,44 @@ melt_status melt_basis_info(const melt_basis* basis, int* ints, double* doubles)
 melt_status melt_basis_get_fp64(const melt_basis* basis, double* freqs, double* w);
 
 /*
+ * Layout of the tensor-core pipeline in shared memory (BF16 / BF16X3 / FP8
+ * bases).  The library picks one by default; melt_autotune times the
+ * candidates on a real batch and keeps the fastest.
+ *   basis_resident   1: the whole basis is loaded once per CTA and kept in
+ *                    shared memory; 0: it is streamed from L2 through a ring
+ *   a_buffers        MMA A-operand (frame sample) buffers: 1 or 2
+ *   stage_slots      ring slots for the FP32 sample span (~14 KB each)
+ *   basis_slots      streamed-basis ring slots (ignored when resident)
+ *   ksteps_per_slot  basis K-steps (16 samples each) per streamed slot
+ */
+typedef struct {
+  int basis_resident;
+  int a_buffers;
+  int stage_slots;
+  int basis_slots;
+  int ksteps_per_slot;
+} melt_plan;
+
+/* melt_plan_get - the layout the next forward will use (host struct out).
+ * MELT_ERR_UNSUPPORTED for an FP32 (CUDA-core) basis, which has no layout. */
+melt_status melt_plan_get(const melt_basis* basis, melt_plan* plan);
+
+/* melt_plan_set - force a layout (plan NULL = back to the default choice).
+ * MELT_ERR_UNSUPPORTED if it does not fit in shared memory; the previous
+ * layout is then kept. */
+melt_status melt_plan_set(melt_basis* basis, const melt_plan* plan);
+
+/*
+ * melt_autotune - run melt_forward on the given batch (same arguments, `out`
+ * is overwritten) once per candidate layout, `reps` timed runs each after
+ * one warm-up, keep the fastest and return it in *best (may be NULL).
+ * Synchronises `stream`.  Not for use inside stream capture.
+ */
+melt_status melt_autotune(melt_basis* basis, const float* wave, const int64_t* offsets,
+                          const int64_t* lengths, int batch, float* out, void* stream, int reps,
+                          melt_plan* best);
+
+/*
  * melt_forward - MelT (Eq. 8) or MFCCT (Eq. 9) features of a batch of clips.
  *   wave     device float[]: clip b occupies wave[offsets[b] .. offsets[b]+lengths[b]);
  *            the whole 4-float-aligned span [offsets[b], offsets[b]+round_up(lengths[b],4))

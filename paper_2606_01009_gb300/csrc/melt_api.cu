@@ -431,6 +431,73 @@ melt_status melt_forward_components(melt_basis* basis, const float* wave,
   return forward_impl(basis, wave, offsets, lengths, batch, out, stream, 1);
 }
 
+melt_status melt_plan_get(const melt_basis* b, melt_plan* plan) {
+  if (!b || !plan) return MELT_ERR_ARG;
+  if (b->precision == MELT_FP32) return MELT_ERR_UNSUPPORTED;
+  return tc_current_plan(&b->tc, plan) ? MELT_OK : MELT_ERR_UNSUPPORTED;
+}
+
+melt_status melt_plan_set(melt_basis* b, const melt_plan* plan) {
+  if (!b) return MELT_ERR_ARG;
+  if (b->precision == MELT_FP32) return MELT_ERR_UNSUPPORTED;
+  if (!plan) {
+    b->tc.forced = false;
+    return MELT_OK;
+  }
+  if (!tc_plan_fits(&b->tc, *plan)) return MELT_ERR_UNSUPPORTED;
+  b->tc.plan = *plan;
+  b->tc.forced = true;
+  return MELT_OK;
+}
+
+melt_status melt_autotune(melt_basis* b, const float* wave, const int64_t* offsets,
+                          const int64_t* lengths, int batch, float* out, void* stream_v, int reps,
+                          melt_plan* best) {
+  if (!b || reps < 1) return MELT_ERR_ARG;
+  if (b->precision == MELT_FP32) return MELT_ERR_UNSUPPORTED;
+  cudaStream_t stream = (cudaStream_t)stream_v;
+  melt_plan cands[64];
+  const int n = tc_candidates(&b->tc, cands, 64);
+  if (n < 1) return MELT_ERR_UNSUPPORTED;
+  cudaEvent_t e0, e1;
+  MELT_CUDA(cudaEventCreate(&e0));
+  MELT_CUDA(cudaEventCreate(&e1));
+  const bool had = b->tc.forced;
+  const melt_plan prev = b->tc.plan;
+  float best_ms = 1e30f;
+  int best_i = -1;
+  melt_status st = MELT_OK;
+  for (int i = 0; i < n && st == MELT_OK; ++i) {
+    b->tc.plan = cands[i];
+    b->tc.forced = true;
+    st = melt_forward(b, wave, offsets, lengths, batch, out, stream);  // warm-up
+    if (st != MELT_OK) break;
+    cudaEventRecord(e0, stream);
+    for (int r = 0; r < reps && st == MELT_OK; ++r)
+      st = melt_forward(b, wave, offsets, lengths, batch, out, stream);
+    cudaEventRecord(e1, stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) st = MELT_ERR_CUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (st == MELT_OK && ms < best_ms) {
+      best_ms = ms;
+      best_i = i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == MELT_OK) st = melt_sync(b, stream);
+  if (st != MELT_OK || best_i < 0) {
+    b->tc.forced = had;
+    b->tc.plan = prev;
+    return st != MELT_OK ? st : MELT_ERR_UNSUPPORTED;
+  }
+  b->tc.plan = cands[best_i];
+  b->tc.forced = true;
+  if (best) *best = cands[best_i];
+  return MELT_OK;
+}
+
 melt_status melt_sync(melt_basis* b, void* stream) {
   if (!b) return MELT_ERR_ARG;
   MELT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));

@@ -52,6 +52,10 @@ uint8_t e4m3_bits(double v) {
 }
 
 constexpr uint32_t kSmemLimit = 227 * 1024;
+constexpr int kMaxCands = 512;
+
+bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc);
+int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap);
 
 uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
 
@@ -70,7 +74,6 @@ bool plan_smem(const TcBasis* tb, TcParams& p, int n_mfcc) {
   p.inv_h8 = 8.0f / (float)p.H;
   p.kstep_bytes = (uint32_t)tb->kstep_bytes;
   const int parts = P == MELT_BF16X3 ? 2 : 1;
-  p.bslot_bytes = p.kstep_bytes * parts;
   if (P == MELT_FP8E4M3) {
     p.lbo_a = kF * 16 + 16;                    // 128 rows x 16 B, +16 B spreads banks
     p.a_bytes = p.lbo_a * (uint32_t)(p.KS * 2);
@@ -92,52 +95,93 @@ bool plan_smem(const TcBasis* tb, TcParams& p, int n_mfcc) {
   if (p.CH > max_rows) p.CH = std::max(1, max_rows);
   p.NCHUNK = (p.zrows + p.CH - 1) / p.CH;
   p.st_bytes = row_bytes * p.CH;  // slots back to back: the FP8 form reads the span contiguously
-  // Layout candidates, best first: the whole basis resident in shared memory
-  // (loaded once per CTA), then a streamed basis ring; two A buffers before one.
-  struct Cand { int resident, zb, nb, ns; };
-  std::vector<Cand> cands;
-  for (int ns = 4; ns >= 3; --ns)
-    for (int zb = 2; zb >= 1; --zb) cands.push_back({1, zb, p.KS, ns});
-  for (int zb = 2; zb >= 1; --zb)
-    for (int nb = std::min(p.KS, 24); nb >= 4; --nb) cands.push_back({0, zb, nb, 3});
-  for (int zb = 2; zb >= 1; --zb)
-    for (int nb = 3; nb >= 2; --nb)
-      for (int ns = 3; ns >= 2; --ns) cands.push_back({0, zb, nb, ns});
-  for (const Cand& c : cands) {
-    p.b_resident = c.resident;
-    p.ZB = c.zb;
-    p.NB = c.nb;
-    p.NS = (P == MELT_FP8E4M3) ? p.NCHUNK : c.ns;
-    const Bars B(p.NS, p.ZB, p.NB);
-    uint32_t off = 0;
-    p.off_a = off;
-    off += align_up(p.abuf_bytes * p.ZB, 128);
-    p.off_st = off;
-    off += align_up(p.st_bytes * p.NS, 128);
-    p.off_b = off;
-    off += align_up(p.bslot_bytes * p.NB, 128);
-    p.off_bar = off;
-    off += align_up(8 * B.total, 128);
-    p.off_tab = off;
-    off += align_up(8 * p.KS, 128);
-    p.off_misc = off;
-    off += 128;
-    p.off_scale = off;
-    off += (P == MELT_FP8E4M3) ? kScaleRing * kF * 4 : 0;
-    p.off_rowmax = off;
-    off += (P == MELT_FP8E4M3) ? align_up((2 * p.zrows + kF) * 4, 128) : 0;
-    p.off_dct = off;
-    off += align_up(4 * n_mfcc * p.MP, 128);
-    if (off + 128 <= kSmemLimit) {
-      p.smem_total = off + 128;
-      p.tmem_cols = p.NC <= 32 ? 64 : p.NC <= 64 ? 128 : p.NC <= 128 ? 256 : 512;
-      p.acc_stride = p.tmem_cols / 2;
-      p.idesc = idesc_f32acc(P == MELT_FP8E4M3 ? 0u : 1u, kF, p.NC);
-      p.desc_hi = (128u >> 4) | (1u << 14);  // SBO = 128 B; version bit (descriptor bit 46)
-      return true;
-    }
+  p.step_bytes = p.kstep_bytes * parts;
+  melt_plan cands[kMaxCands];
+  int nc = 0;
+  if (tb->forced) {
+    cands[nc++] = tb->plan;
+  } else {
+    nc = candidate_list(tb, p, cands, kMaxCands);
+  }
+  for (int i = 0; i < nc; ++i) {
+    if (try_layout(tb, p, cands[i], n_mfcc)) return true;
   }
   return false;
+}
+
+}  // namespace
+
+// ---- layouts
+namespace {
+
+bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) {
+  const int P = tb->precision;
+  if (c.a_buffers < 1 || c.a_buffers > 2 || c.stage_slots < 2 || c.stage_slots > 8) return false;
+  if (!c.basis_resident && (c.basis_slots < 2 || c.basis_slots > 32 || c.ksteps_per_slot < 1))
+    return false;
+  p.b_resident = c.basis_resident ? 1 : 0;
+  p.ZB = c.a_buffers;
+  p.kps = p.b_resident ? 1 : std::min(c.ksteps_per_slot, p.KS);
+  p.NB = p.b_resident ? p.KS : c.basis_slots;
+  p.bslot_bytes = p.b_resident ? p.step_bytes : p.step_bytes * p.kps;
+  p.NS = (P == MELT_FP8E4M3) ? p.NCHUNK : c.stage_slots;
+  const Bars B(p.NS, p.ZB, p.NB);
+  uint32_t off = 0;
+  p.off_a = off;
+  off += align_up(p.abuf_bytes * p.ZB, 128);
+  p.off_st = off;
+  off += align_up(p.st_bytes * p.NS, 128);
+  p.off_b = off;
+  off += align_up(p.bslot_bytes * p.NB, 128);
+  p.off_bar = off;
+  off += align_up(8 * B.total, 128);
+  p.off_tab = off;
+  off += align_up(8 * p.KS, 128);
+  p.off_misc = off;
+  off += 128;
+  p.off_scale = off;
+  off += (P == MELT_FP8E4M3) ? kScaleRing * kF * 4 : 0;
+  p.off_rowmax = off;
+  off += (P == MELT_FP8E4M3) ? align_up((2 * p.zrows + kF) * 4, 128) : 0;
+  p.off_dct = off;
+  off += align_up(4 * n_mfcc * p.MP, 128);
+  if (off + 128 > kSmemLimit) return false;
+  p.smem_total = off + 128;
+  p.tmem_cols = p.NC <= 32 ? 64 : p.NC <= 64 ? 128 : p.NC <= 128 ? 256 : 512;
+  p.acc_stride = p.tmem_cols / 2;
+  p.idesc = idesc_f32acc(P == MELT_FP8E4M3 ? 0u : 1u, kF, p.NC);
+  p.desc_hi = (128u >> 4) | (1u << 14);  // SBO = 128 B; version bit (descriptor bit 46)
+  return true;
+}
+
+// Layouts in preference order (whether each fits is checked by try_layout).
+// Measured on the 64 x 30 s workload (N=400, H=160, BF16): a streamed basis
+// with two A buffers and large multi-k-step slots beats a resident basis with
+// one A buffer (50.6 vs 87 us at M=80), because the second A buffer lets the
+// converters fill the next tile while the MMAs of the current one run.  More
+// staging slots come first (they hide the HBM latency of the waveform), then
+// the largest slot that still fits.
+int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap) {
+  (void)tb;
+  int n = 0;
+  auto add = [&](int res, int zb, int ns, int nb, int kps) {
+    if (n < cap) out[n++] = melt_plan{res, zb, ns, nb, kps};
+  };
+  const int sb = (int)std::max(1u, p.step_bytes);
+  const int kps_hi = std::max(1, std::min(p.KS, 49152 / sb));   // <= 48 KB per slot
+  const int kps_lo = std::max(1, std::min(p.KS, 24576 / sb));   // >= 24 KB per slot
+  for (int ns = 4; ns >= 3; --ns)
+    for (int kps = kps_hi; kps >= kps_lo; --kps)
+      for (int nb = 2; nb <= 3; ++nb) add(0, 2, ns, nb, kps);
+  for (int zb = 2; zb >= 1; --zb)
+    for (int ns = 4; ns >= 3; --ns) add(1, zb, ns, p.KS, 1);
+  for (int ns = 4; ns >= 2; --ns)
+    for (int nb = 8; nb >= 2; --nb) add(0, 2, ns, nb, std::max(1, kps_lo / 2));
+  for (int ns = 4; ns >= 2; --ns)
+    for (int nb = 24; nb >= 2; nb -= 2) add(0, 1, ns, nb, 1);
+  for (int ns = 3; ns >= 2; --ns)
+    for (int nb = 3; nb >= 2; --nb) add(0, 2, ns, nb, 1);
+  return n;
 }
 
 }  // namespace
@@ -202,6 +246,7 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
   tb->kstep_k = P == MELT_FP8E4M3 ? 32 : 16;
   tb->n_cols = NC;
   tb->kstep_bytes = kstep_bytes;
+  tb->n_mfcc = c.n_mfcc;
   {
     TcParams probe;
     std::memset(&probe, 0, sizeof(probe));
@@ -222,6 +267,47 @@ void tc_free(TcBasis* tb) {
 }
 
 int tc_max_mfcc() { return kMaxMfccTc; }
+
+int tc_candidates(const TcBasis* tb, melt_plan* out, int cap) {
+  TcBasis probe = *tb;
+  probe.forced = false;
+  TcParams p;
+  std::memset(&p, 0, sizeof(p));
+  if (!plan_smem(&probe, p, tb->n_mfcc)) return 0;  // fills the geometry
+  melt_plan all[kMaxCands];
+  const int n = candidate_list(tb, p, all, kMaxCands);
+  int m = 0;
+  for (int i = 0; i < n && m < cap; ++i) {
+    TcParams q = p;
+    if (try_layout(tb, q, all[i], tb->n_mfcc)) {
+      bool dup = false;  // several candidates collapse to one layout (e.g. kps clipped)
+      for (int j = 0; j < m; ++j)
+        dup |= std::memcmp(&out[j], &all[i], sizeof(melt_plan)) == 0;
+      if (!dup) out[m++] = all[i];
+    }
+  }
+  return m;
+}
+
+bool tc_plan_fits(const TcBasis* tb, const melt_plan& plan) {
+  TcBasis probe = *tb;
+  probe.forced = true;
+  probe.plan = plan;
+  TcParams p;
+  std::memset(&p, 0, sizeof(p));
+  return plan_smem(&probe, p, tb->n_mfcc);
+}
+
+bool tc_current_plan(const TcBasis* tb, melt_plan* out) {
+  if (tb->forced) {
+    *out = tb->plan;
+    return true;
+  }
+  melt_plan c[1];
+  if (tc_candidates(tb, c, 1) < 1) return false;
+  *out = c[0];
+  return true;
+}
 
 cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream) {
   TcParams p;

@@ -23,8 +23,18 @@ struct TcBasis {
   size_t kstep_bytes = 0;  // bytes of one K-step block of the B operand
   void* d_b = nullptr;     // B operand blocks, one per K-step (hi part for BF16x3)
   void* d_b_lo = nullptr;  // BF16x3: lo part blocks
-  uint32_t* d_kmap = nullptr;  // per K-step: (slice j << 16) | (first sample column r0)
+  uint32_t* d_kmap = nullptr;  // unused
+  int n_mfcc = 0;
+  bool forced = false;         // plan below was set explicitly (melt_plan_set / autotune)
+  melt_plan plan = {};         // forced layout
 };
+
+// Candidate layouts that fit shared memory, best-guess first.
+int tc_candidates(const TcBasis* tb, melt_plan* out, int cap);
+// Layout the launch will use (forced one if set, else the first candidate).
+bool tc_current_plan(const TcBasis* tb, melt_plan* out);
+// true if the layout fits shared memory for this basis.
+bool tc_plan_fits(const TcBasis* tb, const melt_plan& plan);
 
 struct TcLaunch {
   const float* wave;

@@ -72,7 +72,7 @@ struct TcParams {
   const float* wave;
   const TileDesc* tiles;
   int n_tiles;
-  const uint8_t* bimg;   // KS blocks of bslot_bytes
+  const uint8_t* bimg;   // KS blocks of step_bytes
   const float* dct;      // [n_mfcc][M] or null
   float* out;
   int* err;
@@ -83,7 +83,9 @@ struct TcParams {
   float inv_h8;          // 1 / (H / 8)
   int n_out, n_mfcc;
   uint32_t kstep_bytes;  // one B part of one K-step
-  uint32_t bslot_bytes;  // one basis slot (BF16X3: hi + lo parts)
+  uint32_t step_bytes;   // one K-step of the basis (BF16X3: hi + lo parts)
+  uint32_t bslot_bytes;  // one basis slot: kps K-steps (resident: one K-step)
+  int kps;               // K-steps per streamed basis slot
   uint32_t lbo_a;        // A operand: bytes between K-adjacent core matrices
   uint32_t a_bytes;      // one A part
   uint32_t abuf_bytes;   // one A buffer (BF16X3: hi + lo parts)
@@ -211,28 +213,30 @@ static __device__ void role_basis_producer(const TcParams& p, uint32_t sbase, co
     // every K-step block once, each to its own slot; consumers never release them
     for (int s = 0; s < p.KS; ++s) {
       const uint32_t full = sbase + p.off_bar + 8 * (B.b_full + s);
-      mbar_arrive_expect_tx(full, p.bslot_bytes);
-      bulk_g2s_hint(sbase + p.off_b + s * p.bslot_bytes, p.bimg + (size_t)s * p.bslot_bytes,
-                    p.bslot_bytes, full, pol);
+      mbar_arrive_expect_tx(full, p.step_bytes);
+      bulk_g2s_hint(sbase + p.off_b + s * p.step_bytes, p.bimg + (size_t)s * p.step_bytes,
+                    p.step_bytes, full, pol);
     }
     for (int s = 0; s < p.KS; ++s) drain_wait(sbase + p.off_bar + 8 * (B.b_full + s), 0, p.err);
     return;
   }
+  // streamed: slots of kps consecutive K-steps (contiguous in the basis image)
   int slot = 0;
   uint32_t phase = 0;
   int issued = 0;
   bool ok = true;
   for (int tile = blockIdx.x; ok && tile < p.n_tiles; tile += gridDim.x) {
-    for (int s = 0; s < p.KS; ++s) {
+    for (int s0 = 0; s0 < p.KS; s0 += p.kps) {
       const uint32_t full = sbase + p.off_bar + 8 * (B.b_full + slot);
       const uint32_t empty = sbase + p.off_bar + 8 * (B.b_empty + slot);
       if (!mbar_wait(empty, phase ^ 1, abort, p.err, kErrTimeout)) {
         ok = false;
         break;
       }
-      mbar_arrive_expect_tx(full, p.bslot_bytes);
-      bulk_g2s_hint(sbase + p.off_b + slot * p.bslot_bytes, p.bimg + (size_t)s * p.bslot_bytes,
-                    p.bslot_bytes, full, pol);
+      const uint32_t bytes = (uint32_t)min(p.kps, p.KS - s0) * p.step_bytes;
+      mbar_arrive_expect_tx(full, bytes);
+      bulk_g2s_hint(sbase + p.off_b + slot * p.bslot_bytes, p.bimg + (size_t)s0 * p.step_bytes,
+                    bytes, full, pol);
       ++issued;
       if (++slot == p.NB) {
         slot = 0;
@@ -305,24 +309,30 @@ __device__ void role_mma(const TcParams& p, uint8_t* gbase, uint32_t sbase, cons
         }
       }
     } else {
-      for (int s = 0; s < p.KS; ++s) {
-        const uint2 t = tab[s];
+      const uint32_t step16 = p.step_bytes >> 4;
+      for (int s0 = 0; s0 < p.KS && ok; s0 += p.kps) {
         if (!mbar_wait(sbase + p.off_bar + 8 * (B.b_full + bslot), bphase, abort, p.err,
                        kErrTimeout)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t blo = b_lo0 + bslot * bslot16;
-        const uint64_t ad = hi | (alo + t.x);
-        const uint64_t bd = hi | blo;
-        if constexpr (PREC == MELT_FP8E4M3) {
-          mma_f8(d, ad, bd, p.idesc, s > 0);
-        } else {
-          mma_f16(d, ad, bd, p.idesc, s > 0);
-          if constexpr (PREC == MELT_BF16X3) {
-            mma_f16(d, ad, hi | (blo + bpart16), p.idesc, 1);
-            mma_f16(d, hi | (alo + t.x + apart16), bd, p.idesc, 1);
+        const uint32_t blo0 = b_lo0 + bslot * bslot16;
+        const int n = min(p.kps, p.KS - s0);
+        for (int u = 0; u < n; ++u) {
+          const int s = s0 + u;
+          const uint2 t = tab[s];
+          const uint32_t blo = blo0 + u * step16;
+          const uint64_t ad = hi | (alo + t.x);
+          const uint64_t bd = hi | blo;
+          if constexpr (PREC == MELT_FP8E4M3) {
+            mma_f8(d, ad, bd, p.idesc, s > 0);
+          } else {
+            mma_f16(d, ad, bd, p.idesc, s > 0);
+            if constexpr (PREC == MELT_BF16X3) {
+              mma_f16(d, ad, hi | (blo + bpart16), p.idesc, 1);
+              mma_f16(d, hi | (alo + t.x + apart16), bd, p.idesc, 1);
+            }
           }
         }
         mma_commit(sbase + p.off_bar + 8 * (B.b_empty + bslot));
@@ -703,7 +713,7 @@ __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_const
   if (warp == kBWarp) {
     uint2* tab = reinterpret_cast<uint2*>(gbase + p.off_tab);
     const uint32_t b_lo0 = ((sbase + p.off_b) >> 4) | (((uint32_t)p.NC * 16 >> 4) << 16);
-    const uint32_t bslot16 = p.bslot_bytes >> 4;
+    const uint32_t bslot16 = p.step_bytes >> 4;
     if constexpr (PREC == MELT_FP8E4M3) {
       for (int s = lane; s < p.KS; s += 32)
         tab[s] = make_uint2((2u * s * p.lbo_a) >> 4, b_lo0 + s * bslot16);

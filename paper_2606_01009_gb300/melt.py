@@ -50,11 +50,23 @@ SIGNATURES = {
     "melt_forward": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
     "melt_forward_components": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
     "melt_forward_noalloc": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
+    "melt_plan_get": (C.c_int, [_VP, _VP]),
+    "melt_plan_set": (C.c_int, [_VP, _VP]),
+    "melt_autotune": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP, C.c_int, _VP]),
     "melt_sync": (C.c_int, [_VP, _VP]),
     "melt_destroy": (C.c_int, [_VP]),
     "melt_status_string": (C.c_char_p, [C.c_int]),
     "melt_version": (C.c_char_p, []),
 }
+
+
+class MeltPlan(C.Structure):
+    """melt_plan: layout of the tensor-core pipeline in shared memory."""
+    _fields_ = [("basis_resident", C.c_int), ("a_buffers", C.c_int), ("stage_slots", C.c_int),
+                ("basis_slots", C.c_int), ("ksteps_per_slot", C.c_int)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
 class MeltError(RuntimeError):
@@ -184,6 +196,31 @@ def melt_forward_components(basis, wave, offsets, lengths, out, stream=None):
     _check(lib.melt_forward_components(basis, C.c_void_p(wave.data_ptr()), op, lp, int(lens.shape[0]),
                                        C.c_void_p(out.data_ptr()), _stream_ptr(stream)),
            "melt_forward_components")
+
+
+def melt_plan_get(basis) -> dict:
+    pl = MeltPlan()
+    _check(lib.melt_plan_get(basis, C.byref(pl)), "melt_plan_get")
+    return pl.as_dict()
+
+
+def melt_plan_set(basis, plan=None):
+    """plan: dict with the melt_plan fields, or None for the default layout."""
+    if plan is None:
+        _check(lib.melt_plan_set(basis, None), "melt_plan_set")
+        return
+    pl = MeltPlan(**{k: int(v) for k, v in plan.items()})
+    _check(lib.melt_plan_set(basis, C.byref(pl)), "melt_plan_set")
+
+
+def melt_autotune(basis, wave, offsets, lengths, out, stream=None, reps=5) -> dict:
+    lens, lp = _i64(lengths)
+    offs, op = _i64(offsets)
+    pl = MeltPlan()
+    _check(lib.melt_autotune(basis, C.c_void_p(wave.data_ptr()), op, lp, int(lens.shape[0]),
+                             C.c_void_p(out.data_ptr()), _stream_ptr(stream), int(reps), C.byref(pl)),
+           "melt_autotune")
+    return pl.as_dict()
 
 
 def melt_sync(basis, stream=None):

@@ -1,0 +1,101 @@
+"""Layout plans of the tensor-core pipeline: melt_plan_get / melt_plan_set / melt_autotune.
+
+A plan changes only where operands sit in shared memory and how they are
+copied there; every plan issues the same MMAs in the same k order into the
+same accumulator, so every plan must give bit-identical output.
+"""
+import numpy as np
+import pytest
+
+from paper_2606_01009_gb300 import inputs as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def melt():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_01009_gb300 import melt as m
+    return m
+
+
+def _plans():
+    out = []
+    for zb in (1, 2):
+        out.append(dict(basis_resident=1, a_buffers=zb, stage_slots=3, basis_slots=0, ksteps_per_slot=1))
+    for ns, nb, kps in [(2, 2, 1), (3, 3, 2), (4, 2, 5), (4, 2, 8), (3, 2, 9), (4, 6, 1), (2, 2, 30)]:
+        out.append(dict(basis_resident=0, a_buffers=2, stage_slots=ns, basis_slots=nb, ksteps_per_slot=kps))
+    out.append(dict(basis_resident=0, a_buffers=1, stage_slots=4, basis_slots=12, ksteps_per_slot=1))
+    return out
+
+
+def _batch():
+    import torch
+    lens = [0, 401, 128 * 160 + 240, 129 * 160 + 240, 48000, 300 * 160 + 397, 160000]
+    clips = [G.rich_clip(77, i, L) if L >= 16 else np.zeros(L, np.float32) for i, L in enumerate(lens)]
+    pk = G.pack_clips(clips)
+    return pk, torch.from_numpy(pk.wave).cuda()
+
+
+@pytest.mark.parametrize("prec,n_mels", [("bf16", 80), ("bf16", 128), ("fp8", 80), ("bf16x3", 40)])
+def test_every_plan_is_bit_identical(melt, prec, n_mels):
+    import torch
+    pk, wave = _batch()
+    fe = melt.Frontend(precision=prec, n_mels=n_mels)
+    T = fe.total_frames(pk.lengths)
+    ref = fe(wave, pk.offsets, pk.lengths).cpu().numpy()
+    fe.sync()
+    default = melt.melt_plan_get(fe.handle)
+    tried = 0
+    for pl in _plans():
+        try:
+            melt.melt_plan_set(fe.handle, pl)
+        except melt.MeltError as e:
+            assert e.status == melt.MELT_ERR_UNSUPPORTED
+            continue
+        got = torch.full((T, fe.n_out), float("nan"), device="cuda")
+        fe(wave, pk.offsets, pk.lengths, out=got)
+        fe.sync()
+        assert np.array_equal(got.cpu().numpy(), ref), (prec, n_mels, pl)
+        tried += 1
+    assert tried >= 2, (prec, n_mels)
+    melt.melt_plan_set(fe.handle, None)
+    assert melt.melt_plan_get(fe.handle) == default
+    fe.close()
+
+
+def test_plan_round_trip_and_rejections(melt):
+    fe = melt.Frontend(precision="bf16")
+    pl = dict(basis_resident=0, a_buffers=2, stage_slots=3, basis_slots=3, ksteps_per_slot=4)
+    melt.melt_plan_set(fe.handle, pl)
+    assert melt.melt_plan_get(fe.handle) == pl
+    for bad in [dict(pl, a_buffers=3), dict(pl, stage_slots=1), dict(pl, basis_slots=1),
+                dict(pl, ksteps_per_slot=0), dict(pl, stage_slots=8, basis_slots=32, ksteps_per_slot=40)]:
+        with pytest.raises(melt.MeltError) as ei:
+            melt.melt_plan_set(fe.handle, bad)
+        assert ei.value.status == melt.MELT_ERR_UNSUPPORTED
+    assert melt.melt_plan_get(fe.handle) == pl      # a rejected plan leaves the current one
+    fe.close()
+    f32 = melt.Frontend(precision="fp32")
+    with pytest.raises(melt.MeltError) as ei:
+        melt.melt_plan_get(f32.handle)
+    assert ei.value.status == melt.MELT_ERR_UNSUPPORTED
+    f32.close()
+
+
+def test_autotune_keeps_output(melt):
+    import torch
+    pk, wave = _batch()
+    fe = melt.Frontend(precision="bf16")
+    T = fe.total_frames(pk.lengths)
+    ref = fe(wave, pk.offsets, pk.lengths).cpu().numpy()
+    out = torch.empty((T, fe.n_out), device="cuda")
+    best = melt.melt_autotune(fe.handle, wave, pk.offsets, pk.lengths, out, reps=2)
+    assert melt.melt_plan_get(fe.handle) == best
+    got = fe(wave, pk.offsets, pk.lengths).cpu().numpy()
+    fe.sync()
+    assert np.array_equal(got, ref)
+    fe.close()
