@@ -45,6 +45,34 @@ WORKLOADS = {
     "tones_8x1s": ("tones_8x1s", 16000.0, 400, 160, 80, 0.0, 8000.0),
 }
 L2_BYTES = 129e6
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+
+
+def kernel_sources_sha256() -> str:
+    """Hash of the CUDA sources and the ABI header: ties an ncu traffic figure to the kernel it measured."""
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2606_01009_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))
+                   + glob.glob(os.path.join(csrc, "*.h")) + [os.path.join(ROOT, "include", "melt.h")])
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(key: str):
+    """DRAM bytes per launch from an ncu capture of this exact kernel source, else None."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh).get(key)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("kernel_sources_sha256") != kernel_sources_sha256():
+        return None   # the kernel changed since the counters were taken
+    return rec["dram_bytes_per_launch"]
 
 
 def parse():
@@ -183,6 +211,7 @@ class Workload:
     def __init__(self, args, dev):
         import torch
         self.clips, self.pk, self.cfg = make_inputs(args)
+        self.name = args.workload
         self.lens = np.ascontiguousarray(self.pk.lengths, dtype=np.int64)
         self.offs = np.ascontiguousarray(self.pk.offsets, dtype=np.int64)
         self.wave_h = torch.from_numpy(self.pk.wave)
@@ -306,8 +335,9 @@ def roofline(cfg, W, r, peaks, peak_kind):
                 "algorithmic_flops_per_launch": flops, "launch_ms": r["launch_ms"]}
     ach = alg_bytes / sec / 1e9
     peak = peaks["hbm_gbs"]
+    key = f"{prec}/{W.name}/n_mels={cfg['n_mels']}/n_out={n_out}"
     out = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-           "traffic": None, "peak_note": f"hbm_gbs of {peak_kind} peaks (copy bandwidth)",
+           "traffic": measured_traffic(key), "traffic_key": key, "peak_note": f"hbm_gbs of {peak_kind} peaks (copy bandwidth)",
            "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": r["launch_ms"],
            "tensor_tflops": flops / sec / 1e12}
     out["tensor_frac_of_bf16_peak"] = out["tensor_tflops"] / peaks.get("bf16_tflops", 1900.0)
