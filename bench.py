@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grouped", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the mixed two-group 4096-clip batch (grouped graph vs per-clip launches)")
     ap.add_argument("--forms", action=argparse.BooleanOptionalAction, default=True,
                     help="also time every other operand form")
     return ap.parse_args()
@@ -455,6 +457,73 @@ def _jsonable(o):
     return str(o)
 
 
+def time_grouped(args, dev, steps=20, warmup=3, per_clip_steps=2):
+    """Mixed-geometry batch of 4096 clips (16 kHz 400/160/80 and 22.05 kHz 1024/256/80, BF16):
+    melt_forward_grouped with a CUDA graph, without, and one melt_forward per clip."""
+    import torch
+    from paper_2606_01009_gb300 import inputs as G
+    from paper_2606_01009_gb300 import melt
+    clips, ids = G.mixed_groups(pool=16)
+    pk = G.pack_clips(clips)
+    fes = [melt.Frontend(sr=sr, n_fft=n, hop=h, n_mels=m, fmin=lo, fmax=hi, precision="bf16")
+           for (sr, n, h, m, lo, hi) in G.MIXED_GROUPS]
+    wave = torch.from_numpy(pk.wave).to(dev)
+    T = sum(fes[g].num_frames(int(L)) for L, g in zip(pk.lengths, ids))
+    out = torch.empty((T, fes[0].n_out), device=dev)
+    stream = torch.cuda.current_stream(dev)
+    frames_per_group = [sum(fes[g].num_frames(int(L)) for L, gg in zip(pk.lengths, ids) if gg == g)
+                        for g in range(2)]
+    in_b = pk.wave.nbytes
+    res = {"workload": f"mixed_4096: 4096 clips, log-uniform 0.5-30 s, alternating 16 kHz 400/160/80 and "
+                       f"22.05 kHz 1024/256/80; {T} frames ({frames_per_group[0]} + {frames_per_group[1]}), "
+                       f"{in_b / 1e9:.2f} GB in, {T * fes[0].n_out * 4 / 1e9:.2f} GB out (> L2)",
+           "precision": "bf16", "frames_per_step": T}
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / k
+
+    for name, graphs in (("grouped_graph", True), ("grouped_direct", False)):
+        gf = melt.GroupedFrontend(fes, graphs=graphs)
+        ms = timed(lambda: gf(wave, pk.offsets, pk.lengths, ids, out=out, stream=stream), steps, warmup)
+        gf.sync(stream)
+        res[name] = {"ms_per_step": ms, "frames_per_s": T / (ms / 1e3)}
+        gf.close()
+    # one melt_forward per clip, rows at the clip's place in the packed output
+    rows = np.concatenate([[0], np.cumsum([fes[g].num_frames(int(L)) for L, g in zip(pk.lengths, ids)])])
+    fwd = melt.lib.melt_forward
+    import ctypes as C
+    sp = C.c_void_p(stream.cuda_stream)
+    calls = []
+    for b in range(len(clips)):
+        if rows[b + 1] == rows[b]:
+            continue
+        L = np.array([pk.lengths[b]], np.int64)
+        calls.append((fes[ids[b]].handle, C.c_void_p(wave.data_ptr() + 4 * int(pk.offsets[b])), L,
+                      C.c_void_p(out.data_ptr() + 4 * fes[0].n_out * int(rows[b]))))
+
+    def per_clip():
+        for h, wp, L, op in calls:
+            st = fwd(h, wp, None, L.ctypes.data_as(C.POINTER(C.c_int64)), 1, op, sp)
+            if st != 0:
+                raise melt.MeltError(st, "melt_forward")
+    ms = timed(per_clip, per_clip_steps, 1)
+    for fe in fes:
+        fe.sync(stream)
+    res["per_clip_launches"] = {"ms_per_step": ms, "frames_per_s": T / (ms / 1e3), "launches": len(calls)}
+    for fe in fes:
+        fe.close()
+    return res
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -475,6 +544,12 @@ def main():
             res["cpu_baseline"] = cpu_oracle_baseline(W.clips, W.cfg, args.mfcc, args.cpu_seconds)
             ok = {k: v for k, v in forms.items() if "error" not in v}
             res["accuracy_db"], res["accuracy_sample"] = accuracy_vs_oracle(W, ok, W.cfg, args.mfcc)
+        if args.grouped:
+            import torch
+            try:
+                res["grouped"] = time_grouped(args, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
+            except Exception as e:  # reported, not fatal: the headline line above stands
+                res["grouped"] = {"error": str(e)}
         print(json.dumps(res, default=_jsonable), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -214,6 +214,55 @@ melt_status melt_forward_components(melt_basis* basis, const float* wave,
                                     int batch, float* out, void* stream);
 
 /*
+ * Grouped launch over several bases (batching across configurations, Sec. V).
+ *
+ * A melt_group holds up to MELT_MAX_GROUPS bases of one device whose outputs
+ * have the same width (melt_num_outputs); their frame geometries, precisions
+ * and layout plans may differ (e.g. 16 kHz 400/160/80 and 22.05 kHz
+ * 1024/256/80).  One call plans a work list of tiles (basis, clip, 128-frame
+ * run), copies it to the device once per batch layout, and runs one
+ * persistent kernel per basis over its part of the list.  Unless disabled,
+ * the launches of a batch layout are captured once into a CUDA graph and
+ * replayed by later calls with the same layout.
+ */
+#define MELT_MAX_GROUPS 16
+#define MELT_GROUP_NO_GRAPH 1   /* melt_group_create flag: launch directly, no graph */
+
+typedef struct melt_group melt_group;
+
+/*
+ * melt_group_create - bundle `n_bases` bases (host array of handles, 1..16,
+ * all created on the current device, equal melt_num_outputs).  The group
+ * does not own the bases: destroy the group first.  `flags`: 0 or
+ * MELT_GROUP_NO_GRAPH.  Returns MELT_ERR_ARG on a bad argument.
+ */
+melt_status melt_group_create(melt_basis* const* bases, int n_bases, int flags, melt_group** out);
+
+/*
+ * melt_forward_grouped - features of a batch whose clips use different bases.
+ *   wave       device float[], clips packed as for melt_forward (16-byte aligned starts)
+ *   offsets    host int64[batch] start of clip b in wave (floats, multiple of 4),
+ *              or NULL for back-to-back packing rounded up to 4 floats
+ *   lengths    host int64[batch] samples of clip b
+ *   basis_of   host int32[batch] index (0..n_bases-1) of the basis of clip b
+ *   out        device float[sum_b T_b * n_out]: the frames of clip b, with
+ *              T_b = floor((L_b - N_g)/H_g) + 1 of its basis g, in batch order
+ * Asynchronous on `stream`.  A batch layout not seen before (same pointers,
+ * offsets, lengths and basis indices) allocates its device work list and,
+ * with graphs, captures a graph; the group caches the last 8 layouts.
+ * Results equal melt_forward on each clip with its own basis, bit for bit.
+ */
+melt_status melt_forward_grouped(melt_group* group, const float* wave, const int64_t* offsets,
+                                 const int64_t* lengths, const int32_t* basis_of, int batch,
+                                 float* out, void* stream);
+
+/* melt_group_sync - melt_sync of every basis of the group; first error wins. */
+melt_status melt_group_sync(melt_group* group, void* stream);
+
+/* melt_group_destroy - free the group's work lists and graphs (NULL is a no-op). */
+melt_status melt_group_destroy(melt_group* group);
+
+/*
  * melt_sync - wait for `stream`, then report (and clear) any error a kernel of
  * this basis latched while running (MELT_ERR_TIMEOUT), else the stream's own
  * CUDA status.

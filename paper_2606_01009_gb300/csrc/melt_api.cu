@@ -306,6 +306,25 @@ melt_status forward_impl(melt_basis* b, const float* wave, const int64_t* offset
 
 namespace melt {
 
+int64_t basis_frames(const melt_basis* b, int64_t len) { return frames_of(b, len); }
+
+long long plan_clip_tiles(const melt_basis* b, int64_t off, int64_t len, int64_t row, int clip,
+                          int group, TileDesc* dst, long long cap) {
+  const int64_t T = frames_of(b, len);
+  long long n = 0;
+  for (int64_t t0 = 0; t0 < T; t0 += kTileFrames) {
+    if (n >= cap) return -2;
+    TileDesc& d = dst[n++];
+    d.in_off = off + t0 * b->hop;
+    d.out_row = row + t0;
+    d.n_frames = (int32_t)std::min<int64_t>(kTileFrames, T - t0);
+    d.n_samples = (int32_t)std::min<int64_t>(len - t0 * b->hop, INT32_MAX);
+    d.group = group;
+    d.clip = clip;
+  }
+  return n;
+}
+
 long long plan_tiles_into(const melt_basis* b, const int64_t* offsets, const int64_t* lengths,
                           int batch, TileDesc* dst, long long cap) {
   long long n = 0;
@@ -316,18 +335,10 @@ long long plan_tiles_into(const melt_basis* b, const int64_t* offsets, const int
     const int64_t o = offsets ? offsets[c] : off;
     if (o < 0 || (o & 3)) return -1;
     off += (L + 3) & ~int64_t(3);
-    const int64_t T = frames_of(b, L);
-    for (int64_t t0 = 0; t0 < T; t0 += kTileFrames) {
-      if (n >= cap) return -2;
-      TileDesc& d = dst[n++];
-      d.in_off = o + t0 * b->hop;
-      d.out_row = row + t0;
-      d.n_frames = (int32_t)std::min<int64_t>(kTileFrames, T - t0);
-      d.n_samples = (int32_t)std::min<int64_t>(L - t0 * b->hop, INT32_MAX);
-      d.group = 0;
-      d.clip = c;
-    }
-    row += T;
+    const long long k = plan_clip_tiles(b, o, L, row, c, 0, dst + n, cap - n);
+    if (k < 0) return k;
+    n += k;
+    row += frames_of(b, L);
   }
   return n;
 }

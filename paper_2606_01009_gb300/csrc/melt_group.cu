@@ -1,0 +1,260 @@
+// Grouped launch: one batch whose clips use different bases (Sec. V batches
+// many clips per call; here the batch may also mix frame geometries).
+//
+// A call plans one work list of tiles (basis, clip, 128-frame run), grouped
+// by basis so that each basis's tiles are contiguous, and runs one persistent
+// kernel per basis over its range.  Output rows follow the batch order of the
+// clips, whatever basis each clip uses, so the result equals melt_forward on
+// each clip with its own basis.  The work list of a batch layout is copied to
+// the device once and kept; with graphs enabled the per-basis launches are
+// captured once into a CUDA graph and later calls with the same layout replay
+// it with a single cudaGraphLaunch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "melt_internal.h"
+
+using namespace melt;
+
+namespace {
+
+constexpr int kCacheEntries = 8;
+
+struct GroupEntry {
+  // batch layout (cache key)
+  const float* wave = nullptr;
+  float* out = nullptr;
+  int batch = 0;
+  bool has_offsets = false;
+  std::vector<int64_t> offsets, lengths;
+  std::vector<int32_t> ids;
+  // device work list and launches
+  TileDesc* d_tiles = nullptr;
+  std::vector<long long> first, count;  // per basis: range in d_tiles
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;           // recorded after the last launch that read d_tiles
+  unsigned long long last_use = 0;
+};
+
+void free_entry(GroupEntry* e) {
+  if (!e) return;
+  if (e->done) cudaEventSynchronize(e->done);
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  if (e->d_tiles) cudaFree(e->d_tiles);
+  if (e->done) cudaEventDestroy(e->done);
+  delete e;
+}
+
+}  // namespace
+
+struct melt_group {
+  int device = 0;
+  int flags = 0;
+  std::vector<melt_basis*> bases;
+  std::vector<GroupEntry*> cache;
+  unsigned long long tick = 0;
+  cudaStream_t capture = nullptr;  // private stream the graphs are captured on
+  std::vector<TileDesc> host;      // planning scratch
+  std::vector<int64_t> rows;       // planning scratch: first output row of each clip
+};
+
+namespace {
+
+bool same_layout(const GroupEntry* e, const float* wave, const int64_t* offsets,
+                 const int64_t* lengths, const int32_t* ids, int batch, const float* out) {
+  if (e->wave != wave || e->out != out || e->batch != batch) return false;
+  if (e->has_offsets != (offsets != nullptr)) return false;
+  if (std::memcmp(e->lengths.data(), lengths, sizeof(int64_t) * batch) != 0) return false;
+  if (std::memcmp(e->ids.data(), ids, sizeof(int32_t) * batch) != 0) return false;
+  return !offsets || std::memcmp(e->offsets.data(), offsets, sizeof(int64_t) * batch) == 0;
+}
+
+melt_status launch_all(melt_group* g, const GroupEntry* e, cudaStream_t stream) {
+  for (size_t k = 0; k < g->bases.size(); ++k) {
+    if (e->count[k] == 0) continue;
+    const melt_status st = launch_forward_tiles(g->bases[k], e->wave, e->d_tiles + e->first[k],
+                                                (int)e->count[k], e->out, stream);
+    if (st != MELT_OK) return st;
+  }
+  return MELT_OK;
+}
+
+// Plan, upload and (optionally) capture a new batch layout.
+melt_status make_entry(melt_group* g, const float* wave, const int64_t* offsets,
+                       const int64_t* lengths, const int32_t* ids, int batch, float* out,
+                       cudaStream_t stream, GroupEntry** out_entry) {
+  const int nb = (int)g->bases.size();
+  // output rows in batch order; validate every clip first
+  g->rows.resize(batch);
+  int64_t row = 0, off = 0;
+  std::vector<int64_t> offs(batch);
+  for (int c = 0; c < batch; ++c) {
+    const int64_t L = lengths[c];
+    const int32_t k = ids[c];
+    if (L < 0 || k < 0 || k >= nb) return MELT_ERR_ARG;
+    const int64_t o = offsets ? offsets[c] : off;
+    if (o < 0 || (o & 3)) return MELT_ERR_ARG;
+    off += (L + 3) & ~int64_t(3);
+    offs[c] = o;
+    g->rows[c] = row;
+    row += basis_frames(g->bases[k], L);
+  }
+  GroupEntry* e = new (std::nothrow) GroupEntry;
+  if (!e) return MELT_ERR_OOM;
+  e->first.assign(nb, 0);
+  e->count.assign(nb, 0);
+  g->host.clear();
+  for (int k = 0; k < nb; ++k) {
+    e->first[k] = (long long)g->host.size();
+    for (int c = 0; c < batch; ++c) {
+      if (ids[c] != k) continue;
+      const int64_t T = basis_frames(g->bases[k], lengths[c]);
+      const size_t at = g->host.size();
+      g->host.resize(at + (size_t)((T + kTileFrames - 1) / kTileFrames));
+      const long long n = plan_clip_tiles(g->bases[k], offs[c], lengths[c], g->rows[c], c, k,
+                                          g->host.data() + at, (long long)(g->host.size() - at));
+      if (n < 0) {
+        delete e;
+        return MELT_ERR_ARG;
+      }
+    }
+    e->count[k] = (long long)g->host.size() - e->first[k];
+    if (e->count[k] > 0x7fffffffLL) {
+      delete e;
+      return MELT_ERR_ARG;
+    }
+  }
+  e->wave = wave;
+  e->out = out;
+  e->batch = batch;
+  e->has_offsets = offsets != nullptr;
+  if (offsets) e->offsets.assign(offsets, offsets + batch);
+  e->lengths.assign(lengths, lengths + batch);
+  e->ids.assign(ids, ids + batch);
+  melt_status st = MELT_OK;
+  if (cudaEventCreateWithFlags(&e->done, cudaEventDisableTiming) != cudaSuccess) st = MELT_ERR_CUDA;
+  const size_t bytes = std::max<size_t>(g->host.size(), 1) * sizeof(TileDesc);
+  if (st == MELT_OK && cudaMalloc(&e->d_tiles, bytes) != cudaSuccess) st = MELT_ERR_OOM;
+  // pageable source: the call returns once the bytes are staged, so g->host may be reused
+  if (st == MELT_OK && !g->host.empty() &&
+      cudaMemcpyAsync(e->d_tiles, g->host.data(), g->host.size() * sizeof(TileDesc),
+                      cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    st = MELT_ERR_CUDA;
+  if (st == MELT_OK && !(g->flags & MELT_GROUP_NO_GRAPH) && !g->host.empty()) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      st = MELT_ERR_CUDA;
+    } else {
+      const melt_status ls = launch_all(g, e, g->capture);
+      const cudaError_t ce = cudaStreamEndCapture(g->capture, &graph);
+      if (ls != MELT_OK) st = ls;
+      else if (ce != cudaSuccess || !graph) st = MELT_ERR_CUDA;
+      if (st == MELT_OK && cudaGraphInstantiate(&e->exec, graph, 0) != cudaSuccess) {
+        e->exec = nullptr;
+        st = MELT_ERR_CUDA;
+      }
+      if (graph) cudaGraphDestroy(graph);
+    }
+  }
+  if (st != MELT_OK) {
+    cudaStreamSynchronize(stream);  // the upload may still be reading nothing of ours, but be safe
+    free_entry(e);
+    return st;
+  }
+  // insert, evicting the least recently used layout
+  if ((int)g->cache.size() >= kCacheEntries) {
+    auto lru = std::min_element(g->cache.begin(), g->cache.end(),
+                                [](const GroupEntry* a, const GroupEntry* b) {
+                                  return a->last_use < b->last_use;
+                                });
+    free_entry(*lru);
+    g->cache.erase(lru);
+  }
+  g->cache.push_back(e);
+  *out_entry = e;
+  return MELT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+melt_status melt_group_create(melt_basis* const* bases, int n_bases, int flags, melt_group** out) {
+  if (!out || !bases || n_bases < 1 || n_bases > MELT_MAX_GROUPS) return MELT_ERR_ARG;
+  if (flags & ~MELT_GROUP_NO_GRAPH) return MELT_ERR_ARG;
+  *out = nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MELT_ERR_CUDA;
+  for (int k = 0; k < n_bases; ++k) {
+    if (!bases[k] || basis_device(bases[k]) != dev) return MELT_ERR_ARG;
+    if (melt_num_outputs(bases[k]) != melt_num_outputs(bases[0])) return MELT_ERR_ARG;
+  }
+  melt_group* g = new (std::nothrow) melt_group;
+  if (!g) return MELT_ERR_OOM;
+  g->device = dev;
+  g->flags = flags;
+  g->bases.assign(bases, bases + n_bases);
+  if (cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking) != cudaSuccess) {
+    delete g;
+    return MELT_ERR_CUDA;
+  }
+  *out = g;
+  return MELT_OK;
+}
+
+melt_status melt_forward_grouped(melt_group* g, const float* wave, const int64_t* offsets,
+                                 const int64_t* lengths, const int32_t* basis_of, int batch,
+                                 float* out, void* stream_v) {
+  if (!g || batch < 0 || (batch > 0 && (!lengths || !basis_of || !wave || !out)))
+    return MELT_ERR_ARG;
+  if (((uintptr_t)wave & 15) || ((uintptr_t)out & 15)) return MELT_ERR_ARG;
+  if (batch == 0) return MELT_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MELT_ERR_CUDA;
+  if (dev != g->device) return MELT_ERR_ARG;
+  cudaStream_t stream = (cudaStream_t)stream_v;
+  GroupEntry* e = nullptr;
+  for (GroupEntry* c : g->cache)
+    if (same_layout(c, wave, offsets, lengths, basis_of, batch, out)) {
+      e = c;
+      break;
+    }
+  if (!e) {
+    const melt_status st = make_entry(g, wave, offsets, lengths, basis_of, batch, out, stream, &e);
+    if (st != MELT_OK) return st;
+  }
+  e->last_use = ++g->tick;
+  melt_status st = MELT_OK;
+  if (e->exec) {
+    if (cudaGraphLaunch(e->exec, stream) != cudaSuccess) st = MELT_ERR_CUDA;
+  } else {
+    st = launch_all(g, e, stream);
+  }
+  if (st != MELT_OK) return st;
+  if (cudaEventRecord(e->done, stream) != cudaSuccess) return MELT_ERR_CUDA;
+  return MELT_OK;
+}
+
+melt_status melt_group_sync(melt_group* g, void* stream) {
+  if (!g) return MELT_ERR_ARG;
+  melt_status first = MELT_OK;
+  for (melt_basis* b : g->bases) {
+    const melt_status st = melt_sync(b, stream);
+    if (first == MELT_OK) first = st;
+  }
+  return first;
+}
+
+melt_status melt_group_destroy(melt_group* g) {
+  if (!g) return MELT_OK;
+  for (GroupEntry* e : g->cache) free_entry(e);
+  if (g->capture) cudaStreamDestroy(g->capture);
+  delete g;
+  return MELT_OK;
+}
+
+}  // extern "C"

@@ -60,6 +60,14 @@ long long plan_tiles_into(const melt_basis* b, const int64_t* offsets, const int
 melt_status launch_forward_tiles(melt_basis* b, const float* wave, const TileDesc* d_tiles,
                                  int n_tiles, float* out, cudaStream_t stream);
 
+// Frames of a clip of `len` samples under basis b: floor((len - N)/H) + 1, 0 if len < N.
+int64_t basis_frames(const melt_basis* b, int64_t len);
+
+// Tiles of one clip (samples from float index `off`, output rows from `row`)
+// into dst[0..cap).  Returns the tile count, -2 if more than `cap` are needed.
+long long plan_clip_tiles(const melt_basis* b, int64_t off, int64_t len, int64_t row, int clip,
+                          int group, TileDesc* dst, long long cap);
+
 // Device of the basis (the current device when it was created).
 int basis_device(const melt_basis* b);
 

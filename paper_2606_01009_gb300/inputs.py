@@ -38,6 +38,8 @@ __all__ = [
     "pack_clips",
     "PackedBatch",
     "workload",
+    "mixed_groups",
+    "MIXED_GROUPS",
     "xavier_uniform",
     "batch_order",
 ]
@@ -199,6 +201,44 @@ def workload(name: str, seed: int = 1234, clips: int | None = None, first: int =
         return [rich_clip(seed, first + i, 160000, level_dbfs=float(lv[(first + i) % 1024]))
                 for i in range(n)], 16000.0
     raise ValueError(f"unknown workload {name!r}")
+
+
+# Two basis groups of the mixed-geometry workload: (sr, n_fft, hop, n_mels, fmin, fmax).
+MIXED_GROUPS = ((16000.0, 400, 160, 80, 0.0, 8000.0), (22050.0, 1024, 256, 80, 0.0, 8000.0))
+
+
+def mixed_groups(seed: int = 1234, count: int = 4096, first: int = 0, n: int | None = None,
+                 pool: int = 0):
+    """Mixed-geometry batch: ``count`` clips with durations log-uniform in
+    0.5-30 s (mean about 7.2 s); clip i belongs to group i % 2 of
+    ``MIXED_GROUPS`` and is drawn at that group's sample rate.
+
+    ``pool`` > 0 cuts each clip out of one of ``pool`` 30 s clips per group
+    (at a seeded offset) instead of synthesising it: same lengths, much faster
+    for the full 4096-clip batch.  Returns (clips, group ids) for clips
+    ``first .. first+n-1``.
+    """
+    n = count - first if n is None else n
+    d = np.exp(rng_for(seed, _STREAM_LEN, 1).uniform(math.log(0.5), math.log(30.0), count))
+    starts = rng_for(seed, _STREAM_LEN, 2).uniform(0.0, 1.0, count)
+    pools = {}
+    clips, ids = [], []
+    for i in range(first, first + n):
+        gid = i % 2
+        sr = MIXED_GROUPS[gid][0]
+        L = max(16, int(round(d[i] * sr)))
+        if pool > 0:
+            key = (gid, (i // 2) % pool)
+            if key not in pools:
+                pools[key] = rich_clip(seed, 200000 + 1000 * gid + key[1], int(30 * sr), sr=sr)
+            src = pools[key]
+            L = min(L, src.shape[0])
+            s0 = int(starts[i] * (src.shape[0] - L))
+            clips.append(src[s0:s0 + L].copy())
+        else:
+            clips.append(rich_clip(seed, 100000 + i, L, sr=sr))
+        ids.append(gid)
+    return clips, np.asarray(ids, dtype=np.int32)
 
 
 def xavier_uniform(seed: int, fan_out: int, fan_in: int, tag: int = 0) -> np.ndarray:

@@ -25,6 +25,9 @@ MELT_ERR_NO_DEVICE = -6
 MELT_WIN_HANN_PERIODIC = 0
 MELT_WIN_HANN_SYMMETRIC = 1
 
+MELT_MAX_GROUPS = 16
+MELT_GROUP_NO_GRAPH = 1
+
 MELT_FP32 = 0
 MELT_BF16 = 1
 MELT_BF16X3 = 2
@@ -53,6 +56,10 @@ SIGNATURES = {
     "melt_plan_get": (C.c_int, [_VP, _VP]),
     "melt_plan_set": (C.c_int, [_VP, _VP]),
     "melt_autotune": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP, C.c_int, _VP]),
+    "melt_group_create": (C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, C.POINTER(_VP)]),
+    "melt_forward_grouped": (C.c_int, [_VP, _VP, _I64P, _I64P, C.POINTER(C.c_int32), C.c_int, _VP, _VP]),
+    "melt_group_sync": (C.c_int, [_VP, _VP]),
+    "melt_group_destroy": (C.c_int, [_VP]),
     "melt_sync": (C.c_int, [_VP, _VP]),
     "melt_destroy": (C.c_int, [_VP]),
     "melt_status_string": (C.c_char_p, [C.c_int]),
@@ -223,6 +230,36 @@ def melt_autotune(basis, wave, offsets, lengths, out, stream=None, reps=5) -> di
     return pl.as_dict()
 
 
+def melt_group_create(bases, flags=0):
+    """bases: sequence of basis handles (or Frontends)."""
+    hs = [b.handle if hasattr(b, "handle") else b for b in bases]
+    arr = (_VP * len(hs))(*[h.value if isinstance(h, C.c_void_p) else h for h in hs])
+    g = C.c_void_p()
+    _check(lib.melt_group_create(arr, len(hs), int(flags), C.byref(g)), "melt_group_create")
+    return g
+
+
+def melt_forward_grouped(group, wave, offsets, lengths, basis_of, out, stream=None):
+    lens, lp = _i64(lengths)
+    offs, op = _i64(offsets)
+    ids = np.ascontiguousarray(np.asarray(basis_of, dtype=np.int32))
+    if ids.shape[0] != lens.shape[0]:
+        raise ValueError("basis_of and lengths differ in length")
+    wp = wave if isinstance(wave, int) else wave.data_ptr()
+    outp = out if isinstance(out, int) else out.data_ptr()
+    _check(lib.melt_forward_grouped(group, C.c_void_p(wp), op, lp, ids.ctypes.data_as(C.POINTER(C.c_int32)),
+                                    int(lens.shape[0]), C.c_void_p(outp), _stream_ptr(stream)),
+           "melt_forward_grouped")
+
+
+def melt_group_sync(group, stream=None):
+    _check(lib.melt_group_sync(group, _stream_ptr(stream)), "melt_group_sync")
+
+
+def melt_group_destroy(group):
+    _check(lib.melt_group_destroy(group), "melt_group_destroy")
+
+
 def melt_sync(basis, stream=None):
     _check(lib.melt_sync(basis, _stream_ptr(stream)), "melt_sync")
 
@@ -275,6 +312,40 @@ class Frontend:
     def close(self):
         if self.handle is not None:
             melt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GroupedFrontend:
+    """Owns one melt_group over several Frontends (which must outlive it)."""
+
+    def __init__(self, frontends, graphs=True):
+        self.frontends = list(frontends)
+        self.n_out = self.frontends[0].n_out
+        self.handle = melt_group_create(self.frontends, 0 if graphs else MELT_GROUP_NO_GRAPH)
+
+    def total_frames(self, lengths, basis_of):
+        return sum(self.frontends[int(g)].num_frames(int(L)) for L, g in zip(lengths, basis_of))
+
+    def __call__(self, wave, offsets, lengths, basis_of, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.total_frames(lengths, basis_of), self.n_out), device=wave.device,
+                              dtype=torch.float32)
+        melt_forward_grouped(self.handle, wave, offsets, lengths, basis_of, out, stream)
+        return out
+
+    def sync(self, stream=None):
+        melt_group_sync(self.handle, stream)
+
+    def close(self):
+        if self.handle is not None:
+            melt_group_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
