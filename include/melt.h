@@ -263,6 +263,82 @@ melt_status melt_group_sync(melt_group* group, void* stream);
 melt_status melt_group_destroy(melt_group* group);
 
 /*
+ * Learned per-frame correction (a residual MLP on the log-Mel bands) and its
+ * training.  The paper does not evaluate one: Sec. VI-C names a calibration
+ * layer as untested, and Sec. IV-H / Sec. V describe the MelT-to-STFT+Mel gap
+ * as mostly a per-band affine map.  The model, for a frame x of M log-Mel
+ * values:
+ *   xh = (x - mu) / sd                        fixed per-band statistics
+ *   y  = x + W2 GELU(W1 xh + b1) + b2         W1 [Hd x M], W2 [M x Hd], exact-erf GELU
+ * trained on MSE = mean over rows and bands of (y - target)^2 with AdamW
+ * (decoupled weight decay on every parameter).  All arithmetic is FP32.
+ *
+ * Parameters are one packed FP32 vector, row-major blocks in this order:
+ *   W1 [Hd][M], b1 [Hd], W2 [M][Hd], b2 [M]   (melt_mlp_num_params floats)
+ * Matrices X, target, Y are device float [rows][M], row-major.
+ */
+typedef struct melt_mlp melt_mlp;
+
+/* Number of floats of the packed parameter vector (0 for bad sizes). */
+int64_t melt_mlp_num_params(int n_in, int n_hidden);
+
+/*
+ * melt_mlp_create - upload initial parameters (host, packed as above) and the
+ * per-band statistics mu, sd (host float[n_in]; NULL = 0 and 1) to the current
+ * device.  n_in = M in 1..128; n_hidden = Hd, a multiple of 64 in 64..4096.
+ * AdamW defaults: lr 1e-3, betas (0.9, 0.999), eps 1e-8, weight decay 0.01.
+ */
+melt_status melt_mlp_create(int n_in, int n_hidden, const float* params, const float* mu,
+                            const float* sd, melt_mlp** out);
+
+/* Set mu, sd to the population mean and standard deviation (floor 1e-6) of
+ * the n rows of X (device).  Asynchronous on `stream`. */
+melt_status melt_mlp_fit_stats(melt_mlp* mlp, const float* X, int64_t n, void* stream);
+
+/* AdamW hyper-parameters for later steps (lr >= 0, 0 <= betas < 1, eps > 0, wd >= 0). */
+melt_status melt_mlp_set_adamw(melt_mlp* mlp, double lr, double beta1, double beta2, double eps,
+                               double wd);
+
+/*
+ * melt_mlp_grad - loss gradient over one batch, without updating anything.
+ *   X, target  device float[*][M]
+ *   rows       device int64[batch]: the batch is rows[0..batch) of X/target;
+ *              NULL = rows 0..batch-1
+ *   grads      device float[num_params] (packed like the parameters), or NULL
+ *              for the internal buffer
+ *   loss       device float accumulator: the sum of squared errors over the
+ *              batch is ADDED to *loss (divide by batch*M for the MSE), or NULL
+ * Asynchronous on `stream`; the workspace grows to the largest batch seen.
+ */
+melt_status melt_mlp_grad(melt_mlp* mlp, const float* X, const float* target, const int64_t* rows,
+                          int batch, float* grads, float* loss, void* stream);
+
+/* melt_mlp_train_step - melt_mlp_grad, then one AdamW update (step count += 1). */
+melt_status melt_mlp_train_step(melt_mlp* mlp, const float* X, const float* target,
+                                const int64_t* rows, int batch, float* loss, void* stream);
+
+/* melt_mlp_adamw_apply - one AdamW update with caller gradients (device, packed). */
+melt_status melt_mlp_adamw_apply(melt_mlp* mlp, const float* grads, void* stream);
+
+/* melt_mlp_forward - y = x + W2 GELU(W1 xh + b1) + b2 for n rows; Y == X allowed. */
+melt_status melt_mlp_forward(const melt_mlp* mlp, const float* X, float* Y, int64_t n, void* stream);
+
+/* Copy parameters, mu and sd to host buffers (any may be NULL).  Synchronises the device. */
+melt_status melt_mlp_get_params(const melt_mlp* mlp, float* params, float* mu, float* sd);
+
+/* Free the MLP (NULL is a no-op).  Detach it from every basis first.  Synchronises the device. */
+melt_status melt_mlp_destroy(melt_mlp* mlp);
+
+/*
+ * melt_basis_set_correction - apply `mlp` in place to the output of every
+ * later melt_forward / melt_forward_noalloc of this log-Mel basis (NULL
+ * detaches).  The basis does not own the MLP.  MELT_ERR_UNSUPPORTED for an
+ * MFCC basis; MELT_ERR_ARG if the MLP's band count or device differ.
+ * melt_forward_grouped refuses bases with a correction (MELT_ERR_UNSUPPORTED).
+ */
+melt_status melt_basis_set_correction(melt_basis* basis, const melt_mlp* mlp);
+
+/*
  * melt_sync - wait for `stream`, then report (and clear) any error a kernel of
  * this basis latched while running (MELT_ERR_TIMEOUT), else the stream's own
  * CUDA status.

@@ -37,6 +37,7 @@ struct Staging {
   // batch layout the tiles were planned for (plan cache key)
   int key_batch = -1;
   std::vector<int64_t> key_offsets, key_lengths;
+  int64_t rows = 0;            // output rows of the batch
 };
 
 }  // namespace
@@ -57,6 +58,8 @@ struct melt_basis {
   Staging staging[kStagingSlots];
   int next_slot = 0;
   std::vector<TileDesc> plan;  // host scratch for planning
+  int64_t plan_rows = 0;       // output rows of the planned batch
+  const melt_mlp* correction = nullptr;  // applied in place after the log-Mel (not owned)
 };
 
 namespace {
@@ -218,6 +221,7 @@ melt_status plan_tiles(melt_basis* b, const int64_t* offsets, const int64_t* len
     }
     row += T;
   }
+  b->plan_rows = row;
   return MELT_OK;
 }
 
@@ -256,6 +260,7 @@ melt_status stage_plan(melt_basis* b, const int64_t* offsets, const int64_t* len
   MELT_CUDA(cudaMemcpyAsync(s.dev, s.host, b->plan.size() * sizeof(TileDesc),
                             cudaMemcpyHostToDevice, stream));
   s.n = b->plan.size();
+  s.rows = b->plan_rows;
   s.key_batch = batch;
   s.key_lengths.assign(lengths, lengths + batch);
   if (offsets) s.key_offsets.assign(offsets, offsets + batch); else s.key_offsets.clear();
@@ -298,6 +303,10 @@ melt_status forward_impl(melt_basis* b, const float* wave, const int64_t* offset
     e = tc_launch(&b->tc, L, stream);
   }
   if (e != cudaSuccess) return cuda_status(e);
+  if (b->correction && mode == 0) {
+    const melt_status st = mlp_apply(b->correction, out, out, slot->rows, stream);
+    if (st != MELT_OK) return st;
+  }
   MELT_CUDA(cudaEventRecord(slot->done, stream));
   return MELT_OK;
 }
@@ -365,6 +374,8 @@ melt_status launch_forward_tiles(melt_basis* b, const float* wave, const TileDes
 }
 
 int basis_device(const melt_basis* b) { return b->device; }
+
+const melt_mlp* basis_correction(const melt_basis* b) { return b->correction; }
 
 }  // namespace melt
 
@@ -506,6 +517,16 @@ melt_status melt_autotune(melt_basis* b, const float* wave, const int64_t* offse
   b->tc.plan = cands[best_i];
   b->tc.forced = true;
   if (best) *best = cands[best_i];
+  return MELT_OK;
+}
+
+melt_status melt_basis_set_correction(melt_basis* b, const melt_mlp* mlp) {
+  if (!b) return MELT_ERR_ARG;
+  if (mlp) {
+    if (b->n_mfcc != 0) return MELT_ERR_UNSUPPORTED;  // the correction acts on log-Mel bands
+    if (mlp_inputs(mlp) != b->n_mels || mlp_device(mlp) != b->device) return MELT_ERR_ARG;
+  }
+  b->correction = mlp;
   return MELT_OK;
 }
 

@@ -216,6 +216,8 @@ melt_status melt_forward_grouped(melt_group* g, const float* wave, const int64_t
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MELT_ERR_CUDA;
   if (dev != g->device) return MELT_ERR_ARG;
+  for (melt_basis* b : g->bases)
+    if (basis_correction(b)) return MELT_ERR_UNSUPPORTED;  // corrections act on contiguous rows
   cudaStream_t stream = (cudaStream_t)stream_v;
   GroupEntry* e = nullptr;
   for (GroupEntry* c : g->cache)

@@ -71,4 +71,13 @@ long long plan_clip_tiles(const melt_basis* b, int64_t off, int64_t len, int64_t
 // Device of the basis (the current device when it was created).
 int basis_device(const melt_basis* b);
 
+// Correction MLP attached to the basis (melt_basis_set_correction), or nullptr.
+const melt_mlp* basis_correction(const melt_basis* b);
+
+// Correction MLP (melt_mlp.cu): y = x + W2 GELU(W1 (x - mu)/sd + b1) + b2 over
+// n rows of n_in bands; y == x allowed.
+melt_status mlp_apply(const melt_mlp* p, const float* x, float* y, long long n, cudaStream_t s);
+int mlp_inputs(const melt_mlp* p);
+int mlp_device(const melt_mlp* p);
+
 }  // namespace melt

@@ -60,6 +60,18 @@ SIGNATURES = {
     "melt_forward_grouped": (C.c_int, [_VP, _VP, _I64P, _I64P, C.POINTER(C.c_int32), C.c_int, _VP, _VP]),
     "melt_group_sync": (C.c_int, [_VP, _VP]),
     "melt_group_destroy": (C.c_int, [_VP]),
+    "melt_mlp_num_params": (C.c_int64, [C.c_int, C.c_int]),
+    "melt_mlp_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                  C.POINTER(C.c_float), C.POINTER(_VP)]),
+    "melt_mlp_fit_stats": (C.c_int, [_VP, _VP, C.c_int64, _VP]),
+    "melt_mlp_set_adamw": (C.c_int, [_VP, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "melt_mlp_grad": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int, _VP, _VP, _VP]),
+    "melt_mlp_train_step": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int, _VP, _VP]),
+    "melt_mlp_adamw_apply": (C.c_int, [_VP, _VP, _VP]),
+    "melt_mlp_forward": (C.c_int, [_VP, _VP, _VP, C.c_int64, _VP]),
+    "melt_mlp_get_params": (C.c_int, [_VP, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "melt_mlp_destroy": (C.c_int, [_VP]),
+    "melt_basis_set_correction": (C.c_int, [_VP, _VP]),
     "melt_sync": (C.c_int, [_VP, _VP]),
     "melt_destroy": (C.c_int, [_VP]),
     "melt_status_string": (C.c_char_p, [C.c_int]),
@@ -258,6 +270,90 @@ def melt_group_sync(group, stream=None):
 
 def melt_group_destroy(group):
     _check(lib.melt_group_destroy(group), "melt_group_destroy")
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor, an int, or None."""
+    if t is None:
+        return None
+    return C.c_void_p(t if isinstance(t, int) else t.data_ptr())
+
+
+def melt_mlp_num_params(n_in, n_hidden) -> int:
+    return int(lib.melt_mlp_num_params(int(n_in), int(n_hidden)))
+
+
+def melt_mlp_create(n_in, n_hidden, params, mu=None, sd=None):
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    if p.size != melt_mlp_num_params(n_in, n_hidden):
+        raise ValueError("params has the wrong size")
+    m = None if mu is None else np.ascontiguousarray(np.asarray(mu, dtype=np.float32))
+    s = None if sd is None else np.ascontiguousarray(np.asarray(sd, dtype=np.float32))
+    h = C.c_void_p()
+    _check(lib.melt_mlp_create(int(n_in), int(n_hidden), _fptr(p), None if m is None else _fptr(m),
+                               None if s is None else _fptr(s), C.byref(h)), "melt_mlp_create")
+    return h
+
+
+def melt_mlp_fit_stats(mlp, X, n, stream=None):
+    _check(lib.melt_mlp_fit_stats(mlp, _dptr(X), int(n), _stream_ptr(stream)), "melt_mlp_fit_stats")
+
+
+def melt_mlp_set_adamw(mlp, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.01):
+    _check(lib.melt_mlp_set_adamw(mlp, lr, beta1, beta2, eps, wd), "melt_mlp_set_adamw")
+
+
+def melt_mlp_grad(mlp, X, target, rows, batch, grads=None, loss=None, stream=None):
+    _check(lib.melt_mlp_grad(mlp, _dptr(X), _dptr(target), _dptr(rows), int(batch), _dptr(grads),
+                             _dptr(loss), _stream_ptr(stream)), "melt_mlp_grad")
+
+
+def melt_mlp_train_step(mlp, X, target, rows, batch, loss=None, stream=None):
+    _check(lib.melt_mlp_train_step(mlp, _dptr(X), _dptr(target), _dptr(rows), int(batch), _dptr(loss),
+                                   _stream_ptr(stream)), "melt_mlp_train_step")
+
+
+def melt_mlp_adamw_apply(mlp, grads, stream=None):
+    _check(lib.melt_mlp_adamw_apply(mlp, _dptr(grads), _stream_ptr(stream)), "melt_mlp_adamw_apply")
+
+
+def melt_mlp_forward(mlp, X, Y, n, stream=None):
+    _check(lib.melt_mlp_forward(mlp, _dptr(X), _dptr(Y), int(n), _stream_ptr(stream)), "melt_mlp_forward")
+
+
+def melt_mlp_get_params(mlp, n_in, n_hidden):
+    """Returns (params, mu, sd) as float32 numpy arrays."""
+    p = np.zeros(melt_mlp_num_params(n_in, n_hidden), np.float32)
+    m = np.zeros(n_in, np.float32)
+    s = np.zeros(n_in, np.float32)
+    _check(lib.melt_mlp_get_params(mlp, _fptr(p), _fptr(m), _fptr(s)), "melt_mlp_get_params")
+    return p, m, s
+
+
+def melt_mlp_destroy(mlp):
+    _check(lib.melt_mlp_destroy(mlp), "melt_mlp_destroy")
+
+
+def melt_basis_set_correction(basis, mlp):
+    _check(lib.melt_basis_set_correction(basis, mlp), "melt_basis_set_correction")
+
+
+def pack_mlp_params(W1, b1, W2, b2) -> np.ndarray:
+    """Packed parameter vector [W1 | b1 | W2 | b2] (float32)."""
+    return np.concatenate([np.asarray(a, np.float32).reshape(-1) for a in (W1, b1, W2, b2)])
+
+
+def unpack_mlp_params(p, n_in, n_hidden):
+    M, H = n_in, n_hidden
+    W1 = p[:H * M].reshape(H, M)
+    b1 = p[H * M:H * M + H]
+    W2 = p[H * M + H:H * M + H + M * H].reshape(M, H)
+    b2 = p[H * M + H + M * H:]
+    return W1, b1, W2, b2
 
 
 def melt_sync(basis, stream=None):

@@ -1,0 +1,237 @@
+"""Correction MLP on the GPU against the FP64 oracle (oracle/mlp_oracle.py).
+
+* gradients of one batch (gathered rows) element by element;
+* AdamW updates on the same gradients;
+* one train step == gradient + AdamW;
+* the fused inference kernel, and its in-place use behind melt_forward;
+* training on MelT frames toward the STFT+Mel (Slaney) targets lowers the
+  held-out error (the use the correction exists for).
+
+Tolerances: every GPU quantity is an FP32 sum of at most 1024 products fed by
+FP32 values that already carry a few units of roundoff; 1024 x 2^-24 x a few
+stages is about 2e-4 of the largest magnitude in play, which is the bound used.
+"""
+import numpy as np
+import pytest
+
+from oracle import melt_oracle as O
+from oracle import mlp_oracle as P
+from paper_2606_01009_gb300 import inputs as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def melt():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_01009_gb300 import melt as m
+    return m
+
+
+def _problem(n=1500, M=80, Hd=128, seed=3):
+    g = np.random.default_rng(seed)
+    x = (g.standard_normal((n, M)) * 3 - 8).astype(np.float32)
+    tgt = (x * g.uniform(0.7, 1.3, M) + g.uniform(-2, 2, M) + 0.1 * g.standard_normal((n, M))).astype(np.float32)
+    W1 = G.xavier_uniform(seed, Hd, M, 0)
+    W2 = G.xavier_uniform(seed, M, Hd, 1)
+    b1 = (0.1 * g.standard_normal(Hd)).astype(np.float32)
+    b2 = (0.1 * g.standard_normal(M)).astype(np.float32)
+    mu, sd = P.band_stats(x)
+    return x, tgt, [W1, b1, W2, b2], mu.astype(np.float32), sd.astype(np.float32)
+
+
+def _close(got, ref, what, rel=2e-4):
+    ref = np.asarray(ref, np.float64)
+    tol = rel * np.max(np.abs(ref)) + 1e-3 * np.abs(ref)
+    bad = np.abs(np.asarray(got, np.float64) - ref) > tol
+    assert not bad.any(), (what, int(bad.sum()), float(np.max(np.abs(got - ref))), float(np.max(np.abs(ref))))
+
+
+def test_gradients_match_oracle(melt):
+    import torch
+    M, Hd, B = 80, 128, 1024
+    x, tgt, params, mu, sd = _problem(M=M, Hd=Hd)
+    rows = np.random.default_rng(5).choice(x.shape[0], B, replace=False).astype(np.int64)
+    h = melt.melt_mlp_create(M, Hd, melt.pack_mlp_params(*params), mu, sd)
+    X = torch.from_numpy(x).cuda()
+    T = torch.from_numpy(tgt).cuda()
+    R = torch.from_numpy(rows).cuda()
+    grads = torch.zeros(melt.melt_mlp_num_params(M, Hd), device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    melt.melt_mlp_grad(h, X, T, R, B, grads, loss)
+    torch.cuda.synchronize()
+    p64 = [np.asarray(p, np.float64) for p in params]
+    y, cache = P.forward(p64, x[rows], mu.astype(np.float64), sd.astype(np.float64))
+    ref = P.backward(p64, cache, y, tgt[rows], sd.astype(np.float64))
+    got = melt.unpack_mlp_params(grads.cpu().numpy(), M, Hd)
+    for name, gg, rr in zip(["dW1", "db1", "dW2", "db2"], got, ref[:4]):
+        _close(gg, rr, name)
+    sse = float(np.sum((y - tgt[rows]) ** 2))
+    assert loss.item() == pytest.approx(sse, rel=1e-4)
+    melt.melt_mlp_destroy(h)
+
+
+def test_gradients_identity_rows_and_small_batch(melt):
+    import torch
+    M, Hd, B = 40, 64, 37                        # ragged against the 64 x 64 tiles
+    x, tgt, params, mu, sd = _problem(n=37, M=M, Hd=Hd, seed=9)
+    h = melt.melt_mlp_create(M, Hd, melt.pack_mlp_params(*params), mu, sd)
+    grads = torch.zeros(melt.melt_mlp_num_params(M, Hd), device="cuda")
+    melt.melt_mlp_grad(h, torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda(), None, B, grads)
+    torch.cuda.synchronize()
+    p64 = [np.asarray(p, np.float64) for p in params]
+    y, cache = P.forward(p64, x, mu.astype(np.float64), sd.astype(np.float64))
+    ref = P.backward(p64, cache, y, tgt, sd.astype(np.float64))
+    for name, gg, rr in zip(["dW1", "db1", "dW2", "db2"], melt.unpack_mlp_params(grads.cpu().numpy(), M, Hd),
+                            ref[:4]):
+        _close(gg, rr, name)
+    melt.melt_mlp_destroy(h)
+
+
+def test_adamw_matches_oracle_and_train_step_composes(melt):
+    import torch
+    M, Hd, B = 80, 64, 256
+    x, tgt, params, mu, sd = _problem(n=700, M=M, Hd=Hd, seed=11)
+    packed = melt.pack_mlp_params(*params)
+    X, T = torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda()
+    ha = melt.melt_mlp_create(M, Hd, packed, mu, sd)        # grad + adamw_apply
+    hb = melt.melt_mlp_create(M, Hd, packed, mu, sd)        # train_step
+    lr, wd = 3e-3, 0.02
+    for hh in (ha, hb):
+        melt.melt_mlp_set_adamw(hh, lr=lr, wd=wd)
+    n = packed.size
+    p_ref = [np.asarray(p, np.float64) for p in params]
+    st = [(np.zeros_like(p), np.zeros_like(p)) for p in p_ref]
+    grads = torch.zeros(n, device="cuda")
+    order = G.batch_order(1, x.shape[0], 0)
+    for t in range(1, 6):
+        rows = torch.from_numpy(order[(t - 1) * 100:(t - 1) * 100 + B].copy()).cuda()
+        melt.melt_mlp_grad(ha, X, T, rows, B, grads)
+        g_host = grads.cpu().numpy().astype(np.float64)
+        melt.melt_mlp_adamw_apply(ha, grads)
+        melt.melt_mlp_train_step(hb, X, T, rows, B)
+        # oracle AdamW on the very gradients the GPU used
+        gsplit = melt.unpack_mlp_params(g_host, M, Hd)
+        for i in range(4):
+            p_ref[i], m, v = P.adamw_step(p_ref[i], gsplit[i], st[i][0], st[i][1], t, lr=lr, wd=wd)
+            st[i] = (m, v)
+        pa = melt.melt_mlp_get_params(ha, M, Hd)[0]
+        pr = np.concatenate([p.reshape(-1) for p in p_ref])
+        assert np.max(np.abs(pa - pr)) <= 2e-6 * (1 + np.max(np.abs(pr))), t
+        pb = melt.melt_mlp_get_params(hb, M, Hd)[0]
+        assert np.array_equal(pa, pb), t
+        # continue the oracle from the GPU's parameters so later steps compare the update alone
+        p_ref = [np.asarray(a, np.float64) for a in melt.unpack_mlp_params(pa.astype(np.float64), M, Hd)]
+    melt.melt_mlp_destroy(ha)
+    melt.melt_mlp_destroy(hb)
+
+
+def test_forward_kernel_and_in_place(melt):
+    import torch
+    for M, Hd, n in [(80, 256, 1000), (128, 64, 130), (13, 128, 65), (80, 256, 1)]:
+        x, tgt, params, mu, sd = _problem(n=n, M=M, Hd=Hd, seed=M + Hd)
+        h = melt.melt_mlp_create(M, Hd, melt.pack_mlp_params(*params), mu, sd)
+        X = torch.from_numpy(x).cuda()
+        Y = torch.empty_like(X)
+        melt.melt_mlp_forward(h, X, Y, n)
+        p64 = [np.asarray(p, np.float64) for p in params]
+        ref, _ = P.forward(p64, x, mu.astype(np.float64), sd.astype(np.float64))
+        got = Y.cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= 2e-5 * np.max(np.abs(ref)), (M, Hd, n)
+        melt.melt_mlp_forward(h, X, X, n)                  # in place
+        assert np.array_equal(X.cpu().numpy(), got)
+        melt.melt_mlp_destroy(h)
+
+
+def test_fit_stats(melt):
+    import torch
+    x = (np.random.default_rng(2).standard_normal((5000, 80)) * 4 - 7).astype(np.float32)
+    x[:, 3] = 2.5                                          # constant band: sd floor
+    mu, sd = P.band_stats(x.astype(np.float64))
+    h = melt.melt_mlp_create(80, 64, np.zeros(melt.melt_mlp_num_params(80, 64), np.float32))
+    melt.melt_mlp_fit_stats(h, torch.from_numpy(x).cuda(), x.shape[0])
+    _, m, s = melt.melt_mlp_get_params(h, 80, 64)
+    np.testing.assert_allclose(m, mu, rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(s, sd, rtol=1e-5, atol=1e-6)
+    assert s[3] == pytest.approx(1e-6)
+    melt.melt_mlp_destroy(h)
+
+
+def test_correction_behind_melt_forward(melt):
+    import torch
+    clips = [G.rich_clip(71, i, 16000 * 2 + 37 * i) for i in range(5)]
+    pk = G.pack_clips(clips)
+    wave = torch.from_numpy(pk.wave).cuda()
+    M, Hd = 80, 128
+    _, _, params, mu, sd = _problem(n=10, M=M, Hd=Hd, seed=4)
+    mlp = melt.melt_mlp_create(M, Hd, melt.pack_mlp_params(*params), mu, sd)
+    for prec in ["fp32", "bf16"]:
+        fe = melt.Frontend(precision=prec)
+        plain = fe(wave, pk.offsets, pk.lengths)
+        T = plain.shape[0]
+        ref = torch.empty_like(plain)
+        melt.melt_mlp_forward(mlp, plain, ref, T)
+        melt.melt_basis_set_correction(fe.handle, mlp)
+        got = fe(wave, pk.offsets, pk.lengths)
+        got2 = torch.empty_like(got)
+        melt.melt_forward_noalloc(fe.handle, wave, pk.offsets, pk.lengths, got2)
+        fe.sync()
+        assert torch.equal(got, ref) and torch.equal(got2, ref), prec
+        gf = melt.GroupedFrontend([fe])
+        with pytest.raises(melt.MeltError) as ei:
+            gf(wave, pk.offsets, pk.lengths, np.zeros(len(clips), np.int32))
+        assert ei.value.status == melt.MELT_ERR_UNSUPPORTED
+        gf.close()
+        melt.melt_basis_set_correction(fe.handle, None)
+        assert torch.equal(fe(wave, pk.offsets, pk.lengths), plain)
+        fe.close()
+    mf = melt.Frontend(precision="bf16", n_mfcc=40)
+    with pytest.raises(melt.MeltError) as ei:
+        melt.melt_basis_set_correction(mf.handle, mlp)
+    assert ei.value.status == melt.MELT_ERR_UNSUPPORTED
+    mf.close()
+    melt.melt_mlp_destroy(mlp)
+
+
+def test_training_closes_gap_to_stft_mel(melt):
+    """MelT frames -> STFT+Mel (Slaney) targets: the corrected features are much closer held-out."""
+    import torch
+    spec = O.MelTSpec(sr=16000.0, n_fft=400, hop=160, n_mels=80, fmin=0.0, fmax=8000.0)
+    train = [G.rich_clip(81, i, 16000 * 4) for i in range(40)]
+    held = [G.rich_clip(82, i, 16000 * 4) for i in range(6)]
+    fe = melt.Frontend(precision="fp32")
+
+    def feats(clips):
+        pk = G.pack_clips(clips)
+        out = fe(torch.from_numpy(pk.wave).cuda(), pk.offsets, pk.lengths)
+        fe.sync()
+        return out
+
+    Xtr = feats(train)
+    Ttr = torch.from_numpy(np.concatenate([O.stft_mel_clip(c, spec, scale="slaney") for c in train])
+                           .astype(np.float32)).cuda()
+    Xte = feats(held)
+    Tte = np.concatenate([O.stft_mel_clip(c, spec, scale="slaney") for c in held])
+    M, Hd = 80, 256
+    n = Xtr.shape[0]
+    params = melt.pack_mlp_params(G.xavier_uniform(7, Hd, M, 0), np.zeros(Hd), G.xavier_uniform(7, M, Hd, 1),
+                                  np.zeros(M))
+    mlp = melt.melt_mlp_create(M, Hd, params)
+    melt.melt_mlp_fit_stats(mlp, Xtr, n)
+    melt.melt_mlp_set_adamw(mlp, lr=3e-3)
+    B = 1024
+    for ep in range(30):
+        order = torch.from_numpy(G.batch_order(7, n, ep)).cuda()
+        for s in range(0, n - B + 1, B):
+            melt.melt_mlp_train_step(mlp, Xtr, Ttr, order[s:s + B], B)
+    Yte = torch.empty_like(Xte)
+    melt.melt_mlp_forward(mlp, Xte, Yte, Xte.shape[0])
+    plain = O.rmse_db(Xte.cpu().numpy().astype(np.float64), Tte)
+    corr = O.rmse_db(Yte.cpu().numpy().astype(np.float64), Tte)
+    print(f"held-out RMSE vs STFT+Mel (Slaney): plain MelT {plain:.2f} dB, corrected {corr:.2f} dB")
+    assert corr < 0.35 * plain
+    melt.melt_mlp_destroy(mlp)
+    fe.close()
