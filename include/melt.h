@@ -128,14 +128,17 @@ melt_status melt_basis_get_fp64(const melt_basis* basis, double* freqs, double* 
  *   basis_resident   1: the whole basis is loaded once per CTA and kept in
  *                    shared memory; 0: it is streamed from L2 through a ring
  *   a_buffers        MMA A-operand (frame sample) buffers: 1 or 2
- *   stage_slots      ring slots for the FP32 sample span (~14 KB each)
+ *   prefetch_tiles   0..4: how many tiles ahead of the converters the CTA's
+ *                    waveform spans are prefetched into L2 (the converters
+ *                    read samples from global memory; no shared memory is
+ *                    spent on them)
  *   basis_slots      streamed-basis ring slots (ignored when resident)
- *   ksteps_per_slot  basis K-steps (16 samples each) per streamed slot
+ *   ksteps_per_slot  basis K-steps (16 samples each; FP8: 32) per streamed slot
  */
 typedef struct {
   int basis_resident;
   int a_buffers;
-  int stage_slots;
+  int prefetch_tiles;
   int basis_slots;
   int ksteps_per_slot;
 } melt_plan;

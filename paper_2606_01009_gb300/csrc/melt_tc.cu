@@ -70,8 +70,7 @@ bool plan_smem(const TcBasis* tb, TcParams& p, int n_mfcc) {
   p.J = tb->J;
   p.KS = tb->ksteps;
   p.zrows = kF + p.J - 1;
-  p.items = p.zrows * (p.H / 8);
-  p.inv_h8 = 8.0f / (float)p.H;
+  p.nq = p.zrows * (p.H / 4);
   p.kstep_bytes = (uint32_t)tb->kstep_bytes;
   const int parts = P == MELT_BF16X3 ? 2 : 1;
   if (P == MELT_FP8E4M3) {
@@ -84,17 +83,6 @@ bool plan_smem(const TcBasis* tb, TcParams& p, int n_mfcc) {
     p.a_bytes = p.lbo_a * (uint32_t)(p.H / 8);
   }
   p.abuf_bytes = p.a_bytes * parts;
-  // The tile's FP32 span is staged in chunks of whole Z rows, ~16 KB each
-  // (the FP8 form holds the whole span at once).
-  const uint32_t row_bytes = (uint32_t)p.H * 4;
-  const uint32_t span_bytes = row_bytes * p.zrows;
-  p.NCHUNK = (int)((span_bytes + 16383) / 16384);
-  p.CH = (p.zrows + p.NCHUNK - 1) / p.NCHUNK;
-  // a converter thread handles at most kQuadsPerThread float4s of a chunk
-  const int max_rows = kQuadsPerThread * kCvtThreads * 4 / p.H;
-  if (p.CH > max_rows) p.CH = std::max(1, max_rows);
-  p.NCHUNK = (p.zrows + p.CH - 1) / p.CH;
-  p.st_bytes = row_bytes * p.CH;  // slots back to back: the FP8 form reads the span contiguously
   p.step_bytes = p.kstep_bytes * parts;
   melt_plan cands[kMaxCands];
   int nc = 0;
@@ -116,21 +104,20 @@ namespace {
 
 bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) {
   const int P = tb->precision;
-  if (c.a_buffers < 1 || c.a_buffers > 2 || c.stage_slots < 2 || c.stage_slots > 8) return false;
+  if (c.a_buffers < 1 || c.a_buffers > 2 || c.prefetch_tiles < 0 || c.prefetch_tiles > kMaxPrefetch)
+    return false;
   if (!c.basis_resident && (c.basis_slots < 2 || c.basis_slots > 32 || c.ksteps_per_slot < 1))
     return false;
   p.b_resident = c.basis_resident ? 1 : 0;
   p.ZB = c.a_buffers;
+  p.pf = c.prefetch_tiles;
   p.kps = p.b_resident ? 1 : std::min(c.ksteps_per_slot, p.KS);
   p.NB = p.b_resident ? p.KS : c.basis_slots;
   p.bslot_bytes = p.b_resident ? p.step_bytes : p.step_bytes * p.kps;
-  p.NS = (P == MELT_FP8E4M3) ? p.NCHUNK : c.stage_slots;
-  const Bars B(p.NS, p.ZB, p.NB);
+  const Bars B(p.ZB, p.NB);
   uint32_t off = 0;
   p.off_a = off;
   off += align_up(p.abuf_bytes * p.ZB, 128);
-  p.off_st = off;
-  off += align_up(p.st_bytes * p.NS, 128);
   p.off_b = off;
   off += align_up(p.bslot_bytes * p.NB, 128);
   p.off_bar = off;
@@ -155,32 +142,27 @@ bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) 
 }
 
 // Layouts in preference order (whether each fits is checked by try_layout).
-// Measured on the 64 x 30 s workload (N=400, H=160, BF16): a streamed basis
-// with two A buffers and large multi-k-step slots beats a resident basis with
-// one A buffer (50.6 vs 87 us at M=80), because the second A buffer lets the
-// converters fill the next tile while the MMAs of the current one run.  More
-// staging slots come first (they hide the HBM latency of the waveform), then
-// the largest slot that still fits.
+// The waveform needs no shared memory (converters load it from L2, where it
+// was prefetched), so shared memory holds the A buffers and the basis.  A
+// resident basis with two A buffers comes first: the MMAs never wait for a
+// basis copy and the conversion of tile k+1 overlaps the MMAs of tile k.
+// When the basis does not fit beside two A buffers (M > 80 at N = 400, or
+// BF16x3), the basis is streamed from L2 through a ring of the largest slots
+// that fit; the single-buffer layouts come last.
 int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap) {
   (void)tb;
   int n = 0;
-  auto add = [&](int res, int zb, int ns, int nb, int kps) {
-    if (n < cap) out[n++] = melt_plan{res, zb, ns, nb, kps};
+  auto add = [&](int res, int zb, int pf, int nb, int kps) {
+    if (n < cap) out[n++] = melt_plan{res, zb, pf, nb, kps};
   };
   const int sb = (int)std::max(1u, p.step_bytes);
-  const int kps_hi = std::max(1, std::min(p.KS, 49152 / sb));   // <= 48 KB per slot
-  const int kps_lo = std::max(1, std::min(p.KS, 24576 / sb));   // >= 24 KB per slot
-  for (int ns = 4; ns >= 3; --ns)
-    for (int kps = kps_hi; kps >= kps_lo; --kps)
-      for (int nb = 2; nb <= 3; ++nb) add(0, 2, ns, nb, kps);
-  for (int zb = 2; zb >= 1; --zb)
-    for (int ns = 4; ns >= 3; --ns) add(1, zb, ns, p.KS, 1);
-  for (int ns = 4; ns >= 2; --ns)
-    for (int nb = 8; nb >= 2; --nb) add(0, 2, ns, nb, std::max(1, kps_lo / 2));
-  for (int ns = 4; ns >= 2; --ns)
-    for (int nb = 24; nb >= 2; nb -= 2) add(0, 1, ns, nb, 1);
-  for (int ns = 3; ns >= 2; --ns)
-    for (int nb = 3; nb >= 2; --nb) add(0, 2, ns, nb, 1);
+  add(1, 2, 2, p.KS, 1);
+  const int kps_hi = std::max(1, std::min(p.KS, 65536 / sb));   // <= 64 KB per slot
+  for (int kps = kps_hi; kps >= 1; --kps)
+    for (int nb = 2; nb <= 3; ++nb) add(0, 2, 2, nb, kps);
+  add(1, 1, 2, p.KS, 1);
+  for (int kps = kps_hi; kps >= 1; --kps) add(0, 1, 2, 2, kps);
+  for (int nb = 24; nb >= 2; nb -= 2) add(0, 1, 2, nb, 1);
   return n;
 }
 

@@ -6,15 +6,21 @@
 // (Eq. 7), log (Eq. 8) and the optional DCT-II (Eq. 9) fused in the epilogue.
 //
 // One persistent CTA per SM walks a static round-robin list of tiles
-// (128 consecutive frames of one clip).  Warp roles (11 warps):
+// (128 consecutive frames of one clip).  Warp roles (18 warps):
 //   warps 0-3   epilogue: TMEM -> registers, R^2 + I^2, log, (DCT), store
 //   warp  4     TMEM allocator + single-thread tcgen05.mma issuer
 //   warp  5     basis producer: bulk async copies (TMA engine) of the basis
 //               K-step blocks, once per CTA when the basis fits in shared
-//               memory, else streamed through a ring
-//   warp  6     waveform producer: bulk async copies of the tile's FP32
-//               sample span in chunks of ~16 KB into a ring
-//   warps 7-10  converters: staged FP32 samples -> MMA A operand in shared memory
+//               memory next to two A buffers, else streamed through a ring
+//   warps 6-17  converters: waveform samples -> MMA A operand in shared memory
+//
+// Waveform path.  The converters read the tile's FP32 samples straight from
+// global memory into registers (coalesced 16-byte loads) and write the BF16 /
+// e4m3 A operand; one converter thread keeps the spans of the CTA's next
+// tiles streaming into L2 with bulk prefetches, so those loads are L2 hits.
+// No shared memory is spent on staging FP32 samples, which leaves room for a
+// resident basis next to two A buffers (conversion of tile k+1 overlaps the
+// MMAs of tile k, and the MMAs never wait for basis copies).
 //
 // Implicit framing (no im2col in HBM).  Frames overlap (N > H), so the A
 // operand's rows would be H samples apart, which a UMMA shared-memory
@@ -25,15 +31,11 @@
 // so each sample is loaded and converted once into Z (rows of H samples,
 // K-major canonical layout with rows 16 B apart) and the j-shift is a
 // 16-byte offset of the A descriptor's start address.  The J slices
-// accumulate into the same TMEM tile.  Keeping HBM busy takes >= 16 KB bulk
-// copies and >= ~48 KB in flight per SM, so the span is staged by the TMA
-// engine; when the basis is resident the tile has one Z buffer (conversion
-// and MMA of a tile then run back to back, both well inside the tile's HBM
-// time).
+// accumulate into the same TMEM tile.
 // FP8 needs a per-frame scale, which differs between the frames that share
-// a Z row, so the FP8 form stages the tile's span with bulk copies and
-// writes each frame row (im2col inside shared memory only), scaled by
-// 448/amax(frame).
+// a Z row, so the FP8 form first reduces max |x| per Z row, derives each
+// frame's scale, and then writes each frame row (im2col inside shared memory
+// only), scaled by 448/amax(frame).
 //
 // Accumulators: two TMEM tiles of 128 lanes x NC columns (NC = 2*MP, MP =
 // M rounded up to 16): columns [0, MP) hold R, [MP, 2MP) hold I.
@@ -56,17 +58,18 @@ using namespace ptx;
 constexpr int kEpiWarps = 4;
 constexpr int kMmaWarp = 4;
 constexpr int kBWarp = 5;
-constexpr int kProdWarp = 6;
-constexpr int kCvtWarp0 = 7;
-constexpr int kCvtWarps = 4;
-constexpr int kThreads = 32 * (kCvtWarp0 + kCvtWarps);  // 352
-constexpr int kCvtThreads = 32 * kCvtWarps;             // 128
+constexpr int kCvtWarp0 = 6;
+constexpr int kCvtWarps = 12;
+constexpr int kThreads = 32 * (kCvtWarp0 + kCvtWarps);  // 576
+constexpr int kCvtThreads = 32 * kCvtWarps;             // 384
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kF = kTileFrames;  // 128 = UMMA M
 constexpr int kScaleRing = 4;    // FP8 per-frame scale buffers in flight
-constexpr int kQuadsPerThread = 8;  // float4s per converter thread per staged chunk (<= 16 KB)
-constexpr int kEarlyChunks = 5;  // log-Mel rows of up to 80 values are held in registers
+constexpr int kQuadBatch = 8;    // float4 loads per converter thread per batch (two batches in flight)
+constexpr int kItemBatch = 3;    // FP8 frame-row items (16 samples each) per batch
+constexpr int kEpiGroup = 2;     // 16-column chunks per TMEM wait in the epilogue
 constexpr int kMaxMfccTc = 128;  // DCT outputs of the tensor-core epilogue (matrix in shared memory)
+constexpr int kMaxPrefetch = 4;  // tiles whose spans may be prefetched into L2 ahead of use
 
 struct TcParams {
   const float* wave;
@@ -79,8 +82,8 @@ struct TcParams {
   float eps;
   int N, H, M, MP, NC, J, KS;
   int zrows;             // Z rows: 128 + J - 1
-  int items;             // BF16 forms: 8-sample items per tile (zrows * H / 8)
-  float inv_h8;          // 1 / (H / 8)
+  int nq;                // float4 quads of a tile's sample span: zrows * H / 4
+  int pf;                // tiles prefetched into L2 ahead of the converters
   int n_out, n_mfcc;
   uint32_t kstep_bytes;  // one B part of one K-step
   uint32_t step_bytes;   // one K-step of the basis (BF16X3: hi + lo parts)
@@ -90,23 +93,19 @@ struct TcParams {
   uint32_t a_bytes;      // one A part
   uint32_t abuf_bytes;   // one A buffer (BF16X3: hi + lo parts)
   int ZB;                // A buffers
-  int NS, CH, NCHUNK;    // FP8: staging slots, Z rows per chunk, chunks per tile
-  uint32_t st_bytes;     // FP8: bytes per staging slot
   int NB;                // basis slots (resident: NB == KS)
   int b_resident;        // 1: the whole basis stays in shared memory for the CTA's life
   uint32_t tmem_cols, acc_stride, idesc;
   uint32_t desc_hi;      // high word of every operand descriptor (SBO = 128 B, version)
-  uint32_t off_a, off_st, off_b, off_bar, off_misc, off_scale, off_rowmax, off_tab, off_dct;
+  uint32_t off_a, off_b, off_bar, off_misc, off_scale, off_rowmax, off_tab, off_dct;
   uint32_t smem_total;   // dynamic shared memory bytes (incl. alignment slack)
 };
 
 // barrier indices
 struct Bars {
-  int s_full, s_empty, z_full, z_empty, b_full, b_empty, t_full, t_empty, sc_full, drain, total;
-  __host__ __device__ Bars(int NS, int ZB, int NB) {
-    s_full = 0;
-    s_empty = s_full + NS;
-    z_full = s_empty + NS;
+  int z_full, z_empty, b_full, b_empty, t_full, t_empty, sc_full, drain, total;
+  __host__ __device__ Bars(int ZB, int NB) {
+    z_full = 0;
     z_empty = z_full + ZB;
     b_full = z_empty + ZB;
     b_empty = b_full + NB;
@@ -163,7 +162,7 @@ static __device__ __forceinline__ void sts128(uint32_t addr, uint4 v) {
                : "memory");
 }
 
-// Streaming read of 4 samples: read once, keep out of L1.
+// Streaming read of 4 samples that were prefetched into L2: read once, keep out of L1.
 static __device__ __forceinline__ float4 ldg_stream(const float* p) {
   float4 v;
   asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
@@ -172,40 +171,67 @@ static __device__ __forceinline__ float4 ldg_stream(const float* p) {
   return v;
 }
 
-// ----------------------------------------------------------------- roles
-static __device__ void role_wave_producer(const TcParams& p, uint32_t sbase, const Bars& B,
-                                   volatile int* abort) {
-  const uint64_t pol = policy_evict_first();
-  int g = 0;
-  bool ok = true;
-  for (int tile = blockIdx.x; ok && tile < p.n_tiles; tile += gridDim.x) {
-    const TileDesc td = p.tiles[tile];
-    const long long span = (long long)p.zrows * p.H;
-    const long long avail = min(((long long)td.n_samples + 3) & ~3ll, span);
-    for (int c = 0; c < p.NCHUNK; ++c, ++g) {
-      const int slot = g % p.NS;
-      const uint32_t full = sbase + p.off_bar + 8 * (B.s_full + slot);
-      const uint32_t empty = sbase + p.off_bar + 8 * (B.s_empty + slot);
-      if (!mbar_wait(empty, ((g / p.NS) & 1) ^ 1, abort, p.err, kErrTimeout)) {
-        ok = false;
-        break;
-      }
-      const long long f0 = (long long)c * p.CH * p.H;
-      const long long nf = max(0ll, min((long long)p.CH * p.H, avail - f0));
-      if (nf > 0) {
-        mbar_arrive_expect_tx(full, (uint32_t)(nf * 4));
-        bulk_g2s_hint(sbase + p.off_st + slot * p.st_bytes, p.wave + td.in_off + f0,
-                      (uint32_t)(nf * 4), full, pol);
-      } else {
-        mbar_arrive(full);
-      }
-    }
-  }
-  // drain: every issued copy has landed before the CTA can exit
-  for (int k = max(0, g - p.NS); k < g; ++k)
-    drain_wait(sbase + p.off_bar + 8 * (B.s_full + k % p.NS), (k / p.NS) & 1, p.err);
+// Read of 4 samples that neighbouring threads read again (FP8 frame rows): L1-cached.
+static __device__ __forceinline__ float4 ldg_cached(const float* p) {
+  float4 v;
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
 }
 
+// Samples of a tile's span that lie in the clip: the span is zrows * H samples,
+// cut at the clip end rounded up to 4 (the caller guarantees that much is readable).
+static __device__ __forceinline__ long long tile_avail(const TcParams& p, const TileDesc& td) {
+  const long long span = (long long)p.zrows * p.H;
+  return min(((long long)td.n_samples + 3) & ~3ll, span);
+}
+
+// Bulk prefetch of a tile's sample span into L2 (pieces of <= 32 KB).
+static __device__ void prefetch_tile(const TcParams& p, int tile) {
+  const TileDesc td = p.tiles[tile];
+  const long long avail = tile_avail(p, td);
+  const float* src = p.wave + td.in_off;
+  for (long long o = 0; o < avail; o += 8192) {
+    const long long n = min(8192ll, avail - o);
+    prefetch_l2(src + o, (uint32_t)(n * 4));
+  }
+}
+
+// One converter thread runs the prefetch stream: tiles blockIdx.x + i*gridDim.x,
+// `pf` tiles ahead of the tile being converted.  The descriptor of the next
+// tile to prefetch is loaded one step early, so a step never waits on it.
+struct Prefetcher {
+  int next;
+  TileDesc pend;
+  __device__ void start(const TcParams& p) {
+    next = blockIdx.x;
+    for (int i = 0; i < p.pf && next < p.n_tiles; ++i, next += gridDim.x) prefetch_tile(p, next);
+    if (p.pf > 0 && next < p.n_tiles) pend = p.tiles[next];
+  }
+  __device__ void step(const TcParams& p) {
+    if (p.pf > 0 && next < p.n_tiles) {
+      const long long avail = tile_avail(p, pend);
+      const float* src = p.wave + pend.in_off;
+      for (long long o = 0; o < avail; o += 8192)
+        prefetch_l2(src + o, (uint32_t)(min(8192ll, avail - o) * 4));
+      next += gridDim.x;
+      if (next < p.n_tiles) pend = p.tiles[next];
+    }
+  }
+};
+
+// Zero the samples of a quad that lie past the clip end (s = span index of x.x).
+static __device__ __forceinline__ void clip_quad(float4& x, int s, int nsamp) {
+  if (s + 4 > nsamp) {
+    x.x = s < nsamp ? x.x : 0.f;
+    x.y = s + 1 < nsamp ? x.y : 0.f;
+    x.z = s + 2 < nsamp ? x.z : 0.f;
+    x.w = s + 3 < nsamp ? x.w : 0.f;
+  }
+}
+
+// ----------------------------------------------------------------- roles
 static __device__ void role_basis_producer(const TcParams& p, uint32_t sbase, const Bars& B,
                                     volatile int* abort) {
   const uint64_t pol = policy_evict_last();
@@ -351,197 +377,253 @@ __device__ void role_mma(const TcParams& p, uint8_t* gbase, uint32_t sbase, cons
   drain_wait(sbase + p.off_bar + 8 * B.drain, 0, p.err);
 }
 
-// BF16 / BF16X3 converter: staged FP32 span chunks -> Z rows (bf16 hi [, lo]).
+// BF16 / BF16X3 converter: waveform quads (global, L2-prefetched) -> Z rows.
 //
-// Chunk c of a tile holds Z rows [c*CH, c*CH + rows) as contiguous FP32
-// samples.  It is read as float4 "quads" (lanes read consecutive quads:
-// conflict-free), and quad hq is the low or high half (hq & 1) of the Z row
-// segment (row ul, 8-sample group kc) with 8 * (hq >> 1) = (ul - c*CH) H + 8 kc.
-template <int PREC>
-static __device__ void role_convert_staged(const TcParams& p, uint8_t* gbase, uint32_t sbase,
-                                           const Bars& B, volatile int* abort) {
-  const int ct = threadIdx.x - 32 * kCvtWarp0;
-  const int H8 = p.H >> 3;
-  // Every chunk has the same geometry (the last one may have fewer rows), so
-  // this thread's quads and their Z offsets relative to the chunk's first row
-  // are computed once.
-  const int nq_full = p.CH * (p.H >> 2);
-  uint32_t qoff[kQuadsPerThread];
-  int qrow[kQuadsPerThread];
+// Quad q of a tile is the 4 samples at span offset 4q: Z row u = q / (H/4),
+// column r = 4 (q % (H/4)).  Thread ct takes quads ct, ct + 256, ...; lanes of
+// a warp read 512 contiguous bytes per load instruction.  In shared memory,
+// Z element (u, r) sits at (r / 8) * lbo_a + 16 u + 2 (r % 8).
+//
+// The CTA's tiles are one stream of batches (kQuadBatch quads per thread).
+// Two register sets alternate: the loads of batch i+1 are in flight while
+// batch i is converted and stored, across tile boundaries too, so the stream
+// pays one memory latency at its start rather than one per batch.
+struct CvtCursor {
+  int tile, k, b;      // tile index, its ordinal for this CTA, batch within the tile
+  const float* src;    // sample 0 of the tile's span
+  int nsamp;           // samples of the clip from src on
+  TileDesc nxt;        // descriptor of the CTA's following tile (loaded early)
+};
+
+static __device__ __forceinline__ bool cursor_advance(const TcParams& p, CvtCursor& c, int nb) {
+  if (++c.b < nb) return true;
+  c.b = 0;
+  c.tile += gridDim.x;
+  ++c.k;
+  if (c.tile >= p.n_tiles) return false;
+  c.src = p.wave + c.nxt.in_off;
+  c.nsamp = c.nxt.n_samples;
+  if (c.tile + (int)gridDim.x < p.n_tiles) c.nxt = p.tiles[c.tile + gridDim.x];
+  return true;
+}
+
+static __device__ __forceinline__ void cvt_load(const TcParams& p, const CvtCursor& c, int ct,
+                                                float4 (&x)[kQuadBatch]) {
+  const int q0 = c.b * kQuadBatch * kCvtThreads + ct;
 #pragma unroll
-  for (int q = 0; q < kQuadsPerThread; ++q) {
-    const int hq = ct + q * kCvtThreads;
-    const int il = hq >> 1;
-    const int ull = il / H8;
-    const int kc = il - ull * H8;
-    qrow[q] = hq < nq_full ? ull : 1 << 30;
-    qoff[q] = kc * p.lbo_a + ull * 16 + (hq & 1) * 8;
-  }
-  const uint32_t st0 = sbase + p.off_st;
-  int slot = 0;
-  uint32_t sphase = 0;
-  int k = 0;
-  for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++k) {
-    const int zb = p.ZB == 2 ? (k & 1) : 0;
-    if (!warp_wait(sbase + p.off_bar + 8 * (B.z_empty + zb), ((p.ZB == 2 ? (k >> 1) : k) & 1) ^ 1,
-                   abort, p.err))
-      break;
-    const int nsamp = p.tiles[tile].n_samples;
-    const uint32_t zaddr = sbase + p.off_a + zb * p.abuf_bytes;
-    bool ok = true;
-    for (int c = 0; c < p.NCHUNK; ++c) {
-      if (!warp_wait(sbase + p.off_bar + 8 * (B.s_full + slot), sphase, abort, p.err)) {
-        ok = false;
-        break;
-      }
-      const int rows = min(p.CH, p.zrows - c * p.CH);
-      const uint32_t st = st0 + slot * p.st_bytes;
-      const int s_base = c * p.CH * p.H;
-      const uint32_t zrow0 = zaddr + c * p.CH * 16;
-      const bool tail = s_base + rows * p.H > nsamp;  // chunk reaches past the clip's end
-      float4 x[kQuadsPerThread];
-#pragma unroll
-      for (int q = 0; q < kQuadsPerThread; ++q)
-        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(x[q].x), "=f"(x[q].y), "=f"(x[q].z), "=f"(x[q].w)
-                     : "r"(st + 16u * min(ct + q * kCvtThreads, nq_full - 1)));  // stay inside the slot
-      if (tail) {
-#pragma unroll
-        for (int q = 0; q < kQuadsPerThread; ++q) {
-          const int s0 = s_base + 4 * (ct + q * kCvtThreads);
-          x[q].x = s0 < nsamp ? x[q].x : 0.f;
-          x[q].y = s0 + 1 < nsamp ? x[q].y : 0.f;
-          x[q].z = s0 + 2 < nsamp ? x[q].z : 0.f;
-          x[q].w = s0 + 3 < nsamp ? x[q].w : 0.f;
-        }
-      }
-      uint32_t hw[kQuadsPerThread][2];
-#pragma unroll
-      for (int q = 0; q < kQuadsPerThread; ++q) {
-        hw[q][0] = pack_bf16(x[q].x, x[q].y);
-        hw[q][1] = pack_bf16(x[q].z, x[q].w);
-      }
-#pragma unroll
-      for (int q = 0; q < kQuadsPerThread; ++q)
-        if (qrow[q] < rows)
-          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(zrow0 + qoff[q]), "r"(hw[q][0]),
-                       "r"(hw[q][1]));
-      if constexpr (PREC == MELT_BF16X3) {
-#pragma unroll
-        for (int q = 0; q < kQuadsPerThread; ++q) {
-          const uint32_t l0 = pack_bf16(x[q].x - __uint_as_float(hw[q][0] << 16),
-                                        x[q].y - __uint_as_float(hw[q][0] & 0xffff0000u));
-          const uint32_t l1 = pack_bf16(x[q].z - __uint_as_float(hw[q][1] << 16),
-                                        x[q].w - __uint_as_float(hw[q][1] & 0xffff0000u));
-          if (qrow[q] < rows)
-            asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(zrow0 + qoff[q] + p.a_bytes),
-                         "r"(l0), "r"(l1));
-        }
-      }
-      warp_arrive(sbase + p.off_bar + 8 * (B.s_empty + slot));
-      if (++slot == p.NS) {
-        slot = 0;
-        sphase ^= 1;
-      }
-    }
-    if (!ok) break;
-    fence_proxy_async();
-    warp_arrive(sbase + p.off_bar + 8 * (B.z_full + zb));
+  for (int i = 0; i < kQuadBatch; ++i) {
+    const int q = q0 + i * kCvtThreads;
+    x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q < p.nq && 4 * q < c.nsamp) x[i] = ldg_stream(c.src + 4 * q);
   }
 }
 
-// FP8 converter: whole span staged; per-frame amax scale; frame rows (im2col in smem).
+// Convert and store one batch; waits for the A buffer at a tile's first
+// batch and publishes the buffer after its last.  false: a wait gave up.
+template <int PREC>
+static __device__ __forceinline__ bool cvt_store(const TcParams& p, uint32_t sbase, const Bars& B,
+                                                 volatile int* abort, const CvtCursor& c, int ct,
+                                                 int nb, float4 (&x)[kQuadBatch]) {
+  const int zb = p.ZB == 2 ? (c.k & 1) : 0;
+  if (c.b == 0 && !warp_wait(sbase + p.off_bar + 8 * (B.z_empty + zb),
+                             ((p.ZB == 2 ? (c.k >> 1) : c.k) & 1) ^ 1, abort, p.err))
+    return false;
+  const uint32_t zaddr = sbase + p.off_a + zb * p.abuf_bytes;
+  const int h4 = p.H >> 2;
+  const int du = kCvtThreads / h4, dc = kCvtThreads - du * h4;
+  const int q0 = c.b * kQuadBatch * kCvtThreads + ct;
+  int u = q0 / h4, cc = q0 - u * h4;
+#pragma unroll
+  for (int i = 0; i < kQuadBatch; ++i) {
+    const int q = q0 + i * kCvtThreads;
+    if (q < p.nq) {
+      clip_quad(x[i], 4 * q, c.nsamp);
+      const uint32_t h0 = pack_bf16(x[i].x, x[i].y), h1 = pack_bf16(x[i].z, x[i].w);
+      const uint32_t a = zaddr + (uint32_t)(cc >> 1) * p.lbo_a + (uint32_t)u * 16u + (cc & 1) * 8u;
+      asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(h0), "r"(h1));
+      if constexpr (PREC == MELT_BF16X3) {
+        const uint32_t l0 = pack_bf16(x[i].x - __uint_as_float(h0 << 16),
+                                      x[i].y - __uint_as_float(h0 & 0xffff0000u));
+        const uint32_t l1 = pack_bf16(x[i].z - __uint_as_float(h1 << 16),
+                                      x[i].w - __uint_as_float(h1 & 0xffff0000u));
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + p.a_bytes), "r"(l0), "r"(l1));
+      }
+    }
+    cc += dc;
+    u += du;
+    if (cc >= h4) {
+      cc -= h4;
+      ++u;
+    }
+  }
+  if (c.b == nb - 1) {
+    fence_proxy_async();
+    warp_arrive(sbase + p.off_bar + 8 * (B.z_full + zb));
+  }
+  return true;
+}
+
+template <int PREC>
+static __device__ void role_convert_bf16(const TcParams& p, uint32_t sbase, const Bars& B,
+                                         volatile int* abort) {
+  const int ct = threadIdx.x - 32 * kCvtWarp0;
+  const int nb = (p.nq + kQuadBatch * kCvtThreads - 1) / (kQuadBatch * kCvtThreads);
+  if ((int)blockIdx.x >= p.n_tiles) return;
+  Prefetcher pf;
+  if (ct == 0) pf.start(p);
+  CvtCursor cur;
+  cur.tile = blockIdx.x;
+  cur.k = 0;
+  cur.b = 0;
+  {
+    const TileDesc td = p.tiles[cur.tile];
+    cur.src = p.wave + td.in_off;
+    cur.nsamp = td.n_samples;
+  }
+  if (cur.tile + (int)gridDim.x < p.n_tiles) cur.nxt = p.tiles[cur.tile + gridDim.x];
+  float4 xa[kQuadBatch], xb[kQuadBatch];
+  cvt_load(p, cur, ct, xa);
+  CvtCursor nxt = cur;
+  bool more = cursor_advance(p, nxt, nb);
+  for (;;) {
+    if (more) cvt_load(p, nxt, ct, xb);
+    if (ct == 0 && cur.b == 0) pf.step(p);
+    if (!cvt_store<PREC>(p, sbase, B, abort, cur, ct, nb, xa) || !more) break;
+    cur = nxt;
+    more = cursor_advance(p, nxt, nb);
+    if (more) cvt_load(p, nxt, ct, xa);
+    if (ct == 0 && cur.b == 0) pf.step(p);
+    if (!cvt_store<PREC>(p, sbase, B, abort, cur, ct, nb, xb) || !more) break;
+    cur = nxt;
+    more = cursor_advance(p, nxt, nb);
+  }
+}
+
+// Max over the lanes of a warp that hold the same Z row u, merged into
+// row_max[u] (float bits of non-negative values order like unsigned ints).
+// Every lane of the warp calls this together; rows >= zrows are ignored.
+static __device__ __forceinline__ void warp_row_max(unsigned* row_max, int u, unsigned bits,
+                                                    int zrows) {
+  const int lane = threadIdx.x & 31;
+  unsigned rem = 0xffffffffu;
+  while (rem) {
+    const int leader = __ffs(rem) - 1;
+    const int ul = __shfl_sync(0xffffffffu, u, leader);
+    const unsigned in = __ballot_sync(0xffffffffu, u == ul);
+    const unsigned m = __reduce_max_sync(0xffffffffu, u == ul ? bits : 0u);
+    if (lane == leader && ul < zrows && m) atomicMax(row_max + ul, m);
+    rem &= ~in;
+  }
+}
+
+// FP8 converter: per-Z-row max |x|, per-frame scale, quantised frame rows.
 static __device__ void role_convert_fp8(const TcParams& p, uint8_t* gbase, uint32_t sbase,
                                  const Bars& B, volatile int* abort) {
   const int ct = threadIdx.x - 32 * kCvtWarp0;
-  const int cw = ct >> 5, lane = threadIdx.x & 31;
+  const int h4 = p.H >> 2;
+  const int du = kCvtThreads / h4, dc = kCvtThreads % h4;
   const int KL = p.N - (p.J - 1) * p.H;  // samples of the last slice of a frame
-  const int G = 2 * p.KS;                // 16-byte groups per frame row
-  float* rowmax = reinterpret_cast<float*>(gbase + p.off_rowmax);
-  float* rowpre = rowmax + p.zrows;
-  float* inv_s = rowpre + p.zrows;
+  const int G = 2 * p.KS;                // 16-sample groups per frame row
+  unsigned* rowmax = reinterpret_cast<unsigned*>(gbase + p.off_rowmax);  // [zrows]
+  unsigned* rowpre = rowmax + p.zrows;                                   // [zrows], r < KL
+  float* inv_s = reinterpret_cast<float*>(rowpre + p.zrows);             // [kF]
   float* scales = reinterpret_cast<float*>(gbase + p.off_scale);
-  const float* span = reinterpret_cast<const float*>(gbase + p.off_st);
-  int g = 0;
+  Prefetcher pf;
+  if (ct == 0) pf.start(p);
   int k = 0;
+  TileDesc td_next;
+  if ((int)blockIdx.x < p.n_tiles) td_next = p.tiles[blockIdx.x];
   for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++k) {
+    if (ct == 0) pf.step(p);
     const int zb = p.ZB == 2 ? (k & 1) : 0;
-    bool ok = warp_wait(sbase + p.off_bar + 8 * (B.z_empty + zb),
-                        ((p.ZB == 2 ? (k >> 1) : k) & 1) ^ 1, abort, p.err);
-    for (int c = 0; ok && c < p.NCHUNK; ++c)
-      ok = warp_wait(sbase + p.off_bar + 8 * (B.s_full + c), ((g + c) / p.NS) & 1, abort, p.err);
-    // all converter warps take the same decision before any named barrier
-    if (!named_barrier_and(1, kCvtThreads, ok)) break;
-    const int nsamp = p.tiles[tile].n_samples;
-    // 1. per Z row: max |x| over the row and over its first KL samples
-    for (int u = cw; u < p.zrows; u += kCvtWarps) {
-      float mf = 0.f, mp = 0.f;
-      for (int r = lane; r < p.H; r += 32) {
-        const int s = u * p.H + r;
-        const float v = s < nsamp ? fabsf(span[s]) : 0.f;
-        mf = fmaxf(mf, v);
-        if (r < KL) mp = fmaxf(mp, v);
-      }
+    const TileDesc td = td_next;
+    if (tile + (int)gridDim.x < p.n_tiles) td_next = p.tiles[tile + gridDim.x];
+    const float* src = p.wave + td.in_off;
+    const int nsamp = td.n_samples;
+    // 0. reset the row maxima (the previous tile's readers passed two barriers since)
+    for (int i = ct; i < 2 * p.zrows; i += kCvtThreads) rowmax[i] = 0u;
+    named_barrier(1, kCvtThreads);
+    // 1. max |x| per Z row, over the whole row and over its first KL samples
+    {
+      int u = ct / h4, c = ct - (ct / h4) * h4;
+      for (int q0 = 0; q0 < p.nq; q0 += kQuadBatch * kCvtThreads) {
+        float4 x[kQuadBatch];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        mf = fmaxf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
-        mp = fmaxf(mp, __shfl_xor_sync(0xffffffffu, mp, o));
-      }
-      if (lane == 0) {
-        rowmax[u] = mf;
-        rowpre[u] = mp;
+        for (int i = 0; i < kQuadBatch; ++i) {
+          const int q = q0 + ct + i * kCvtThreads;
+          x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (q < p.nq && 4 * q < nsamp) x[i] = ldg_cached(src + 4 * q);
+        }
+#pragma unroll
+        for (int i = 0; i < kQuadBatch; ++i) {
+          const int q = q0 + ct + i * kCvtThreads;
+          clip_quad(x[i], 4 * q, nsamp);
+          const float m = fmaxf(fmaxf(fabsf(x[i].x), fabsf(x[i].y)), fmaxf(fabsf(x[i].z), fabsf(x[i].w)));
+          const unsigned bits = q < p.nq ? __float_as_uint(m) : 0u;
+          warp_row_max(rowmax, u, bits, p.zrows);
+          warp_row_max(rowpre, u, 4 * c < KL ? bits : 0u, p.zrows);
+          c += dc;
+          u += du;
+          if (c >= h4) {
+            c -= h4;
+            ++u;
+          }
+        }
       }
     }
     named_barrier(1, kCvtThreads);
     // 2. frame scale: s_t = amax/448, quantiser multiplier 448/amax (1 for silent frames)
     if (ct < kF) {
       const int f = ct;
-      float amax = rowpre[f + p.J - 1];
-      for (int j = 0; j < p.J - 1; ++j) amax = fmaxf(amax, rowmax[f + j]);
+      float amax = __uint_as_float(rowpre[f + p.J - 1]);
+      for (int j = 0; j < p.J - 1; ++j) amax = fmaxf(amax, __uint_as_float(rowmax[f + j]));
       const bool pos = amax > 0.f;
       inv_s[f] = pos ? 448.f / amax : 1.f;
       const float st = pos ? amax / 448.f : 1.f;
       scales[(k % kScaleRing) * kF + f] = st / 448.f;
     }
-    named_barrier(1, kCvtThreads);
+    bool ok = warp_wait(sbase + p.off_bar + 8 * (B.z_empty + zb),
+                        ((p.ZB == 2 ? (k >> 1) : k) & 1) ^ 1, abort, p.err);
+    // all converter warps take the same decision at this barrier
+    if (!named_barrier_and(1, kCvtThreads, ok)) break;
     // 3. quantised frame rows, K-major canonical layout (16-byte core rows)
     const uint32_t abase = sbase + p.off_a + zb * p.abuf_bytes;
-    for (int it = ct; it < kF * G; it += kCvtThreads) {
-      const int f = it / G;
-      const int gq = it - f * G;
-      const float inv = inv_s[f];
-      const int n0 = gq * 16;
-      float x[16];
+    const int items = kF * G;
+    for (int i0 = 0; i0 < items; i0 += kItemBatch * kCvtThreads) {
+      float4 x[kItemBatch][4];
 #pragma unroll
-      for (int e = 0; e < 16; e += 4) {
-        const int n = n0 + e;
-        const int s = f * p.H + n;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (n + 3 < p.N && s + 3 < nsamp) {
-          v = *reinterpret_cast<const float4*>(span + s);
-        } else {
-          float t[4] = {0.f, 0.f, 0.f, 0.f};
-          for (int q = 0; q < 4; ++q)
-            if (n + q < p.N && s + q < nsamp) t[q] = span[s + q];
-          v = make_float4(t[0], t[1], t[2], t[3]);
+      for (int b = 0; b < kItemBatch; ++b) {
+        const int it = i0 + ct + b * kCvtThreads;
+        const int f = it / G, g = it - (it / G) * G;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int n = 16 * g + 4 * e;
+          const int s = f * p.H + n;
+          x[b][e] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (it < items && n < p.N && s < nsamp) x[b][e] = ldg_cached(src + s);
         }
-        x[e] = v.x * inv;
-        x[e + 1] = v.y * inv;
-        x[e + 2] = v.z * inv;
-        x[e + 3] = v.w * inv;
       }
-      uint4 q;
-      q.x = pack_e4m3x4(x[0], x[1], x[2], x[3]);
-      q.y = pack_e4m3x4(x[4], x[5], x[6], x[7]);
-      q.z = pack_e4m3x4(x[8], x[9], x[10], x[11]);
-      q.w = pack_e4m3x4(x[12], x[13], x[14], x[15]);
-      sts128(abase + gq * p.lbo_a + f * 16, q);
+#pragma unroll
+      for (int b = 0; b < kItemBatch; ++b) {
+        const int it = i0 + ct + b * kCvtThreads;
+        if (it < items) {
+          const int f = it / G, g = it - (it / G) * G;
+          const float inv = inv_s[f];
+          uint32_t w[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int n = 16 * g + 4 * e;
+            float4 v = x[b][e];
+            clip_quad(v, f * p.H + n, nsamp);
+            w[e] = pack_e4m3x4(v.x * inv, v.y * inv, v.z * inv, v.w * inv);
+          }
+          sts128(abase + (uint32_t)g * p.lbo_a + (uint32_t)f * 16u, make_uint4(w[0], w[1], w[2], w[3]));
+        }
+      }
     }
     fence_proxy_async();
     warp_arrive(sbase + p.off_bar + 8 * (B.z_full + zb));
     warp_arrive(sbase + p.off_bar + 8 * (B.sc_full + (k % kScaleRing)));
-    for (int c = 0; c < p.NCHUNK; ++c) warp_arrive(sbase + p.off_bar + 8 * (B.s_empty + c));
-    g += p.NCHUNK;
   }
 }
 
@@ -555,8 +637,12 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
   const bool vec8 = ((p.n_out & 7) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 31) == 0);
   const int nch = p.MP >> 4;
   int k = 0;
+  TileDesc td_next;
+  if ((int)blockIdx.x < p.n_tiles) td_next = p.tiles[blockIdx.x];
   for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++k) {
     const int acc = k & 1;
+    const TileDesc td = td_next;  // loaded one tile early
+    if (tile + (int)gridDim.x < p.n_tiles) td_next = p.tiles[tile + gridDim.x];
     if (!warp_wait(sbase + p.off_bar + 8 * (B.t_full + acc), (k >> 1) & 1, abort, p.err)) break;
     float sc = 1.f;
     if constexpr (PREC == MELT_FP8E4M3) {
@@ -566,80 +652,55 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
       sc = scales[(k % kScaleRing) * kF + row];
     }
     tc_fence_after();
-    const TileDesc td = p.tiles[tile];
     const bool valid = row < td.n_frames;
     const uint32_t t0 = tmem_base + ((uint32_t)(32 * warp) << 16) + acc * p.acc_stride;
     float* orow = p.out + (size_t)(td.out_row + row) * p.n_out;
     if constexpr (!MFCC) {
-      if (nch <= kEarlyChunks) {
-        // every value of the row into registers, TMEM released before the stores
-        float v[16 * kEarlyChunks];
+      // groups of up to kEpiGroup 16-column chunks: all of a group's TMEM loads
+      // are issued before one wait; TMEM is released after the last group's wait
+#pragma unroll 1
+      for (int c0 = 0; c0 < nch; c0 += kEpiGroup) {
+        float re[kEpiGroup][16], im[kEpiGroup][16];
 #pragma unroll
-        for (int c = 0; c < kEarlyChunks; ++c) {
-          if (c < nch) {
-            float re[16], im[16];
-            tmem_ld16(t0 + 16 * c, re);
-            tmem_ld16(t0 + p.MP + 16 * c, im);
-            tmem_ld_wait(re, im);
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const float r = re[e] * sc, i = im[e] * sc;
-              v[16 * c + e] = __logf(fmaf(r, r, fmaf(i, i, p.eps)));
-            }
+        for (int g = 0; g < kEpiGroup; ++g) {
+          if (c0 + g < nch) {
+            tmem_ld16(t0 + 16 * (c0 + g), re[g]);
+            tmem_ld16(t0 + p.MP + 16 * (c0 + g), im[g]);
           }
         }
-        tc_fence_before();
-        warp_arrive(sbase + p.off_bar + 8 * (B.t_empty + acc));
-        if (valid) {
+        tmem_ld_wait();
 #pragma unroll
-          for (int c = 0; c < kEarlyChunks; ++c) {
-            if (c < nch) {
-              if (vec8 && 16 * c + 16 <= p.M) {
-                stg256(orow + 16 * c, v + 16 * c);
-                stg256(orow + 16 * c + 8, v + 16 * c + 8);
+        for (int g = 0; g < kEpiGroup; ++g) {
+          reg_fence16(re[g]);
+          reg_fence16(im[g]);
+        }
+        if (c0 + kEpiGroup >= nch) {
+          tc_fence_before();
+          warp_arrive(sbase + p.off_bar + 8 * (B.t_empty + acc));
+        }
+#pragma unroll
+        for (int g = 0; g < kEpiGroup; ++g) {
+          const int cc = c0 + g;
+          if (cc < nch) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const float r = re[g][e] * sc, i = im[g][e] * sc;
+              re[g][e] = __logf(fmaf(r, r, fmaf(i, i, p.eps)));
+            }
+            if (valid) {
+              if (vec8 && 16 * cc + 16 <= p.M) {
+                stg256(orow + 16 * cc, re[g]);
+                stg256(orow + 16 * cc + 8, re[g] + 8);
               } else {
 #pragma unroll
                 for (int e = 0; e < 16; ++e)
-                  if (16 * c + e < p.M) orow[16 * c + e] = v[16 * c + e];
+                  if (16 * cc + e < p.M) orow[16 * cc + e] = re[g][e];
               }
             }
           }
         }
-        continue;
       }
-      // longer rows: chunk by chunk, the next chunk's TMEM load overlapping this one's math
-      float re[2][16], im[2][16];
-      tmem_ld16(t0, re[0]);
-      tmem_ld16(t0 + p.MP, im[0]);
-      for (int c = 0; c < nch; c += 2) {
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          const int cc = c + half;
-          if (cc >= nch) break;
-          tmem_ld_wait(re[half], im[half]);
-          if (cc + 1 < nch) {
-            tmem_ld16(t0 + 16 * (cc + 1), re[half ^ 1]);
-            tmem_ld16(t0 + p.MP + 16 * (cc + 1), im[half ^ 1]);
-          }
-          float v[16];
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const float r = re[half][e] * sc, i = im[half][e] * sc;
-            v[e] = __logf(fmaf(r, r, fmaf(i, i, p.eps)));
-          }
-          if (valid) {
-            if (vec8 && 16 * cc + 16 <= p.M) {
-              stg256(orow + 16 * cc, v);
-              stg256(orow + 16 * cc + 8, v + 8);
-            } else {
-#pragma unroll
-              for (int e = 0; e < 16; ++e)
-                if (16 * cc + e < p.M) orow[16 * cc + e] = v[e];
-            }
-          }
-        }
-      }
-      tmem_ld_wait();
+      continue;
     } else {
       // MFCC: the frame's log-Mel row stays in registers; C[k] = sum_m lm[m] D[k][m]
       float lm[16 * NCH];
@@ -655,6 +716,8 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
           lm[16 * c + e] = (16 * c + e < p.M) ? __logf(fmaf(r, r, i * i) + p.eps) : 0.f;
         }
       }
+      tc_fence_before();
+      warp_arrive(sbase + p.off_bar + 8 * (B.t_empty + acc));
 #pragma unroll 1
       for (int kk = 0; kk < p.n_mfcc; ++kk) {
         const float4* d4 = reinterpret_cast<const float4*>(dct + kk * 16 * NCH);
@@ -670,8 +733,6 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
         if (valid) orow[kk] = a0 + a1;
       }
     }
-    tc_fence_before();
-    warp_arrive(sbase + p.off_bar + 8 * (B.t_empty + acc));
   }
 }
 
@@ -682,16 +743,12 @@ __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_const
   const uint32_t sbase = (raw + 127u) & ~127u;
   uint8_t* gbase = smem_raw + (sbase - raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const Bars B(p.NS, p.ZB, p.NB);
+  const Bars B(p.ZB, p.NB);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + p.off_misc);
   volatile int* abort = reinterpret_cast<volatile int*>(gbase + p.off_misc + 4);
 
   if (threadIdx.x == 0) {
     auto bar = [&](int i) { return sbase + p.off_bar + 8 * i; };
-    for (int i = 0; i < p.NS; ++i) {
-      mbar_init(bar(B.s_full + i), 1);
-      mbar_init(bar(B.s_empty + i), kCvtWarps);
-    }
     for (int i = 0; i < p.ZB; ++i) {
       mbar_init(bar(B.z_full + i), kCvtWarps);
       mbar_init(bar(B.z_empty + i), 1);
@@ -752,14 +809,11 @@ __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_const
   } else if (warp == kBWarp) {
     if (lane == 0) role_basis_producer(p, sbase, B, abort);
     __syncwarp();
-  } else if (warp == kProdWarp) {
-    if (lane == 0) role_wave_producer(p, sbase, B, abort);
-    __syncwarp();
   } else if (warp >= kCvtWarp0) {
     if constexpr (PREC == MELT_FP8E4M3)
       role_convert_fp8(p, gbase, sbase, B, abort);
     else
-      role_convert_staged<PREC>(p, gbase, sbase, B, abort);
+      role_convert_bf16<PREC>(p, sbase, B, abort);
     __syncwarp();
   } else {
     role_epilogue<PREC, NCH, MFCC>(p, gbase, sbase, B, tmem_base, abort);

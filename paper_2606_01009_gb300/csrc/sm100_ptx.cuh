@@ -97,6 +97,12 @@ static __device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void* s
       : "memory");
 }
 
+// Bring `bytes` (multiple of 16) at `src` (16-byte aligned) into L2 ahead of
+// use; no completion signal, no shared memory.
+static __device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 static __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -232,6 +238,18 @@ static __device__ __forceinline__ void tmem_ld_wait(float (&a)[16], float (&b)[1
         "+f"(b[12]), "+f"(b[13]), "+f"(b[14]), "+f"(b[15])
       :
       : "memory");
+}
+
+// Compiler-only fence: marks 16 registers as rewritten here, so that no use of
+// them (written asynchronously by tcgen05.ld) is moved above a preceding
+// tcgen05.wait::ld.
+static __device__ __forceinline__ void reg_fence16(float (&a)[16]) {
+  asm volatile(""
+               : "+f"(a[0]), "+f"(a[1]), "+f"(a[2]), "+f"(a[3]), "+f"(a[4]), "+f"(a[5]), "+f"(a[6]),
+                 "+f"(a[7]), "+f"(a[8]), "+f"(a[9]), "+f"(a[10]), "+f"(a[11]), "+f"(a[12]),
+                 "+f"(a[13]), "+f"(a[14]), "+f"(a[15])
+               :
+               : "memory");
 }
 
 }  // namespace ptx
