@@ -134,6 +134,12 @@ melt_status melt_basis_get_fp64(const melt_basis* basis, double* freqs, double* 
  *                    spent on them)
  *   basis_slots      streamed-basis ring slots (ignored when resident)
  *   ksteps_per_slot  basis K-steps (16 samples each; FP8: 32) per streamed slot
+ *   cta_pair         1 (BF16 only): clusters of two CTAs share each MMA
+ *                    (tcgen05 cta_group::2, 256 frames); each CTA keeps half
+ *                    of the basis resident (basis_resident must be 1) and
+ *                    stages its waveform span through a ring of bulk copies
+ *                    (as many ~14 KB slots as fit; prefetch_tiles, basis_slots
+ *                    and ksteps_per_slot are ignored).  0: one CTA per MMA.
  */
 typedef struct {
   int basis_resident;
@@ -141,6 +147,7 @@ typedef struct {
   int prefetch_tiles;
   int basis_slots;
   int ksteps_per_slot;
+  int cta_pair;
 } melt_plan;
 
 /* melt_plan_get - the layout the next forward will use (host struct out).

@@ -5,7 +5,7 @@
 #include <cstring>
 #include <vector>
 
-#include "melt_tc_kernel.cuh"
+#include "melt_tc2_kernel.cuh"
 
 namespace melt {
 
@@ -55,6 +55,7 @@ constexpr uint32_t kSmemLimit = 227 * 1024;
 constexpr int kMaxCands = 512;
 
 bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc);
+bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc);
 int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap);
 
 uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
@@ -92,7 +93,8 @@ bool plan_smem(const TcBasis* tb, TcParams& p, int n_mfcc) {
     nc = candidate_list(tb, p, cands, kMaxCands);
   }
   for (int i = 0; i < nc; ++i) {
-    if (try_layout(tb, p, cands[i], n_mfcc)) return true;
+    if (cands[i].cta_pair ? try_layout_pair(tb, p, cands[i], n_mfcc) : try_layout(tb, p, cands[i], n_mfcc))
+      return true;
   }
   return false;
 }
@@ -104,6 +106,11 @@ namespace {
 
 bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) {
   const int P = tb->precision;
+  if (c.cta_pair != 0) return false;
+  p.NS = p.CH = p.NCHUNK = 0;
+  p.st_bytes = p.off_st = 0;
+  p.b_lbo = (uint32_t)p.NC * 16;
+  p.step_bytes = p.kstep_bytes * (P == MELT_BF16X3 ? 2 : 1);
   if (c.a_buffers < 1 || c.a_buffers > 2 || c.prefetch_tiles < 0 || c.prefetch_tiles > kMaxPrefetch)
     return false;
   if (!c.basis_resident && (c.basis_slots < 2 || c.basis_slots > 32 || c.ksteps_per_slot < 1))
@@ -141,6 +148,61 @@ bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) 
   return true;
 }
 
+// CTA-pair layout (BF16): A buffers, the waveform staging ring and this
+// CTA's half of the basis (resident), then barriers and tables.  The ring
+// takes every slot that still fits (2..8).
+bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) {
+  if (c.cta_pair != 1 || tb->precision != MELT_BF16 || !tb->d_b2) return false;
+  if (c.basis_resident != 1 || c.a_buffers < 1 || c.a_buffers > 2) return false;
+  if (c.prefetch_tiles < 0 || c.prefetch_tiles > kMaxPrefetch) return false;
+  p.b_resident = 1;
+  p.ZB = c.a_buffers;
+  p.pf = 0;
+  p.kps = 1;
+  p.NB = p.KS;
+  p.step_bytes = p.kstep_bytes / 2;  // one K-step block of this CTA's N/2 basis rows
+  p.bslot_bytes = p.step_bytes;
+  p.b_lbo = (uint32_t)(p.NC / 2) * 16;
+  // staging chunks: whole Z rows, <= 16 KB, <= what one converter pass covers
+  const uint32_t row_bytes = (uint32_t)p.H * 4;
+  const uint32_t span_bytes = row_bytes * p.zrows;
+  int nchunk = (int)((span_bytes + 16383) / 16384);
+  int ch = (p.zrows + nchunk - 1) / nchunk;
+  const int max_rows = kPQuads * kPCvtThreads * 4 / p.H;
+  if (ch > max_rows) ch = std::max(1, max_rows);
+  p.CH = ch;
+  p.NCHUNK = (p.zrows + ch - 1) / ch;
+  p.st_bytes = row_bytes * ch;
+  for (int ns = 8; ns >= 2; --ns) {
+    const PairBars B(ns, p.ZB, p.KS);
+    uint32_t off = 0;
+    p.off_a = off;
+    off += align_up(p.abuf_bytes * p.ZB, 128);
+    p.off_st = off;
+    off += align_up(p.st_bytes * ns, 128);
+    p.off_b = off;
+    off += align_up(p.step_bytes * p.KS, 128);
+    p.off_bar = off;
+    off += align_up(8 * B.total, 128);
+    p.off_tab = off;
+    off += align_up(8 * p.KS, 128);
+    p.off_misc = off;
+    off += 128;
+    p.off_scale = p.off_rowmax = off;
+    p.off_dct = off;
+    off += align_up(4 * n_mfcc * p.MP, 128);
+    if (off + 128 > kSmemLimit) continue;
+    p.NS = ns;
+    p.smem_total = off + 128;
+    p.tmem_cols = p.NC <= 32 ? 64 : p.NC <= 64 ? 128 : p.NC <= 128 ? 256 : 512;
+    p.acc_stride = p.tmem_cols / 2;
+    p.idesc = idesc_f32acc(1u, 2 * kF, p.NC);  // M = 256 over the pair
+    p.desc_hi = (128u >> 4) | (1u << 14);
+    return true;
+  }
+  return false;
+}
+
 // Layouts in preference order (whether each fits is checked by try_layout).
 // The waveform needs no shared memory (converters load it from L2, where it
 // was prefetched), so shared memory holds the A buffers and the basis.  A
@@ -153,9 +215,19 @@ int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap
   (void)tb;
   int n = 0;
   auto add = [&](int res, int zb, int pf, int nb, int kps) {
-    if (n < cap) out[n++] = melt_plan{res, zb, pf, nb, kps};
+    if (n < cap) out[n++] = melt_plan{res, zb, pf, nb, kps, 0};
   };
-  const int sb = (int)std::max(1u, p.step_bytes);
+  const int sb = (int)std::max(1u, p.kstep_bytes * (tb->precision == MELT_BF16X3 ? 2u : 1u));
+  if (tb->precision == MELT_BF16 && tb->d_b2) {
+    // CTA pairs first where the staging ring keeps >= 4 slots (measured on the
+    // 64 x 30 s batch: 44 us vs 50 us single-CTA at M = 80; with 2 slots at
+    // M = 128 the pair is slower than a single CTA, 71 vs 62 us)
+    for (int zb = 2; zb >= 1; --zb) {
+      const melt_plan pc{1, zb, 0, p.KS, 1, 1};
+      TcParams q = p;
+      if (n < cap && try_layout_pair(tb, q, pc, tb->n_mfcc) && q.NS >= 4) out[n++] = pc;
+    }
+  }
   add(1, 2, 2, p.KS, 1);
   const int kps_hi = std::max(1, std::min(p.KS, 65536 / sb));   // <= 64 KB per slot
   for (int kps = kps_hi; kps >= 1; --kps)
@@ -237,15 +309,29 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
   if (cudaMalloc(&tb->d_b, img.size()) != cudaSuccess) return MELT_ERR_OOM;
   if (cudaMemcpy(tb->d_b, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return MELT_ERR_CUDA;
+  if (P == MELT_BF16) {
+    // CTA-pair image: the K-step blocks of basis rows [0, MP) (W_r), then those
+    // of rows [MP, 2 MP) (W_i); each block is 2 core columns x MP rows x 16 B
+    const size_t half_step = (size_t)MP * 32;
+    std::vector<uint8_t> img2((size_t)2 * KS * half_step, 0);
+    for (int h = 0; h < 2; ++h)
+      for (int s = 0; s < KS; ++s)
+        for (int cc = 0; cc < 2; ++cc)
+          for (int r = 0; r < MP; ++r)
+            std::memcpy(img2.data() + ((size_t)h * KS + s) * half_step + (size_t)cc * MP * 16 + (size_t)r * 16,
+                        img.data() + (size_t)s * kstep_bytes + (size_t)cc * NC * 16 + (size_t)(h * MP + r) * 16,
+                        16);
+    if (cudaMalloc(&tb->d_b2, img2.size()) != cudaSuccess) return MELT_ERR_OOM;
+    if (cudaMemcpy(tb->d_b2, img2.data(), img2.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return MELT_ERR_CUDA;
+  }
   return MELT_OK;
 }
 
 void tc_free(TcBasis* tb) {
   cudaFree(tb->d_b);
-  cudaFree(tb->d_b_lo);
-  cudaFree(tb->d_kmap);
-  tb->d_b = tb->d_b_lo = nullptr;
-  tb->d_kmap = nullptr;
+  cudaFree(tb->d_b2);
+  tb->d_b = tb->d_b2 = nullptr;
 }
 
 int tc_max_mfcc() { return kMaxMfccTc; }
@@ -261,7 +347,7 @@ int tc_candidates(const TcBasis* tb, melt_plan* out, int cap) {
   int m = 0;
   for (int i = 0; i < n && m < cap; ++i) {
     TcParams q = p;
-    if (try_layout(tb, q, all[i], tb->n_mfcc)) {
+    if (all[i].cta_pair ? try_layout_pair(tb, q, all[i], tb->n_mfcc) : try_layout(tb, q, all[i], tb->n_mfcc)) {
       bool dup = false;  // several candidates collapse to one layout (e.g. kps clipped)
       for (int j = 0; j < m; ++j)
         dup |= std::memcmp(&out[j], &all[i], sizeof(melt_plan)) == 0;
@@ -296,31 +382,67 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
   std::memset(&p, 0, sizeof(p));
   if (!plan_smem(tb, p, L.n_mfcc)) return cudaErrorInvalidConfiguration;
   if (L.n_mfcc > kMaxMfccTc) return cudaErrorInvalidValue;
+  const bool pair = p.NS > 0;  // only the CTA-pair layout stages the waveform
   p.wave = L.wave;
   p.tiles = L.tiles;
   p.n_tiles = L.n_tiles;
-  p.bimg = static_cast<const uint8_t*>(tb->d_b);
+  p.bimg = static_cast<const uint8_t*>(pair ? tb->d_b2 : tb->d_b);
   p.dct = L.dct;
   p.out = L.out;
   p.err = L.err;
   p.eps = L.eps;
   p.n_mfcc = L.n_mfcc;
   p.n_out = L.n_mfcc ? L.n_mfcc : tb->n_mels;
-  KernelFn fn = L.n_mfcc ? kernel_for_mfcc(tb->precision, p.MP / 16)
-                        : kernel_for_plain(tb->precision, p.MP / 16);
+  KernelFn fn = pair ? kernel_for_pair(L.n_mfcc > 0, p.MP / 16)
+                     : (L.n_mfcc ? kernel_for_mfcc(tb->precision, p.MP / 16)
+                                 : kernel_for_plain(tb->precision, p.MP / 16));
   if (!fn) return cudaErrorInvalidValue;
   const int smem = (int)p.smem_total;
-  static thread_local KernelFn last_fn = nullptr;
-  static thread_local int last_smem = 0;
-  if (fn != last_fn || smem > last_smem) {
+  static thread_local KernelFn last_fn[4] = {nullptr, nullptr, nullptr, nullptr};
+  static thread_local int last_smem[4] = {0, 0, 0, 0};
+  static thread_local int last_i = 0;
+  int hit = -1;
+  for (int i = 0; i < 4; ++i)
+    if (last_fn[i] == fn && last_smem[i] >= smem) hit = i;
+  if (hit < 0) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    last_fn = fn;
-    last_smem = smem;
+    last_fn[last_i] = fn;
+    last_smem[last_i] = smem;
+    last_i = (last_i + 1) & 3;
   }
-  const int grid = std::min(L.n_tiles, L.sm_count);
-  fn<<<grid, kThreads, smem, stream>>>(p);
-  return cudaGetLastError();
+  if (!pair) {
+    const int grid = std::min(L.n_tiles, L.sm_count);
+    fn<<<grid, kThreads, smem, stream>>>(p);
+    return cudaGetLastError();
+  }
+  // CTA pairs: clusters of two, as many as can be resident at once (persistent)
+  p.n_pairs = (L.n_tiles + 1) / 2;
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kPThreads, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TcBasis* mtb = const_cast<TcBasis*>(tb);
+  if (mtb->pair_clusters < 0 || mtb->pair_smem != smem) {
+    cfg.gridDim = dim3(2 * (L.sm_count / 2), 1, 1);
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&n, fn, &cfg);
+    if (e != cudaSuccess) return e;
+    mtb->pair_clusters = n;
+    mtb->pair_smem = smem;
+  }
+  if (mtb->pair_clusters < 1) return cudaErrorInvalidConfiguration;
+  const int clusters = std::min(p.n_pairs, mtb->pair_clusters);
+  cfg.gridDim = dim3(2 * clusters, 1, 1);
+  return cudaLaunchKernelEx(&cfg, fn, p);
 }
 
 }  // namespace melt

@@ -21,10 +21,11 @@ struct TcBasis {
   int kstep_k = 0;      // K per MMA instruction (16 for BF16, 32 for FP8)
   int n_cols = 0;       // UMMA N = 2M rounded up to a multiple of 16
   size_t kstep_bytes = 0;  // bytes of one K-step block of the B operand
-  void* d_b = nullptr;     // B operand blocks, one per K-step (hi part for BF16x3)
-  void* d_b_lo = nullptr;  // BF16x3: lo part blocks
-  uint32_t* d_kmap = nullptr;  // unused
+  void* d_b = nullptr;     // B operand blocks, one per K-step (BF16x3: hi and lo parts)
+  void* d_b2 = nullptr;    // BF16 CTA-pair image: W_r rows' blocks, then W_i rows' blocks
   int n_mfcc = 0;
+  int pair_clusters = -1;  // co-resident 2-CTA clusters of the pair kernel (-1: not queried)
+  int pair_smem = 0;       // shared memory size that count was queried for
   bool forced = false;         // plan below was set explicitly (melt_plan_set / autotune)
   melt_plan plan = {};         // forced layout
 };

@@ -1,0 +1,469 @@
+// Device side of the CTA-pair tensor-core MelT kernel (BF16), included by
+// melt_tc2.cu.
+#pragma once
+// The pair kernel runs as clusters of two CTAs on neighbouring SMs.  The even
+// CTA issues 2-SM MMAs (tcgen05 cta_group::2, M = 256): each CTA supplies the
+// A operand of its own 128-frame tile, and the basis B is split by its rows
+// between the two, so each CTA keeps only half of it (W_r rows in the even
+// CTA, W_i rows in the odd one) resident in shared memory.  The half that is
+// saved holds a TMA staging ring for the waveform, so the FP32 samples arrive
+// by bulk copies (deep in flight, no registers) while the basis never moves.
+// Each CTA's TMEM receives R and I of its own frames, so the epilogue is the
+// single-CTA one.
+//
+// Warp roles per CTA (11 warps):
+//   warps 0-3   epilogue: TMEM -> registers, R^2 + I^2, log, (DCT), store
+//   warp  4     TMEM allocation for the pair; in the even CTA, the MMA issuer
+//   warp  5     basis producer: this CTA's half of the basis, once
+//   warp  6     waveform producer: bulk copies of the tile's FP32 span into a ring
+//   warps 7-10  converters: staged FP32 samples -> polyphase Z rows (BF16)
+//
+// Synchronisation.  Barriers that gate the pair's MMAs live in the even CTA
+// and count arrivals from both CTAs (the odd CTA arrives through its
+// shared::cluster address): Z buffers full (converters of both), accumulators
+// drained (epilogues of both), odd half of the basis loaded.  MMA completion
+// is multicast to both CTAs' barriers (Z buffer free, accumulator full).
+// Every wait is bounded; both CTAs meet in a cluster barrier before either
+// releases TMEM or exits, so no CTA touches a peer that has left.
+#include "melt_tc_kernel.cuh"
+
+namespace melt {
+namespace tc {
+
+constexpr int kPEpiWarps = 4;
+constexpr int kPMmaWarp = 4;
+constexpr int kPBWarp = 5;
+constexpr int kPProdWarp = 6;
+constexpr int kPCvtWarp0 = 7;
+constexpr int kPCvtWarps = 4;
+constexpr int kPThreads = 32 * (kPCvtWarp0 + kPCvtWarps);  // 352
+constexpr int kPCvtThreads = 32 * kPCvtWarps;              // 128
+constexpr int kPQuads = 8;  // float4s per converter thread per staged chunk (<= 16 KB)
+
+struct PairBars {
+  int s_full, s_empty, z_full, z_empty, b_full, peer_b, t_full, t_empty, drain, total;
+  __host__ __device__ PairBars(int NS, int ZB, int KS) {
+    s_full = 0;
+    s_empty = s_full + NS;
+    z_full = s_empty + NS;
+    z_empty = z_full + ZB;
+    b_full = z_empty + ZB;
+    peer_b = b_full + 1;  // the resident half basis completes on one barrier
+    t_full = peer_b + 1;
+    t_empty = t_full + 2;
+    drain = t_empty + 2;
+    total = drain + 1;
+  }
+};
+
+struct PairCtx {
+  uint32_t sbase;      // this CTA's shared base (shared::cta address)
+  uint32_t rank;       // 0 = even CTA (MMA issuer), 1 = odd
+  int cluster, n_clusters;
+  volatile int* abort;
+};
+
+static __device__ __forceinline__ uint32_t pbar(const TcParams& p, const PairCtx& c, int i) {
+  return c.sbase + p.off_bar + 8 * i;
+}
+
+// Arrival of one warp on a barrier of the even CTA.
+static __device__ __forceinline__ void warp_arrive_leader(uint32_t local_bar) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive_cluster(mapa_shared(local_bar, 0));
+}
+
+static __device__ __forceinline__ bool warp_wait_cl(uint32_t bar, uint32_t parity, volatile int* abort,
+                                                    int* err) {
+  bool ok = true;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait_cluster(bar, parity, abort, err, kErrTimeout);
+  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
+// Tile of pair q for this CTA; an odd tile past the end is an empty tile.
+static __device__ __forceinline__ TileDesc pair_tile(const TcParams& p, const PairCtx& c, int q) {
+  const int t = 2 * q + (int)c.rank;
+  TileDesc td;
+  if (t < p.n_tiles) return p.tiles[t];
+  td.in_off = 0;
+  td.out_row = 0;
+  td.n_frames = 0;
+  td.n_samples = 0;
+  td.group = 0;
+  td.clip = -1;
+  return td;
+}
+
+static __device__ void pair_wave_producer(const TcParams& p, const PairCtx& c, const PairBars& B) {
+  const uint64_t pol = policy_evict_first();
+  int g = 0;
+  bool ok = true;
+  for (int q = c.cluster; ok && q < p.n_pairs; q += c.n_clusters) {
+    const TileDesc td = pair_tile(p, c, q);
+    if (td.n_frames == 0) continue;  // empty tile: the converters skip it too
+    const long long avail = tile_avail(p, td);
+    for (int ch = 0; ch < p.NCHUNK; ++ch, ++g) {
+      const int slot = g % p.NS;
+      const uint32_t full = pbar(p, c, B.s_full + slot);
+      if (!mbar_wait(pbar(p, c, B.s_empty + slot), ((g / p.NS) & 1) ^ 1, c.abort, p.err,
+                     kErrTimeout)) {
+        ok = false;
+        break;
+      }
+      const long long f0 = (long long)ch * p.CH * p.H;
+      const long long nf = max(0ll, min((long long)p.CH * p.H, avail - f0));
+      if (nf > 0) {
+        mbar_arrive_expect_tx(full, (uint32_t)(nf * 4));
+        bulk_g2s_hint(c.sbase + p.off_st + slot * p.st_bytes, p.wave + td.in_off + f0,
+                      (uint32_t)(nf * 4), full, pol);
+      } else {
+        mbar_arrive(full);
+      }
+    }
+  }
+  // every issued copy has landed before the CTA can exit
+  for (int k = max(0, g - p.NS); k < g; ++k)
+    drain_wait(pbar(p, c, B.s_full + k % p.NS), (k / p.NS) & 1, p.err);
+}
+
+static __device__ void pair_basis_producer(const TcParams& p, const PairCtx& c, const PairBars& B) {
+  const uint64_t pol = policy_evict_last();
+  const uint32_t total = p.step_bytes * (uint32_t)p.KS;
+  const uint8_t* src = p.bimg + (size_t)c.rank * total;  // this CTA's half
+  const uint32_t full = pbar(p, c, B.b_full);
+  mbar_arrive_expect_tx(full, total);
+  for (uint32_t o = 0; o < total; o += 32768u)
+    bulk_g2s_hint(c.sbase + p.off_b + o, src + o, min(32768u, total - o), full, pol);
+  drain_wait(full, 0, p.err);
+  if (c.rank == 1) mbar_arrive_cluster(mapa_shared(pbar(p, c, B.peer_b), 0));
+}
+
+// Even CTA only: one thread issues every pair MMA.
+static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx& c,
+                                const PairBars& B, uint32_t tmem_base) {
+  const uint2* tab = reinterpret_cast<const uint2*>(gbase + p.off_tab);
+  const uint64_t hi = (uint64_t)p.desc_hi << 32;
+  const uint32_t a_lo0 = ((c.sbase + p.off_a) >> 4) | ((p.lbo_a >> 4) << 16);
+  const uint32_t abuf16 = p.abuf_bytes >> 4;
+  int k = 0;
+  bool ok = true;
+  for (int q = c.cluster; q < p.n_pairs; q += c.n_clusters, ++k) {
+    const int zb = p.ZB == 2 ? (k & 1) : 0;
+    const int acc = k & 1;
+    ok = mbar_wait_cluster(pbar(p, c, B.z_full + zb), (p.ZB == 2 ? (k >> 1) : k) & 1, c.abort, p.err,
+                           kErrTimeout) &&
+         mbar_wait_cluster(pbar(p, c, B.t_empty + acc), ((k >> 1) & 1) ^ 1, c.abort, p.err,
+                           kErrTimeout);
+    if (ok && k == 0)
+      ok = mbar_wait(pbar(p, c, B.b_full), 0, c.abort, p.err, kErrTimeout) &&
+           mbar_wait_cluster(pbar(p, c, B.peer_b), 0, c.abort, p.err, kErrTimeout);
+    if (!ok) break;
+    tc_fence_after();
+    const uint32_t d = tmem_base + acc * p.acc_stride;
+    const uint32_t alo = a_lo0 + zb * abuf16;
+    const uint32_t tab_s = smem_u32(tab);
+#pragma unroll 1
+    for (int s0 = 0; s0 < p.KS; s0 += 8) {
+      uint32_t tx[8], ty[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                     : "=r"(tx[u]), "=r"(ty[u])
+                     : "r"(tab_s + 8u * min(s0 + u, p.KS - 1)));
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (s0 + u < p.KS) mma_f16_pair(d, hi | (alo + tx[u]), hi | ty[u], p.idesc, s0 + u > 0);
+    }
+    mma_commit_pair_mc(pbar(p, c, B.z_empty + zb), 3);
+    mma_commit_pair_mc(pbar(p, c, B.t_full + acc), 3);
+  }
+  // no pair MMA may still be running when either CTA releases TMEM
+  mma_commit_pair_mc(pbar(p, c, B.drain), 3);
+}
+
+// Staged FP32 span chunks -> Z rows (bf16).  Chunk ch of a tile holds Z rows
+// [ch*CH, ch*CH + rows) as contiguous FP32 samples, read as float4 "quads"
+// (lanes read consecutive quads: conflict-free); quad hq is the low or high
+// half (hq & 1) of the Z row segment (row ul, 8-sample group kc) with
+// 8 * (hq >> 1) = (ul - ch*CH) H + 8 kc.
+static __device__ void pair_convert(const TcParams& p, const PairCtx& c, const PairBars& B) {
+  const int ct = threadIdx.x - 32 * kPCvtWarp0;
+  const int H8 = p.H >> 3;
+  const int nq_full = p.CH * (p.H >> 2);
+  uint32_t qoff[kPQuads];
+  int qrow[kPQuads];
+#pragma unroll
+  for (int q = 0; q < kPQuads; ++q) {
+    const int hq = ct + q * kPCvtThreads;
+    const int il = hq >> 1;
+    const int ull = il / H8;
+    const int kc = il - ull * H8;
+    qrow[q] = hq < nq_full ? ull : 1 << 30;
+    qoff[q] = kc * p.lbo_a + ull * 16 + (hq & 1) * 8;
+  }
+  const uint32_t st0 = c.sbase + p.off_st;
+  int slot = 0;
+  uint32_t sphase = 0;
+  int k = 0;
+  for (int qp = c.cluster; qp < p.n_pairs; qp += c.n_clusters, ++k) {
+    const int zb = p.ZB == 2 ? (k & 1) : 0;
+    if (!warp_wait_cl(pbar(p, c, B.z_empty + zb), ((p.ZB == 2 ? (k >> 1) : k) & 1) ^ 1, c.abort,
+                      p.err))
+      break;
+    const TileDesc td = pair_tile(p, c, qp);
+    const int nsamp = td.n_samples;
+    const uint32_t zaddr = c.sbase + p.off_a + zb * p.abuf_bytes;
+    bool ok = true;
+    for (int ch = 0; td.n_frames > 0 && ch < p.NCHUNK; ++ch) {
+      if (!warp_wait(pbar(p, c, B.s_full + slot), sphase, c.abort, p.err)) {
+        ok = false;
+        break;
+      }
+      const int rows = min(p.CH, p.zrows - ch * p.CH);
+      const uint32_t st = st0 + slot * p.st_bytes;
+      const int s_base = ch * p.CH * p.H;
+      const uint32_t zrow0 = zaddr + ch * p.CH * 16;
+      const bool tail = s_base + rows * p.H > nsamp;
+      float4 x[kPQuads];
+#pragma unroll
+      for (int q = 0; q < kPQuads; ++q)
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(x[q].x), "=f"(x[q].y), "=f"(x[q].z), "=f"(x[q].w)
+                     : "r"(st + 16u * min(ct + q * kPCvtThreads, nq_full - 1)));
+      if (tail) {
+#pragma unroll
+        for (int q = 0; q < kPQuads; ++q) clip_quad(x[q], s_base + 4 * (ct + q * kPCvtThreads), nsamp);
+      }
+#pragma unroll
+      for (int q = 0; q < kPQuads; ++q) {
+        if (qrow[q] < rows) {
+          const uint32_t h0 = pack_bf16(x[q].x, x[q].y), h1 = pack_bf16(x[q].z, x[q].w);
+          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(zrow0 + qoff[q]), "r"(h0), "r"(h1));
+        }
+      }
+      warp_arrive(pbar(p, c, B.s_empty + slot));
+      if (++slot == p.NS) {
+        slot = 0;
+        sphase ^= 1;
+      }
+    }
+    if (!ok) break;
+    fence_proxy_async();
+    warp_arrive_leader(pbar(p, c, B.z_full + zb));
+  }
+}
+
+template <int NCH, bool MFCC>
+__device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& c, const PairBars& B,
+                              uint32_t tmem_base) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = 32 * warp + lane;
+  const float* dct = reinterpret_cast<const float*>(gbase + p.off_dct);
+  const bool vec8 = ((p.n_out & 7) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 31) == 0);
+  const int nch = p.MP >> 4;
+  int k = 0;
+  for (int q = c.cluster; q < p.n_pairs; q += c.n_clusters, ++k) {
+    const int acc = k & 1;
+    const TileDesc td = pair_tile(p, c, q);
+    if (!warp_wait_cl(pbar(p, c, B.t_full + acc), (k >> 1) & 1, c.abort, p.err)) break;
+    tc_fence_after();
+    const bool valid = row < td.n_frames;
+    const uint32_t t0 = tmem_base + ((uint32_t)(32 * warp) << 16) + acc * p.acc_stride;
+    float* orow = p.out + (size_t)(td.out_row + row) * p.n_out;
+    if (td.n_frames == 0) {  // empty tile: nothing to read
+      tc_fence_before();
+      warp_arrive_leader(pbar(p, c, B.t_empty + acc));
+      continue;
+    }
+    if constexpr (!MFCC) {
+#pragma unroll 1
+      for (int c0 = 0; c0 < nch; c0 += kEpiGroup) {
+        float re[kEpiGroup][16], im[kEpiGroup][16];
+#pragma unroll
+        for (int g = 0; g < kEpiGroup; ++g) {
+          if (c0 + g < nch) {
+            tmem_ld16(t0 + 16 * (c0 + g), re[g]);
+            tmem_ld16(t0 + p.MP + 16 * (c0 + g), im[g]);
+          }
+        }
+        tmem_ld_wait();
+#pragma unroll
+        for (int g = 0; g < kEpiGroup; ++g) {
+          reg_fence16(re[g]);
+          reg_fence16(im[g]);
+        }
+        if (c0 + kEpiGroup >= nch) {
+          tc_fence_before();
+          warp_arrive_leader(pbar(p, c, B.t_empty + acc));
+        }
+#pragma unroll
+        for (int g = 0; g < kEpiGroup; ++g) {
+          const int cc = c0 + g;
+          if (cc < nch) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const float r = re[g][e], i = im[g][e];
+              re[g][e] = __logf(fmaf(r, r, fmaf(i, i, p.eps)));
+            }
+            if (valid) {
+              if (vec8 && 16 * cc + 16 <= p.M) {
+                stg256(orow + 16 * cc, re[g]);
+                stg256(orow + 16 * cc + 8, re[g] + 8);
+              } else {
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                  if (16 * cc + e < p.M) orow[16 * cc + e] = re[g][e];
+              }
+            }
+          }
+        }
+      }
+    } else {
+      float lm[16 * NCH];
+#pragma unroll
+      for (int cc = 0; cc < NCH; ++cc) {
+        float re[16], im[16];
+        tmem_ld16(t0 + 16 * cc, re);
+        tmem_ld16(t0 + 16 * NCH + 16 * cc, im);
+        tmem_ld_wait(re, im);
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          lm[16 * cc + e] = (16 * cc + e < p.M) ? __logf(fmaf(re[e], re[e], im[e] * im[e]) + p.eps) : 0.f;
+      }
+      tc_fence_before();
+      warp_arrive_leader(pbar(p, c, B.t_empty + acc));
+#pragma unroll 1
+      for (int kk = 0; kk < p.n_mfcc; ++kk) {
+        const float4* d4 = reinterpret_cast<const float4*>(dct + kk * 16 * NCH);
+        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+        for (int qq = 0; qq < 4 * NCH; ++qq) {
+          const float4 d = d4[qq];
+          a0 = fmaf(lm[4 * qq], d.x, a0);
+          a1 = fmaf(lm[4 * qq + 1], d.y, a1);
+          a0 = fmaf(lm[4 * qq + 2], d.z, a0);
+          a1 = fmaf(lm[4 * qq + 3], d.w, a1);
+        }
+        if (valid) orow[kk] = a0 + a1;
+      }
+    }
+  }
+}
+
+template <int NCH, bool MFCC>
+__global__ void __launch_bounds__(kPThreads, 1) melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 127u) & ~127u;
+  uint8_t* gbase = smem_raw + (sbase - raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const PairBars B(p.NS, p.ZB, p.KS);
+  PairCtx c;
+  c.sbase = sbase;
+  c.rank = cluster_ctarank();
+  c.cluster = blockIdx.x >> 1;
+  c.n_clusters = gridDim.x >> 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + p.off_misc);
+  c.abort = reinterpret_cast<volatile int*>(gbase + p.off_misc + 4);
+
+  if (threadIdx.x == 0) {
+    auto bar = [&](int i) { return sbase + p.off_bar + 8 * i; };
+    for (int i = 0; i < p.NS; ++i) {
+      mbar_init(bar(B.s_full + i), 1);
+      mbar_init(bar(B.s_empty + i), kPCvtWarps);
+    }
+    for (int i = 0; i < p.ZB; ++i) {
+      mbar_init(bar(B.z_full + i), 2 * kPCvtWarps);  // converters of both CTAs (even CTA's copy is used)
+      mbar_init(bar(B.z_empty + i), 1);
+    }
+    mbar_init(bar(B.b_full), 1);
+    mbar_init(bar(B.peer_b), 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(bar(B.t_full + i), 1);
+      mbar_init(bar(B.t_empty + i), 2 * kPEpiWarps);  // epilogues of both CTAs
+    }
+    mbar_init(bar(B.drain), 1);
+    *c.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == kPBWarp) {
+    // K-step table: A start offset (16-byte units, polyphase j-shift) and B low word
+    uint2* tab = reinterpret_cast<uint2*>(gbase + p.off_tab);
+    const uint32_t b_lo0 = ((sbase + p.off_b) >> 4) | ((p.b_lbo >> 4) << 16);
+    const uint32_t step16 = p.step_bytes >> 4;
+    for (int j = 0, s0 = 0; j < p.J; ++j) {
+      const int steps = (min(p.H, p.N - j * p.H) + 15) / 16;
+      for (int kk = lane; kk < steps; kk += 32)
+        tab[s0 + kk] = make_uint2((2u * kk * p.lbo_a + 16u * j) >> 4, b_lo0 + (s0 + kk) * step16);
+      s0 += steps;
+    }
+  }
+  if (warp == kPMmaWarp) {
+    tmem_alloc_pair(smem_u32(tmem_slot), p.tmem_cols);
+    tmem_relinquish_pair();
+  }
+  if constexpr (MFCC) {
+    if (warp < kPEpiWarps) {
+      float* dct = reinterpret_cast<float*>(gbase + p.off_dct);
+      for (int i = threadIdx.x; i < p.n_mfcc * p.MP; i += 32 * kPEpiWarps) {
+        const int kk = i / p.MP, m = i - kk * p.MP;
+        dct[i] = m < p.M ? p.dct[kk * p.M + m] : 0.f;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // both CTAs' barriers exist before either arrives on the other's
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == kPMmaWarp) {
+    if (lane == 0) {
+      if (c.rank == 0) pair_mma(p, gbase, c, B, tmem_base);
+      drain_wait(pbar(p, c, B.drain), 0, p.err);
+    }
+    __syncwarp();
+  } else if (warp == kPBWarp) {
+    if (lane == 0) pair_basis_producer(p, c, B);
+    __syncwarp();
+  } else if (warp == kPProdWarp) {
+    if (lane == 0) pair_wave_producer(p, c, B);
+    __syncwarp();
+  } else if (warp >= kPCvtWarp0) {
+    pair_convert(p, c, B);
+    __syncwarp();
+  } else {
+    pair_epilogue<NCH, MFCC>(p, gbase, c, B, tmem_base);
+    __syncwarp();
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // neither CTA leaves (or frees TMEM) while its peer may still use it
+  if (warp == kPMmaWarp) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem_base, p.tmem_cols);
+  }
+}
+
+template <bool MFCC>
+KernelFn pick_pair_kernel(int nch) {
+  if constexpr (!MFCC) {
+    (void)nch;
+    return melt_tc_pair_kernel<1, false>;
+  } else {
+    switch (nch) {
+      case 1: return melt_tc_pair_kernel<1, true>;
+      case 2: return melt_tc_pair_kernel<2, true>;
+      case 3: return melt_tc_pair_kernel<3, true>;
+      case 4: return melt_tc_pair_kernel<4, true>;
+      case 5: return melt_tc_pair_kernel<5, true>;
+      case 6: return melt_tc_pair_kernel<6, true>;
+      case 7: return melt_tc_pair_kernel<7, true>;
+      case 8: return melt_tc_pair_kernel<8, true>;
+      default: return nullptr;
+    }
+  }
+}
+
+}  // namespace tc
+}  // namespace melt

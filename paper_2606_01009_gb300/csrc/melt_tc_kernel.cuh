@@ -99,6 +99,12 @@ struct TcParams {
   uint32_t desc_hi;      // high word of every operand descriptor (SBO = 128 B, version)
   uint32_t off_a, off_b, off_bar, off_misc, off_scale, off_rowmax, off_tab, off_dct;
   uint32_t smem_total;   // dynamic shared memory bytes (incl. alignment slack)
+  // CTA-pair kernel only: FP32 span staging ring and the half-basis layout
+  int NS, CH, NCHUNK;    // staging slots, Z rows per chunk, chunks per tile
+  uint32_t st_bytes;     // bytes per staging slot
+  uint32_t off_st;
+  uint32_t b_lbo;        // B operand: bytes between the two K core columns of a K-step block
+  int n_pairs;           // tile pairs (tile 2q + rank of pair q goes to CTA `rank`)
 };
 
 // barrier indices
@@ -236,14 +242,14 @@ static __device__ void role_basis_producer(const TcParams& p, uint32_t sbase, co
                                     volatile int* abort) {
   const uint64_t pol = policy_evict_last();
   if (p.b_resident) {
-    // every K-step block once, each to its own slot; consumers never release them
-    for (int s = 0; s < p.KS; ++s) {
-      const uint32_t full = sbase + p.off_bar + 8 * (B.b_full + s);
-      mbar_arrive_expect_tx(full, p.step_bytes);
-      bulk_g2s_hint(sbase + p.off_b + s * p.step_bytes, p.bimg + (size_t)s * p.step_bytes,
-                    p.step_bytes, full, pol);
-    }
-    for (int s = 0; s < p.KS; ++s) drain_wait(sbase + p.off_bar + 8 * (B.b_full + s), 0, p.err);
+    // the whole basis once, in copies of <= 32 KB that all complete on b_full[0];
+    // consumers never release it
+    const uint32_t full = sbase + p.off_bar + 8 * B.b_full;
+    const uint32_t total = p.step_bytes * (uint32_t)p.KS;
+    mbar_arrive_expect_tx(full, total);
+    for (uint32_t o = 0; o < total; o += 32768u)
+      bulk_g2s_hint(sbase + p.off_b + o, p.bimg + o, min(32768u, total - o), full, pol);
+    drain_wait(full, 0, p.err);
     return;
   }
   // streamed: slots of kps consecutive K-steps (contiguous in the basis image)
@@ -297,9 +303,7 @@ __device__ void role_mma(const TcParams& p, uint8_t* gbase, uint32_t sbase, cons
                    kErrTimeout))
       break;
     bool ok = true;
-    if (p.b_resident && k == 0)
-      for (int s = 0; ok && s < p.KS; ++s)
-        ok = mbar_wait(sbase + p.off_bar + 8 * (B.b_full + s), 0, abort, p.err, kErrTimeout);
+    if (p.b_resident && k == 0) ok = mbar_wait(sbase + p.off_bar + 8 * B.b_full, 0, abort, p.err, kErrTimeout);
     if (!ok) break;
     tc_fence_after();
     const uint32_t d = tmem_base + acc * p.acc_stride;
@@ -852,6 +856,8 @@ KernelFn pick_kernel(int nch) {
 // Defined in melt_tc_plain.cu (log-Mel) and melt_tc_mfcc.cu (MFCC epilogue).
 KernelFn kernel_for_plain(int prec, int nch);
 KernelFn kernel_for_mfcc(int prec, int nch);
+// Defined in melt_tc2.cu: the CTA-pair kernel (BF16).
+KernelFn kernel_for_pair(bool mfcc, int nch);
 
 }  // namespace tc
 }  // namespace melt

@@ -48,7 +48,7 @@ static __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t pari
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(ok)
       : "r"(bar), "r"(parity)
@@ -57,6 +57,9 @@ static __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t pari
 }
 
 // Wait for the phase with parity `parity` of barrier `bar` to complete.
+// Polls with the non-blocking test_wait: a suspended try_wait was measured
+// to resume microseconds after the phase completed (notably for arrivals
+// from the peer CTA), which stalls every hand-off of the pipeline.
 // Returns false (after latching `err_bit` in *err and setting *abort) when
 // the wait ran past the limit or another thread of the CTA aborted.
 static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
@@ -237,6 +240,108 @@ static __device__ __forceinline__ void tmem_ld_wait(float (&a)[16], float (&b)[1
         "+f"(b[5]), "+f"(b[6]), "+f"(b[7]), "+f"(b[8]), "+f"(b[9]), "+f"(b[10]), "+f"(b[11]),
         "+f"(b[12]), "+f"(b[13]), "+f"(b[14]), "+f"(b[15])
       :
+      : "memory");
+}
+
+// ------------------------------------------------- CTA pairs (cluster of 2)
+// Rank of this CTA in its cluster.
+static __device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Shared-memory address of the same offset in CTA `rank` of the cluster.
+static __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+// Arrive on an mbarrier given by a shared::cluster address (possibly in the
+// peer CTA), with the instruction's default release semantics (CTA scope).
+// Used where the data the arrival publishes lives in the arriving CTA's own
+// shared memory or TMEM and is consumed by its own SM's tensor core; only the
+// signal crosses CTAs.  (A cluster-scope release was measured to wait for the
+// SM's in-flight bulk copies, i.e. about one HBM latency per hand-off.)
+static __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+static __device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait with cluster-scope acquire (barriers that the peer CTA or the
+// pair's MMAs arrive on); same contract as mbar_wait.
+static __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
+                                                         volatile int* abort, int* err, int err_bit) {
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*abort) return false;
+      if (globaltimer() - t0 > kWaitLimitNs) {
+        atomicOr(err, err_bit);
+        *abort = 1;
+        return false;
+      }
+    }
+  }
+}
+
+// Every thread of both CTAs: release this CTA's prior writes, wait for the peer.
+static __device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" :::
+               "memory");
+}
+
+// TMEM allocation shared by the CTA pair: one warp of each CTA executes these
+// together (same column count); both CTAs get the same TMEM address.
+static __device__ __forceinline__ void tmem_alloc_pair(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+}
+
+static __device__ __forceinline__ void tmem_relinquish_pair() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+
+static __device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+// 2-SM MMA issued by one thread of the pair's even CTA: A is split by rows (each
+// CTA's 128 rows at the same shared-memory offset), B by its N rows (first
+// half in the even CTA, second half in the odd one); each CTA's TMEM receives
+// its own 128 rows of D over all N columns.
+static __device__ __forceinline__ void mma_f16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                                    uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// Arrive on the mbarrier at offset `bar` of every CTA in `cta_mask` once the
+// pair MMAs issued so far by this thread have completed.
+static __device__ __forceinline__ void mma_commit_pair_mc(uint32_t bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], "
+      "%1;" ::"r"(bar),
+      "h"(cta_mask)
       : "memory");
 }
 

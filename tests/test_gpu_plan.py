@@ -25,10 +25,15 @@ def melt():
 def _plans():
     out = []
     for zb, pf in ((1, 0), (2, 2), (2, 4)):
-        out.append(dict(basis_resident=1, a_buffers=zb, prefetch_tiles=pf, basis_slots=0, ksteps_per_slot=1))
+        out.append(dict(basis_resident=1, a_buffers=zb, prefetch_tiles=pf, basis_slots=0, ksteps_per_slot=1,
+                        cta_pair=0))
     for pf, nb, kps in [(0, 2, 1), (1, 3, 2), (2, 2, 5), (2, 2, 8), (3, 2, 9), (2, 6, 1), (2, 2, 30)]:
-        out.append(dict(basis_resident=0, a_buffers=2, prefetch_tiles=pf, basis_slots=nb, ksteps_per_slot=kps))
-    out.append(dict(basis_resident=0, a_buffers=1, prefetch_tiles=2, basis_slots=12, ksteps_per_slot=1))
+        out.append(dict(basis_resident=0, a_buffers=2, prefetch_tiles=pf, basis_slots=nb, ksteps_per_slot=kps,
+                        cta_pair=0))
+    out.append(dict(basis_resident=0, a_buffers=1, prefetch_tiles=2, basis_slots=12, ksteps_per_slot=1, cta_pair=0))
+    for zb in (1, 2):   # CTA pairs (BF16 only): half of the basis per CTA, 2-SM MMAs
+        out.append(dict(basis_resident=1, a_buffers=zb, prefetch_tiles=0, basis_slots=0, ksteps_per_slot=1,
+                        cta_pair=1))
     return out
 
 
@@ -69,12 +74,13 @@ def test_every_plan_is_bit_identical(melt, prec, n_mels):
 
 def test_plan_round_trip_and_rejections(melt):
     fe = melt.Frontend(precision="bf16")
-    pl = dict(basis_resident=0, a_buffers=2, prefetch_tiles=3, basis_slots=3, ksteps_per_slot=4)
+    pl = dict(basis_resident=0, a_buffers=2, prefetch_tiles=3, basis_slots=3, ksteps_per_slot=4, cta_pair=0)
     melt.melt_plan_set(fe.handle, pl)
     assert melt.melt_plan_get(fe.handle) == pl
     for bad in [dict(pl, a_buffers=3), dict(pl, prefetch_tiles=-1), dict(pl, prefetch_tiles=5),
                 dict(pl, basis_slots=1), dict(pl, ksteps_per_slot=0),
-                dict(pl, basis_slots=32, ksteps_per_slot=40)]:
+                dict(pl, basis_slots=32, ksteps_per_slot=40), dict(pl, cta_pair=2),
+                dict(pl, cta_pair=1)]:          # a pair plan needs the resident basis
         with pytest.raises(melt.MeltError) as ei:
             melt.melt_plan_set(fe.handle, bad)
         assert ei.value.status == melt.MELT_ERR_UNSUPPORTED
