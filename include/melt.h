@@ -215,6 +215,33 @@ melt_status melt_forward_noalloc(melt_basis* basis, const float* wave, const int
                                  const int64_t* lengths, int batch, float* out, void* stream);
 
 /*
+ * melt_forward_host - melt_forward on a batch held in host memory: the same
+ *   features (Eq. 8 / Eq. 9), bit for bit, with the host<->device transfers
+ *   done by the library and overlapped with the kernels.  The batch is cut
+ *   into chunks of whole clips; each chunk's samples are copied to a device
+ *   slot, processed and its features copied back on one of four internal
+ *   streams, so the copies of some chunks run while others compute.
+ *   wave     host float[], clip b at wave[offsets[b] .. offsets[b]+lengths[b])
+ *            (page-locked memory lets the copies run asynchronously; any
+ *            host memory is accepted)
+ *   offsets  host int64[batch], multiples of 4, non-decreasing (NULL = packed
+ *            back to back at 4-float alignment, as for melt_forward)
+ *   lengths  host int64[batch]
+ *   out      host float[sum_b T_b * n_out]
+ *   stream   work already queued on `stream` happens before the copies, and
+ *            later work on `stream` happens after every feature is in `out`;
+ *            the call returns before that (synchronise `stream` before
+ *            reading `out` or reusing `wave`).
+ * The basis keeps the device slots, the four streams and the chunk plan of
+ * the last batch layout (they grow to the largest chunk seen and are freed
+ * by melt_destroy).  The correction MLP, if attached, is applied as in
+ * melt_forward.  MELT_ERR_ARG for bad pointers, lengths, unordered offsets or
+ * a basis of another device.
+ */
+melt_status melt_forward_host(melt_basis* basis, const float* wave, const int64_t* offsets,
+                              const int64_t* lengths, int batch, float* out, void* stream);
+
+/*
  * melt_forward_components - debug form: the raw projection (Eq. 6) for every
  * frame, out = device float[sum_b T_b * 2M]: per frame M values of R then M of I.
  * Only MELT_FP32 bases.  Arguments otherwise as melt_forward.

@@ -60,6 +60,7 @@ struct melt_basis {
   std::vector<TileDesc> plan;  // host scratch for planning
   int64_t plan_rows = 0;       // output rows of the planned batch
   const melt_mlp* correction = nullptr;  // applied in place after the log-Mel (not owned)
+  HostPipe* host_pipe = nullptr;         // melt_forward_host buffers and streams
 };
 
 namespace {
@@ -78,6 +79,7 @@ melt_status cuda_status(cudaError_t e) {
 
 void free_basis(melt_basis* b) {
   if (!b) return;
+  host_pipe_free(b->host_pipe);
   cudaFree(b->d_w32);
   cudaFree(b->d_dct);
   cudaFree(b->d_err);
@@ -376,6 +378,8 @@ melt_status launch_forward_tiles(melt_basis* b, const float* wave, const TileDes
 int basis_device(const melt_basis* b) { return b->device; }
 
 const melt_mlp* basis_correction(const melt_basis* b) { return b->correction; }
+
+HostPipe*& basis_host_pipe(melt_basis* b) { return b->host_pipe; }
 
 }  // namespace melt
 

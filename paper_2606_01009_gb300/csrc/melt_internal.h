@@ -81,3 +81,12 @@ int mlp_inputs(const melt_mlp* p);
 int mlp_device(const melt_mlp* p);
 
 }  // namespace melt
+
+// ---- host-buffer entry point (melt_host.cu): per-basis pipeline state
+namespace melt {
+struct HostPipe;
+// The basis's host pipeline slot (created on first use of melt_forward_host).
+HostPipe*& basis_host_pipe(melt_basis* b);
+// Release a pipeline (called when its basis is destroyed; NULL is a no-op).
+void host_pipe_free(HostPipe* hp);
+}  // namespace melt

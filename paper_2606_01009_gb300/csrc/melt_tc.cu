@@ -411,25 +411,31 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
     last_smem[last_i] = smem;
     last_i = (last_i + 1) & 3;
   }
-  if (!pair) {
-    const int grid = std::min(L.n_tiles, L.sm_count);
-    fn<<<grid, kThreads, smem, stream>>>(p);
-    return cudaGetLastError();
-  }
-  // CTA pairs: clusters of two, as many as can be resident at once (persistent)
-  p.n_pairs = (L.n_tiles + 1) / 2;
+  // Programmatic dependent launch: this grid may be scheduled while the
+  // previous kernel of the stream drains; the kernel orders its own global
+  // memory accesses after that kernel with griddepcontrol.wait.
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof(cfg));
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(kPThreads, 1, 1);
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = L.pdl ? 1 : 0;
   cfg.dynamicSmemBytes = (size_t)smem;
   cfg.stream = stream;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (!pair) {
+    cfg.gridDim = dim3(std::min(L.n_tiles, L.sm_count), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    return cudaLaunchKernelEx(&cfg, fn, p);
+  }
+  // CTA pairs: clusters of two, as many as can be resident at once (persistent)
+  p.n_pairs = (L.n_tiles + 1) / 2;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = 2;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kPThreads, 1, 1);
+  cfg.numAttrs = 2;
   TcBasis* mtb = const_cast<TcBasis*>(tb);
   if (mtb->pair_clusters < 0 || mtb->pair_smem != smem) {
     cfg.gridDim = dim3(2 * (L.sm_count / 2), 1, 1);

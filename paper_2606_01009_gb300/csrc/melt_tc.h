@@ -47,6 +47,7 @@ struct TcLaunch {
   float eps;
   int* err;
   int sm_count;
+  bool pdl = true;    // launch with programmatic stream serialisation
 };
 
 melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64);

@@ -416,7 +416,11 @@ __global__ void __launch_bounds__(kPThreads, 1) melt_tc_pair_kernel(const __grid
   cluster_sync_all();  // both CTAs' barriers exist before either arrives on the other's
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  if (threadIdx.x == 0) pdl_launch_dependents();
 
+  // MMA issuer and basis producer start at once (own data only); the roles
+  // that read tiles or the waveform, or write features, wait for the
+  // previous kernel of the stream first (programmatic dependent launch).
   if (warp == kPMmaWarp) {
     if (lane == 0) {
       if (c.rank == 0) pair_mma(p, gbase, c, B, tmem_base);
@@ -427,12 +431,15 @@ __global__ void __launch_bounds__(kPThreads, 1) melt_tc_pair_kernel(const __grid
     if (lane == 0) pair_basis_producer(p, c, B);
     __syncwarp();
   } else if (warp == kPProdWarp) {
+    pdl_wait();
     if (lane == 0) pair_wave_producer(p, c, B);
     __syncwarp();
   } else if (warp >= kPCvtWarp0) {
+    pdl_wait();
     pair_convert(p, c, B);
     __syncwarp();
   } else {
+    pdl_wait();
     pair_epilogue<NCH, MFCC>(p, gbase, c, B, tmem_base);
     __syncwarp();
   }

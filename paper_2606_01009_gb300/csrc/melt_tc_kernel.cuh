@@ -806,7 +806,12 @@ __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_const
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  if (threadIdx.x == 0) pdl_launch_dependents();
 
+  // The MMA issuer and the basis producer touch only this launch's own
+  // basis and shared memory, so they start at once; every role that reads
+  // the tile list, the waveform or writes features first waits for the
+  // previous kernel of the stream (programmatic dependent launch).
   if (warp == kMmaWarp) {
     if (lane == 0) role_mma<PREC>(p, gbase, sbase, B, tmem_base, abort);
     __syncwarp();
@@ -814,12 +819,14 @@ __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_const
     if (lane == 0) role_basis_producer(p, sbase, B, abort);
     __syncwarp();
   } else if (warp >= kCvtWarp0) {
+    pdl_wait();
     if constexpr (PREC == MELT_FP8E4M3)
       role_convert_fp8(p, gbase, sbase, B, abort);
     else
       role_convert_bf16<PREC>(p, sbase, B, abort);
     __syncwarp();
   } else {
+    pdl_wait();
     role_epilogue<PREC, NCH, MFCC>(p, gbase, sbase, B, tmem_base, abort);
     __syncwarp();
   }

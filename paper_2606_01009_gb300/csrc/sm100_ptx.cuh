@@ -243,6 +243,17 @@ static __device__ __forceinline__ void tmem_ld_wait(float (&a)[16], float (&b)[1
       : "memory");
 }
 
+// ------------------------------------------- programmatic dependent launch
+// Let the next kernel of the stream (launched with programmatic stream
+// serialisation) be scheduled as this grid's CTAs leave.
+static __device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Wait until the previous kernel of the stream has completed and its memory
+// is visible; a no-op when this grid was not launched early.
+static __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ------------------------------------------------- CTA pairs (cluster of 2)
 // Rank of this CTA in its cluster.
 static __device__ __forceinline__ uint32_t cluster_ctarank() {

@@ -53,6 +53,7 @@ SIGNATURES = {
     "melt_forward": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
     "melt_forward_components": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
     "melt_forward_noalloc": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
+    "melt_forward_host": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
     "melt_plan_get": (C.c_int, [_VP, _VP]),
     "melt_plan_set": (C.c_int, [_VP, _VP]),
     "melt_autotune": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP, C.c_int, _VP]),
@@ -208,6 +209,22 @@ def melt_forward_noalloc(basis, wave, offsets, lengths, out, stream=None):
     outp = out if isinstance(out, int) else out.data_ptr()
     _check(lib.melt_forward_noalloc(basis, C.c_void_p(wp), op, lp, int(lens.shape[0]), C.c_void_p(outp),
                                     _stream_ptr(stream)), "melt_forward_noalloc")
+
+
+def melt_forward_host(basis, wave, offsets, lengths, out, stream=None):
+    """wave/out: host buffers (numpy arrays or CPU torch tensors, pinned for async copies).
+
+    Asynchronous on `stream`: synchronise it before reading `out`."""
+    lens, lp = _i64(lengths)
+    offs, op = _i64(offsets)
+
+    def hptr(a):
+        return a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()
+
+    if isinstance(out, np.ndarray) and (out.dtype != np.float32 or not out.flags.c_contiguous):
+        raise ValueError("out must be a contiguous float32 array")
+    _check(lib.melt_forward_host(basis, C.c_void_p(hptr(wave)), op, lp, int(lens.shape[0]),
+                                 C.c_void_p(hptr(out)), _stream_ptr(stream)), "melt_forward_host")
 
 
 def melt_forward_components(basis, wave, offsets, lengths, out, stream=None):
