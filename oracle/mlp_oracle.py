@@ -60,6 +60,26 @@ def forward(params, x, mu, sd):
     return y, (x, xh, h, a)
 
 
+def forward_bf16(params, x, mu, sd):
+    """The model with the operand rounding of a BF16 tensor-core evaluation.
+
+    x-hat, W1, GELU(h) and W2 are rounded to bfloat16 (nearest-even) before
+    they enter a product; the products, the sums and everything else are exact
+    (FP64).  Returns (y, (xh_b, h, a_b, W1_b, W2_b)).  A BF16 evaluation
+    with FP32 accumulation differs from this only by its summation order and
+    by where FP32 rounding moves a value across a bfloat16 rounding boundary.
+    """
+    from oracle.melt_oracle import round_bf16
+    W1, b1, W2, b2 = (np.asarray(p, np.float64) for p in params)
+    x = np.asarray(x, np.float64)
+    xh_b = round_bf16((x - mu) / sd)
+    W1_b, W2_b = round_bf16(W1), round_bf16(W2)
+    h = xh_b @ W1_b.T + b1
+    a_b = round_bf16(gelu(h))
+    y = x + a_b @ W2_b.T + b2
+    return y, (xh_b, h, a_b, W1_b, W2_b)
+
+
 def loss(y, target) -> float:
     d = np.asarray(y, np.float64) - np.asarray(target, np.float64)
     return float(np.mean(d * d))

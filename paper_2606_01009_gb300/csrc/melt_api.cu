@@ -288,6 +288,7 @@ melt_status forward_impl(melt_basis* b, const float* wave, const int64_t* offset
   if (slot->n == 0) return MELT_OK;
   const int n_tiles = (int)slot->n;
   cudaError_t e;
+  bool fused = false;  // the kernel applied the correction itself
   if (b->precision == MELT_FP32 || mode == 1) {
     SimtParams p;
     p.wave = wave; p.tiles = slot->dev; p.n_tiles = n_tiles;
@@ -302,10 +303,12 @@ melt_status forward_impl(melt_basis* b, const float* wave, const int64_t* offset
     L.wave = wave; L.tiles = slot->dev; L.n_tiles = n_tiles; L.out = out;
     L.dct = b->d_dct; L.n_mfcc = b->n_mfcc; L.eps = (float)b->eps; L.err = b->d_err;
     L.sm_count = b->sm_count;
+    L.mlp = mode == 0 ? b->correction : nullptr;
+    L.fused = &fused;
     e = tc_launch(&b->tc, L, stream);
   }
   if (e != cudaSuccess) return cuda_status(e);
-  if (b->correction && mode == 0) {
+  if (b->correction && mode == 0 && !fused) {
     const melt_status st = mlp_apply(b->correction, out, out, slot->rows, stream);
     if (st != MELT_OK) return st;
   }
@@ -355,8 +358,9 @@ long long plan_tiles_into(const melt_basis* b, const int64_t* offsets, const int
 }
 
 melt_status launch_forward_tiles(melt_basis* b, const float* wave, const TileDesc* d_tiles,
-                                 int n_tiles, float* out, cudaStream_t stream) {
+                                 int n_tiles, float* out, int64_t rows, cudaStream_t stream) {
   cudaError_t e;
+  bool fused = false;
   if (b->precision == MELT_FP32) {
     SimtParams p;
     p.wave = wave; p.tiles = d_tiles; p.n_tiles = n_tiles;
@@ -370,9 +374,13 @@ melt_status launch_forward_tiles(melt_basis* b, const float* wave, const TileDes
     L.wave = wave; L.tiles = d_tiles; L.n_tiles = n_tiles; L.out = out;
     L.dct = b->d_dct; L.n_mfcc = b->n_mfcc; L.eps = (float)b->eps; L.err = b->d_err;
     L.sm_count = b->sm_count;
+    L.mlp = b->correction;
+    L.fused = &fused;
     e = tc_launch(&b->tc, L, stream);
   }
-  return cuda_status(e);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (b->correction && !fused) return mlp_apply(b->correction, out, out, rows, stream);
+  return MELT_OK;
 }
 
 int basis_device(const melt_basis* b) { return b->device; }
@@ -530,6 +538,23 @@ melt_status melt_basis_set_correction(melt_basis* b, const melt_mlp* mlp) {
     if (b->n_mfcc != 0) return MELT_ERR_UNSUPPORTED;  // the correction acts on log-Mel bands
     if (mlp_inputs(mlp) != b->n_mels || mlp_device(mlp) != b->device) return MELT_ERR_ARG;
   }
+  // the BF16 image for the fused epilogue is allocated here, so that forward
+  // calls (the allocation-free one included) allocate nothing
+  if (mlp && b->precision == MELT_BF16 && b->tc.d_b2 && mlp_fused_shape_ok(b->n_mels, mlp_hidden(mlp))) {
+    const long long half = mlp_fused_half_bytes(b->n_mels, mlp_hidden(mlp));
+    if (!b->tc.d_mlp_img || b->tc.mlp_half != half) {
+      MELT_CUDA(cudaDeviceSynchronize());  // no kernel may still read the old image
+      cudaFree(b->tc.d_mlp_img);
+      b->tc.d_mlp_img = nullptr;
+      b->tc.mlp_hd = 0;
+      MELT_CUDA(cudaMalloc(&b->tc.d_mlp_img, 2 * half));
+      b->tc.mlp_half = half;
+    }
+    b->tc.mlp_hd = mlp_hidden(mlp);
+  } else {
+    b->tc.mlp_hd = 0;
+  }
+  b->tc.pair_clusters = -1;  // the pair kernel's shared memory may have changed
   b->correction = mlp;
   return MELT_OK;
 }

@@ -77,7 +77,7 @@ melt_status launch_all(melt_group* g, const GroupEntry* e, cudaStream_t stream) 
   for (size_t k = 0; k < g->bases.size(); ++k) {
     if (e->count[k] == 0) continue;
     const melt_status st = launch_forward_tiles(g->bases[k], e->wave, e->d_tiles + e->first[k],
-                                                (int)e->count[k], e->out, stream);
+                                                (int)e->count[k], e->out, 0 /* grouped bases carry no correction */, stream);
     if (st != MELT_OK) return st;
   }
   return MELT_OK;

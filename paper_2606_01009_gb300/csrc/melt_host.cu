@@ -212,7 +212,6 @@ extern "C" melt_status melt_forward_host(melt_basis* b, const float* wave, const
   // every internal stream starts after the work already queued on `stream`
   HCUDA(cudaEventRecord(hp->start, stream));
   for (int i = 0; i < kHostSlots; ++i) HCUDA(cudaStreamWaitEvent(hp->streams[i], hp->start, 0));
-  const melt_mlp* corr = basis_correction(b);
   for (size_t k = 0; k < hp->chunks.size(); ++k) {
     const Chunk& ch = hp->chunks[k];
     const int s = (int)(k % kHostSlots);
@@ -220,13 +219,9 @@ extern "C" melt_status melt_forward_host(melt_basis* b, const float* wave, const
     HCUDA(cudaMemcpyAsync(hp->d_wave[s], wave + ch.span0, (size_t)(ch.span1 - ch.span0) * sizeof(float),
                           cudaMemcpyHostToDevice, cs));
     if (ch.tiles > 0) {
-      melt_status st = launch_forward_tiles(b, hp->d_wave[s], hp->d_tiles + ch.tile0, (int)ch.tiles,
-                                            hp->d_out[s], cs);
+      const melt_status st = launch_forward_tiles(b, hp->d_wave[s], hp->d_tiles + ch.tile0,
+                                                  (int)ch.tiles, hp->d_out[s], ch.rows, cs);
       if (st != MELT_OK) return st;
-      if (corr) {
-        st = mlp_apply(corr, hp->d_out[s], hp->d_out[s], ch.rows, cs);
-        if (st != MELT_OK) return st;
-      }
       HCUDA(cudaMemcpyAsync(out + ch.row0 * n_out, hp->d_out[s], (size_t)(ch.rows * n_out) * sizeof(float),
                             cudaMemcpyDeviceToHost, cs));
     }

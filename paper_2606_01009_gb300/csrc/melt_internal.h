@@ -56,9 +56,11 @@ namespace melt {
 long long plan_tiles_into(const melt_basis* b, const int64_t* offsets, const int64_t* lengths,
                           int batch, TileDesc* dst, long long cap);
 
-// Launches the basis's forward kernel over `n_tiles` device tile descriptors.
+// Launches the basis's forward kernel over `n_tiles` device tile descriptors
+// and applies the attached correction to the `rows` output rows (fused in the
+// kernel where the layout allows, else as a separate pass).
 melt_status launch_forward_tiles(melt_basis* b, const float* wave, const TileDesc* d_tiles,
-                                 int n_tiles, float* out, cudaStream_t stream);
+                                 int n_tiles, float* out, int64_t rows, cudaStream_t stream);
 
 // Frames of a clip of `len` samples under basis b: floor((len - N)/H) + 1, 0 if len < N.
 int64_t basis_frames(const melt_basis* b, int64_t len);
@@ -79,6 +81,13 @@ const melt_mlp* basis_correction(const melt_basis* b);
 melt_status mlp_apply(const melt_mlp* p, const float* x, float* y, long long n, cudaStream_t s);
 int mlp_inputs(const melt_mlp* p);
 int mlp_device(const melt_mlp* p);
+int mlp_hidden(const melt_mlp* p);
+// The correction fused in the CTA-pair kernel's epilogue: shapes it supports,
+// bytes of one CTA's half of its BF16 weight image, and the repacking of the
+// current FP32 parameters into that image (asynchronous on s).
+bool mlp_fused_shape_ok(int M, int Hd);
+long long mlp_fused_half_bytes(int M, int Hd);
+melt_status mlp_fused_image(const melt_mlp* p, void* d_img, cudaStream_t s);
 
 }  // namespace melt
 

@@ -29,6 +29,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "melt_internal.h"
 
 namespace {
@@ -418,6 +420,78 @@ melt_status check_batch(const melt_mlp* p, const float* X, const float* T, int b
 
 namespace melt {
 
+// ---- image of the MLP for the CTA-pair kernel's fused epilogue
+// Two halves, one per CTA of a pair; each half is
+//   W1 blocks  MP/16 K-steps x [2 core columns][Hd/2 rows][8 bf16]   rows n of W1
+//              from r*Hd/2 (hidden units), K = bands (zero past M)
+//   W2 blocks  Hd/16 K-steps x [2 core columns][MP/2 rows][8 bf16]   rows o of W2
+//              from r*MP/2 (bands, zero past M), K = hidden units
+//   vectors    FP32 b1[Hd], b2[MP], mu[MP], 1/sd[MP] (zero past M), padded to 128 B
+// The blocks are the no-swizzle K-major core-matrix layout of the tcgen05
+// B operand (rows 16 B apart, the two core columns of a K-step Hd/2*16 or
+// MP/2*16 bytes apart).
+bool mlp_fused_shape_ok(int M, int Hd) {
+  const int MP = (M + 15) / 16 * 16;
+  return M >= 1 && M <= 128 && Hd >= 32 && Hd <= 256 && Hd % 32 == 0 && MP <= Hd / 2 &&
+         (MP / 2) % 8 == 0;
+}
+
+long long mlp_fused_half_bytes(int M, int Hd) {
+  const int MP = (M + 15) / 16 * 16;
+  const long long w1 = (long long)(MP / 16) * 2 * (Hd / 2) * 16;
+  const long long w2 = (long long)(Hd / 16) * 2 * (MP / 2) * 16;
+  const long long vec = ((long long)(Hd + 3 * MP) * 4 + 127) / 128 * 128;
+  return w1 + w2 + vec;
+}
+
+__global__ void fused_image_kernel(const float* prm, const float* mu, const float* sd, int M, int Hd,
+                                   uint8_t* img, long long half) {
+  const int MP = (M + 15) / 16 * 16;
+  const long long w1b = (long long)(MP / 16) * 2 * (Hd / 2) * 8;  // bf16 elements
+  const long long w2b = (long long)(Hd / 16) * 2 * (MP / 2) * 8;
+  const int nvec = Hd + 3 * MP;
+  const long long per_half = w1b + w2b + nvec;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * per_half) return;
+  const int r = (int)(i / per_half);
+  long long e = i - (long long)r * per_half;
+  uint8_t* base = img + (long long)r * half;
+  const float* W1 = prm;
+  const float* b1 = W1 + (long long)Hd * M;
+  const float* W2 = b1 + Hd;
+  const float* b2 = W2 + (long long)M * Hd;
+  if (e < w1b) {
+    const int rows = Hd / 2;
+    const int s = (int)(e / (2 * rows * 8));
+    const int rem = (int)(e - (long long)s * 2 * rows * 8);
+    const int cc = rem / (rows * 8), row = (rem / 8) % rows, q = rem % 8;
+    const int n = r * rows + row, k = 16 * s + 8 * cc + q;
+    const float v = k < M ? W1[(long long)n * M + k] : 0.f;
+    reinterpret_cast<__nv_bfloat16*>(base)[e] = __float2bfloat16_rn(v);
+    return;
+  }
+  e -= w1b;
+  if (e < w2b) {
+    const int rows = MP / 2;
+    const int s = (int)(e / (2 * rows * 8));
+    const int rem = (int)(e - (long long)s * 2 * rows * 8);
+    const int cc = rem / (rows * 8), row = (rem / 8) % rows, q = rem % 8;
+    const int o = r * rows + row, k = 16 * s + 8 * cc + q;
+    const float v = o < M ? W2[(long long)o * Hd + k] : 0.f;
+    reinterpret_cast<__nv_bfloat16*>(base + w1b * 2)[e] = __float2bfloat16_rn(v);
+    return;
+  }
+  e -= w2b;
+  float* vec = reinterpret_cast<float*>(base + (w1b + w2b) * 2);
+  const int j = (int)e;
+  float v;
+  if (j < Hd) v = b1[j];
+  else if (j < Hd + MP) v = (j - Hd < M) ? b2[j - Hd] : 0.f;
+  else if (j < Hd + 2 * MP) v = (j - Hd - MP < M) ? mu[j - Hd - MP] : 0.f;
+  else v = (j - Hd - 2 * MP < M) ? 1.f / sd[j - Hd - 2 * MP] : 0.f;
+  vec[j] = v;
+}
+
 melt_status mlp_apply(const melt_mlp* p, const float* x, float* y, long long n, cudaStream_t s) {
   if (n <= 0) return MELT_OK;
   const float* W1 = p->d_params;
@@ -436,6 +510,20 @@ melt_status mlp_apply(const melt_mlp* p, const float* x, float* y, long long n, 
 }
 
 int mlp_inputs(const melt_mlp* p) { return p->M; }
+
+melt_status mlp_fused_image(const melt_mlp* p, void* d_img, cudaStream_t s) {
+  const int MP = (p->M + 15) / 16 * 16;
+  const long long per_half = (long long)(MP / 16) * 2 * (p->Hd / 2) * 8 +
+                             (long long)(p->Hd / 16) * 2 * (MP / 2) * 8 + p->Hd + 3 * MP;
+  const long long n = 2 * per_half;
+  fused_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+      p->d_params, p->d_mu, p->d_sd, p->M, p->Hd, static_cast<uint8_t*>(d_img),
+      mlp_fused_half_bytes(p->M, p->Hd));
+  return cudaGetLastError() == cudaSuccess ? MELT_OK : MELT_ERR_CUDA;
+}
+
+int mlp_hidden(const melt_mlp* p) { return p->Hd; }
+
 int mlp_device(const melt_mlp* p) { return p->device; }
 
 }  // namespace melt

@@ -64,8 +64,7 @@ extern "C" melt_status melt_forward_noalloc(melt_basis* basis, const float* wave
   if (cudaMemcpyAsync(g_dev_tiles[dev], g_host_tiles, (size_t)n * sizeof(TileDesc),
                       cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return MELT_ERR_CUDA;
-  const melt_status st = launch_forward_tiles(basis, wave, g_dev_tiles[dev], (int)n, out, stream);
-  if (st != MELT_OK || !basis_correction(basis)) return st;
   const TileDesc& last = g_host_tiles[n - 1];  // tiles are in output-row order
-  return mlp_apply(basis_correction(basis), out, out, last.out_row + last.n_frames, stream);
+  return launch_forward_tiles(basis, wave, g_dev_tiles[dev], (int)n, out,
+                              last.out_row + last.n_frames, stream);
 }

@@ -107,6 +107,7 @@ namespace {
 bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) {
   const int P = tb->precision;
   if (c.cta_pair != 0) return false;
+  p.Hd = 0;
   p.NS = p.CH = p.NCHUNK = 0;
   p.st_bytes = p.off_st = 0;
   p.b_lbo = (uint32_t)p.NC * 16;
@@ -163,6 +164,23 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
   p.step_bytes = p.kstep_bytes / 2;  // one K-step block of this CTA's N/2 basis rows
   p.bslot_bytes = p.step_bytes;
   p.b_lbo = (uint32_t)(p.NC / 2) * 16;
+  // fused correction MLP: its weight half in shared memory, one projection
+  // accumulator in TMEM and the MLP's operands beside it
+  p.Hd = tb->mlp_hd;
+  if (p.Hd > 0) {
+    // TMEM: accumulator [0, NC), x-hat [192, 192 + MP/2), H [256, 256 + Hd)
+    if (n_mfcc != 0 || p.NC > 192 || 256 + p.Hd > 512) return false;
+    p.mlp_half = (uint32_t)tb->mlp_half;
+    p.w1_step = (uint32_t)(p.Hd / 2) * 32;
+    p.w2_step = (uint32_t)(p.MP / 2) * 32;
+    p.mlp_w2_off = (uint32_t)(p.MP / 16) * p.w1_step;
+    p.mlp_vec_off = p.mlp_w2_off + (uint32_t)(p.Hd / 16) * p.w2_step;
+    p.a1_col = 192;
+    p.h_col = 256;
+    p.y_col = 256 + (uint32_t)p.Hd / 2;
+    p.idesc1 = idesc_f32acc(1u, 2 * kF, (uint32_t)p.Hd);
+    p.idesc2 = idesc_f32acc(1u, 2 * kF, (uint32_t)p.MP);
+  }
   // staging chunks: whole Z rows, <= 16 KB, <= what one converter pass covers
   const uint32_t row_bytes = (uint32_t)p.H * 4;
   const uint32_t span_bytes = row_bytes * p.zrows;
@@ -182,6 +200,8 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
     off += align_up(p.st_bytes * ns, 128);
     p.off_b = off;
     off += align_up(p.step_bytes * p.KS, 128);
+    p.off_mlp = off;
+    off += p.Hd > 0 ? align_up(p.mlp_half, 128) : 0u;
     p.off_bar = off;
     off += align_up(8 * B.total, 128);
     p.off_tab = off;
@@ -225,7 +245,10 @@ int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap
     for (int zb = 2; zb >= 1; --zb) {
       const melt_plan pc{1, zb, 0, p.KS, 1, 1};
       TcParams q = p;
-      if (n < cap && try_layout_pair(tb, q, pc, tb->n_mfcc) && q.NS >= 4) out[n++] = pc;
+      // with the correction fused, a pair layout with fewer slots still beats
+      // a separate pass of the MLP over the features
+      if (n < cap && try_layout_pair(tb, q, pc, tb->n_mfcc) && q.NS >= (tb->mlp_hd ? 2 : 4))
+        out[n++] = pc;
     }
   }
   add(1, 2, 2, p.KS, 1);
@@ -331,7 +354,9 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
 void tc_free(TcBasis* tb) {
   cudaFree(tb->d_b);
   cudaFree(tb->d_b2);
+  cudaFree(tb->d_mlp_img);
   tb->d_b = tb->d_b2 = nullptr;
+  tb->d_mlp_img = nullptr;
 }
 
 int tc_max_mfcc() { return kMaxMfccTc; }
@@ -393,10 +418,19 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
   p.eps = L.eps;
   p.n_mfcc = L.n_mfcc;
   p.n_out = L.n_mfcc ? L.n_mfcc : tb->n_mels;
-  KernelFn fn = pair ? kernel_for_pair(L.n_mfcc > 0, p.MP / 16)
-                     : (L.n_mfcc ? kernel_for_mfcc(tb->precision, p.MP / 16)
-                                 : kernel_for_plain(tb->precision, p.MP / 16));
+  const bool fused = pair && p.Hd > 0 && L.mlp != nullptr;
+  if (pair && p.Hd > 0 && !L.mlp) p.Hd = 0;  // plan made for a correction that is not passed
+  KernelFn fn = fused ? kernel_for_pair_mlp(p.MP / 16)
+                : pair ? kernel_for_pair(L.n_mfcc > 0, p.MP / 16)
+                       : (L.n_mfcc ? kernel_for_mfcc(tb->precision, p.MP / 16)
+                                   : kernel_for_plain(tb->precision, p.MP / 16));
   if (!fn) return cudaErrorInvalidValue;
+  if (fused) {
+    // the MLP's current parameters (training may have changed them) as BF16
+    p.mlp_img = static_cast<const uint8_t*>(tb->d_mlp_img);
+    if (mlp_fused_image(L.mlp, tb->d_mlp_img, stream) != MELT_OK) return cudaErrorLaunchFailure;
+  }
+  if (L.fused) *L.fused = fused;
   const int smem = (int)p.smem_total;
   static thread_local KernelFn last_fn[4] = {nullptr, nullptr, nullptr, nullptr};
   static thread_local int last_smem[4] = {0, 0, 0, 0};

@@ -26,6 +26,10 @@ struct TcBasis {
   int n_mfcc = 0;
   int pair_clusters = -1;  // co-resident 2-CTA clusters of the pair kernel (-1: not queried)
   int pair_smem = 0;       // shared memory size that count was queried for
+  // correction MLP fused in the CTA-pair kernel's epilogue (0 hidden units: none)
+  int mlp_hd = 0;
+  void* d_mlp_img = nullptr;  // BF16 weight image, two halves of mlp_half bytes
+  long long mlp_half = 0;
   bool forced = false;         // plan below was set explicitly (melt_plan_set / autotune)
   melt_plan plan = {};         // forced layout
 };
@@ -48,6 +52,8 @@ struct TcLaunch {
   int* err;
   int sm_count;
   bool pdl = true;    // launch with programmatic stream serialisation
+  const melt_mlp* mlp = nullptr;  // correction attached to the basis (fused when the layout allows)
+  bool* fused = nullptr;          // out: true when the kernel applied `mlp` itself
 };
 
 melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64);

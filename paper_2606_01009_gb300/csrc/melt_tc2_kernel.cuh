@@ -18,6 +18,16 @@
 //   warp  6     waveform producer: bulk copies of the tile's FP32 span into a ring
 //   warps 7-10  converters: staged FP32 samples -> polyphase Z rows (BF16)
 //
+// Fused correction MLP (template flag MLP).  After the log-Mel of a tile the
+// epilogue writes x-hat = (x - mu)/sd as BF16 into TMEM and the even CTA
+// issues two more 2-SM MMAs with the A operand in TMEM: H = x-hat W1^T
+// (W1 rows split between the CTAs like the basis) and, after the epilogue has
+// replaced H in place by GELU(H + b1) in BF16, Y = GELU(H) W2^T.  The
+// epilogue then stores x + Y + b2.  TMEM per CTA: the projection accumulator
+// (one, columns [0, NC)), x-hat at a1_col, H (and, in place, GELU(H)) at
+// h_col, Y at y_col inside H's upper half.  The next tile's projection MMAs
+// run while the epilogue works through the MLP of this one.
+//
 // Synchronisation.  Barriers that gate the pair's MMAs live in the even CTA
 // and count arrivals from both CTAs (the odd CTA arrives through its
 // shared::cluster address): Z buffers full (converters of both), accumulators
@@ -41,7 +51,8 @@ constexpr int kPCvtThreads = 32 * kPCvtWarps;              // 128
 constexpr int kPQuads = 8;  // float4s per converter thread per staged chunk (<= 16 KB)
 
 struct PairBars {
-  int s_full, s_empty, z_full, z_empty, b_full, peer_b, t_full, t_empty, drain, total;
+  int s_full, s_empty, z_full, z_empty, b_full, peer_b, t_full, t_empty, h_full, a2_full, y_full,
+      drain, total;
   __host__ __device__ PairBars(int NS, int ZB, int KS) {
     s_full = 0;
     s_empty = s_full + NS;
@@ -51,7 +62,10 @@ struct PairBars {
     peer_b = b_full + 1;  // the resident half basis completes on one barrier
     t_full = peer_b + 1;
     t_empty = t_full + 2;
-    drain = t_empty + 2;
+    h_full = t_empty + 2;  // fused MLP: hidden layer in TMEM
+    a2_full = h_full + 1;  //            GELU(H) written back (both CTAs' epilogues)
+    y_full = a2_full + 1;  //            MLP output in TMEM
+    drain = y_full + 1;
     total = drain + 1;
   }
 };
@@ -131,28 +145,58 @@ static __device__ void pair_basis_producer(const TcParams& p, const PairCtx& c, 
   const uint32_t total = p.step_bytes * (uint32_t)p.KS;
   const uint8_t* src = p.bimg + (size_t)c.rank * total;  // this CTA's half
   const uint32_t full = pbar(p, c, B.b_full);
-  mbar_arrive_expect_tx(full, total);
+  const uint32_t mlp = p.Hd > 0 ? p.mlp_half : 0u;       // fused MLP: this CTA's weight half
+  mbar_arrive_expect_tx(full, total + mlp);
   for (uint32_t o = 0; o < total; o += 32768u)
     bulk_g2s_hint(c.sbase + p.off_b + o, src + o, min(32768u, total - o), full, pol);
+  const uint8_t* msrc = p.mlp_img + (size_t)c.rank * mlp;
+  for (uint32_t o = 0; o < mlp; o += 32768u)
+    bulk_g2s_hint(c.sbase + p.off_mlp + o, msrc + o, min(32768u, mlp - o), full, pol);
   drain_wait(full, 0, p.err);
   if (c.rank == 1) mbar_arrive_cluster(mapa_shared(pbar(p, c, B.peer_b), 0));
 }
 
+// Fused MLP of the tile with ordinal j (even CTA's MMA thread): H = x-hat W1^T,
+// then, once both epilogues have written GELU(H) back, Y = GELU(H) W2^T.
+// x-hat of tile j is in TMEM: the caller has seen the epilogues' release of
+// tile j's accumulator, which follows the x-hat stores.
+static __device__ bool pair_mlp_gemms(const TcParams& p, const PairCtx& c, const PairBars& B,
+                                      uint32_t tmem_base, int j) {
+  const uint64_t hi = (uint64_t)p.desc_hi << 32;
+  const uint32_t w1 = ((c.sbase + p.off_mlp) >> 4) | ((((uint32_t)p.Hd / 2 * 16) >> 4) << 16);
+  const uint32_t w2 = ((c.sbase + p.off_mlp + p.mlp_w2_off) >> 4) | ((((uint32_t)p.MP / 2 * 16) >> 4) << 16);
+  const int ks1 = p.MP / 16, ks2 = p.Hd / 16;
+  tc_fence_after();
+  for (int s = 0; s < ks1; ++s)
+    mma_f16_pair_ts(tmem_base + p.h_col, tmem_base + p.a1_col + 8 * s, hi | (w1 + s * (p.w1_step >> 4)),
+                    p.idesc1, s > 0);
+  mma_commit_pair_mc(pbar(p, c, B.h_full), 3);
+  if (!mbar_wait_cluster(pbar(p, c, B.a2_full), j & 1, c.abort, p.err, kErrTimeout)) return false;
+  tc_fence_after();
+  for (int s = 0; s < ks2; ++s)
+    mma_f16_pair_ts(tmem_base + p.y_col, tmem_base + p.h_col + 8 * s, hi | (w2 + s * (p.w2_step >> 4)),
+                    p.idesc2, s > 0);
+  mma_commit_pair_mc(pbar(p, c, B.y_full), 3);
+  return true;
+}
+
 // Even CTA only: one thread issues every pair MMA.
+template <bool MLP>
 static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx& c,
                                 const PairBars& B, uint32_t tmem_base) {
   const uint2* tab = reinterpret_cast<const uint2*>(gbase + p.off_tab);
   const uint64_t hi = (uint64_t)p.desc_hi << 32;
   const uint32_t a_lo0 = ((c.sbase + p.off_a) >> 4) | ((p.lbo_a >> 4) << 16);
   const uint32_t abuf16 = p.abuf_bytes >> 4;
+  constexpr int nacc = MLP ? 1 : 2;  // the fused MLP's TMEM leaves room for one accumulator
   int k = 0;
   bool ok = true;
   for (int q = c.cluster; q < p.n_pairs; q += c.n_clusters, ++k) {
     const int zb = p.ZB == 2 ? (k & 1) : 0;
-    const int acc = k & 1;
+    const int acc = k % nacc;
     ok = mbar_wait_cluster(pbar(p, c, B.z_full + zb), (p.ZB == 2 ? (k >> 1) : k) & 1, c.abort, p.err,
                            kErrTimeout) &&
-         mbar_wait_cluster(pbar(p, c, B.t_empty + acc), ((k >> 1) & 1) ^ 1, c.abort, p.err,
+         mbar_wait_cluster(pbar(p, c, B.t_empty + acc), ((k / nacc) & 1) ^ 1, c.abort, p.err,
                            kErrTimeout);
     if (ok && k == 0)
       ok = mbar_wait(pbar(p, c, B.b_full), 0, c.abort, p.err, kErrTimeout) &&
@@ -176,6 +220,19 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
     }
     mma_commit_pair_mc(pbar(p, c, B.z_empty + zb), 3);
     mma_commit_pair_mc(pbar(p, c, B.t_full + acc), 3);
+    if constexpr (MLP) {
+      // the MLP of the previous tile, while this tile's projection runs
+      if (k > 0 && !pair_mlp_gemms(p, c, B, tmem_base, k - 1)) {
+        ok = false;
+        break;
+      }
+    }
+  }
+  if constexpr (MLP) {
+    // the last tile's MLP: wait for its x-hat (the release of its accumulator)
+    if (ok && k > 0 &&
+        mbar_wait_cluster(pbar(p, c, B.t_empty), (k - 1) & 1, c.abort, p.err, kErrTimeout))
+      pair_mlp_gemms(p, c, B, tmem_base, k - 1);
   }
   // no pair MMA may still be running when either CTA releases TMEM
   mma_commit_pair_mc(pbar(p, c, B.drain), 3);
@@ -350,7 +407,104 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
   }
 }
 
-template <int NCH, bool MFCC>
+// Epilogue with the fused correction MLP: log-Mel of the row (kept in
+// registers), x-hat to TMEM, GELU of the hidden layer in place, then
+// y = x + Y + b2 stored.  Every step is taken for an empty tile too (without
+// loads or stores) so that both CTAs keep the barrier phases in step.
+template <int NCH>
+__device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairCtx& c, const PairBars& B,
+                                  uint32_t tmem_base) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = 32 * warp + lane;
+  const float* vec = reinterpret_cast<const float*>(gbase + p.off_mlp + p.mlp_vec_off);
+  const float* b1 = vec;                 // [Hd]
+  const float* b2 = vec + p.Hd;          // [MP]
+  const float* mu = b2 + p.MP;           // [MP]
+  const float* isd = mu + p.MP;          // [MP]
+  const bool vec8 = ((p.n_out & 7) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 31) == 0);
+  const uint32_t tl = tmem_base + ((uint32_t)(32 * warp) << 16);  // this warp's lanes
+  int k = 0;
+  for (int q = c.cluster; q < p.n_pairs; q += c.n_clusters, ++k) {
+    const TileDesc td = pair_tile(p, c, q);
+    const bool live = td.n_frames > 0;
+    const bool valid = row < td.n_frames;
+    float* orow = p.out + (size_t)(td.out_row + row) * p.n_out;
+    // 1. log-Mel (Eq. 8) of the row, and x-hat in BF16 into TMEM
+    if (!warp_wait_cl(pbar(p, c, B.t_full), k & 1, c.abort, p.err)) break;
+    tc_fence_after();
+    float v[16 * NCH];
+    if (live) {
+#pragma unroll
+      for (int cc = 0; cc < NCH; ++cc) {
+        float re[16], im[16];
+        tmem_ld16(tl + 16 * cc, re);
+        tmem_ld16(tl + p.MP + 16 * cc, im);
+        tmem_ld_wait(re, im);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[16 * cc + e] = __logf(fmaf(re[e], re[e], fmaf(im[e], im[e], p.eps)));
+        uint32_t w[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int m = 16 * cc + 2 * e;
+          w[e] = pack_bf16((v[2 * e + 16 * cc] - mu[m]) * isd[m], (v[2 * e + 1 + 16 * cc] - mu[m + 1]) * isd[m + 1]);
+        }
+        tmem_st8(tl + p.a1_col + 8 * cc, w);
+      }
+      tmem_st_wait();
+    }
+    tc_fence_before();
+    warp_arrive_leader(pbar(p, c, B.t_empty));
+    // 2. hidden layer: GELU(H + b1) in BF16, written over H's lower half
+    if (!warp_wait_cl(pbar(p, c, B.h_full), k & 1, c.abort, p.err)) break;
+    tc_fence_after();
+    if (live) {
+#pragma unroll 1
+      for (int cc = 0; cc < p.Hd / 16; ++cc) {
+        float h[16];
+        tmem_ld16(tl + p.h_col + 16 * cc, h);
+        tmem_ld_wait();
+        reg_fence16(h);
+        uint32_t w[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float h0 = h[2 * e] + b1[16 * cc + 2 * e], h1 = h[2 * e + 1] + b1[16 * cc + 2 * e + 1];
+          w[e] = pack_bf16(0.5f * h0 * (1.f + erff(h0 * 0.70710678118654752f)),
+                           0.5f * h1 * (1.f + erff(h1 * 0.70710678118654752f)));
+        }
+        tmem_st8(tl + p.h_col + 8 * cc, w);
+      }
+      tmem_st_wait();
+    }
+    tc_fence_before();
+    warp_arrive_leader(pbar(p, c, B.a2_full));
+    // 3. y = x + Y + b2
+    if (!warp_wait_cl(pbar(p, c, B.y_full), k & 1, c.abort, p.err)) break;
+    tc_fence_after();
+    if (live) {
+#pragma unroll
+      for (int cc = 0; cc < NCH; ++cc) {
+        float y[16];
+        tmem_ld16(tl + p.y_col + 16 * cc, y);
+        tmem_ld_wait();
+        reg_fence16(y);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) y[e] = v[16 * cc + e] + y[e] + b2[16 * cc + e];
+        if (valid) {
+          if (vec8 && 16 * cc + 16 <= p.M) {
+            stg256(orow + 16 * cc, y);
+            stg256(orow + 16 * cc + 8, y + 8);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              if (16 * cc + e < p.M) orow[16 * cc + e] = y[e];
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int NCH, bool MFCC, bool MLP>
 __global__ void __launch_bounds__(kPThreads, 1) melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -382,6 +536,9 @@ __global__ void __launch_bounds__(kPThreads, 1) melt_tc_pair_kernel(const __grid
       mbar_init(bar(B.t_full + i), 1);
       mbar_init(bar(B.t_empty + i), 2 * kPEpiWarps);  // epilogues of both CTAs
     }
+    mbar_init(bar(B.h_full), 1);
+    mbar_init(bar(B.a2_full), 2 * kPEpiWarps);
+    mbar_init(bar(B.y_full), 1);
     mbar_init(bar(B.drain), 1);
     *c.abort = 0;
     fence_mbar_init();
@@ -423,7 +580,7 @@ __global__ void __launch_bounds__(kPThreads, 1) melt_tc_pair_kernel(const __grid
   // previous kernel of the stream first (programmatic dependent launch).
   if (warp == kPMmaWarp) {
     if (lane == 0) {
-      if (c.rank == 0) pair_mma(p, gbase, c, B, tmem_base);
+      if (c.rank == 0) pair_mma<MLP>(p, gbase, c, B, tmem_base);
       drain_wait(pbar(p, c, B.drain), 0, p.err);
     }
     __syncwarp();
@@ -440,7 +597,10 @@ __global__ void __launch_bounds__(kPThreads, 1) melt_tc_pair_kernel(const __grid
     __syncwarp();
   } else {
     pdl_wait();
-    pair_epilogue<NCH, MFCC>(p, gbase, c, B, tmem_base);
+    if constexpr (MLP)
+      pair_epilogue_mlp<NCH>(p, gbase, c, B, tmem_base);
+    else
+      pair_epilogue<NCH, MFCC>(p, gbase, c, B, tmem_base);
     __syncwarp();
   }
   tc_fence_before();
@@ -456,19 +616,35 @@ template <bool MFCC>
 KernelFn pick_pair_kernel(int nch) {
   if constexpr (!MFCC) {
     (void)nch;
-    return melt_tc_pair_kernel<1, false>;
+    return melt_tc_pair_kernel<1, false, false>;
   } else {
     switch (nch) {
-      case 1: return melt_tc_pair_kernel<1, true>;
-      case 2: return melt_tc_pair_kernel<2, true>;
-      case 3: return melt_tc_pair_kernel<3, true>;
-      case 4: return melt_tc_pair_kernel<4, true>;
-      case 5: return melt_tc_pair_kernel<5, true>;
-      case 6: return melt_tc_pair_kernel<6, true>;
-      case 7: return melt_tc_pair_kernel<7, true>;
-      case 8: return melt_tc_pair_kernel<8, true>;
+      case 1: return melt_tc_pair_kernel<1, true, false>;
+      case 2: return melt_tc_pair_kernel<2, true, false>;
+      case 3: return melt_tc_pair_kernel<3, true, false>;
+      case 4: return melt_tc_pair_kernel<4, true, false>;
+      case 5: return melt_tc_pair_kernel<5, true, false>;
+      case 6: return melt_tc_pair_kernel<6, true, false>;
+      case 7: return melt_tc_pair_kernel<7, true, false>;
+      case 8: return melt_tc_pair_kernel<8, true, false>;
       default: return nullptr;
     }
+  }
+}
+
+// Fused-MLP instantiations: log-Mel rows of 16 * nch bands (the fused shape
+// needs 2 MP <= Hd <= 256, so nch <= 8).
+inline KernelFn pick_pair_mlp_kernel(int nch) {
+  switch (nch) {
+    case 1: return melt_tc_pair_kernel<1, false, true>;
+    case 2: return melt_tc_pair_kernel<2, false, true>;
+    case 3: return melt_tc_pair_kernel<3, false, true>;
+    case 4: return melt_tc_pair_kernel<4, false, true>;
+    case 5: return melt_tc_pair_kernel<5, false, true>;
+    case 6: return melt_tc_pair_kernel<6, false, true>;
+    case 7: return melt_tc_pair_kernel<7, false, true>;
+    case 8: return melt_tc_pair_kernel<8, false, true>;
+    default: return nullptr;
   }
 }
 

@@ -105,6 +105,15 @@ struct TcParams {
   uint32_t off_st;
   uint32_t b_lbo;        // B operand: bytes between the two K core columns of a K-step block
   int n_pairs;           // tile pairs (tile 2q + rank of pair q goes to CTA `rank`)
+  // CTA-pair kernel with the correction MLP fused in its epilogue (Hd > 0)
+  const uint8_t* mlp_img;  // two halves of mlp_half bytes (W1 blocks, W2 blocks, vectors)
+  uint32_t mlp_half;
+  int Hd;                  // hidden units
+  uint32_t off_mlp;        // shared-memory offset of this CTA's half
+  uint32_t mlp_w2_off, mlp_vec_off;  // W2 blocks and FP32 vectors within a half
+  uint32_t w1_step, w2_step;         // bytes per K-step block of this CTA's W1 / W2 rows
+  uint32_t idesc1, idesc2;           // the two MLP GEMMs (M = 256, N = Hd / MP)
+  uint32_t a1_col, h_col, y_col;     // TMEM columns of x-hat, the hidden layer, the output
 };
 
 // barrier indices
@@ -865,6 +874,8 @@ KernelFn kernel_for_plain(int prec, int nch);
 KernelFn kernel_for_mfcc(int prec, int nch);
 // Defined in melt_tc2.cu: the CTA-pair kernel (BF16).
 KernelFn kernel_for_pair(bool mfcc, int nch);
+// Defined in melt_tc2_mlp.cu: the CTA-pair kernel with the fused correction MLP.
+KernelFn kernel_for_pair_mlp(int nch);
 
 }  // namespace tc
 }  // namespace melt
