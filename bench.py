@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grouped", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the mixed two-group 4096-clip batch (grouped graph vs per-clip launches)")
+    ap.add_argument("--correction", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the correction MLP: fused in the epilogue vs a separate pass")
     ap.add_argument("--forms", action=argparse.BooleanOptionalAction, default=True,
                     help="also time every other operand form")
     return ap.parse_args()
@@ -521,6 +523,56 @@ def time_grouped(args, dev, steps=20, warmup=3, per_clip_steps=2):
     return res
 
 
+def time_correction(args, W, dev, steps=200, warmup=5):
+    """BF16 log-Mel with the per-frame correction MLP (80 -> 256 -> 80) attached:
+    plain, fused in the kernel's epilogue, and as a separate FP32 pass after it."""
+    import torch
+    from paper_2606_01009_gb300 import inputs as G
+    from paper_2606_01009_gb300 import melt
+    cfg = W.cfg
+    fe = melt.Frontend(sr=cfg["sr"], n_fft=cfg["n_fft"], hop=cfg["hop"], n_mels=cfg["n_mels"],
+                       fmin=cfg["fmin"], fmax=cfg["fmax"], precision="bf16")
+    M, Hd = fe.n_out, 256
+    T = fe.total_frames(W.lens)
+    waves, outs, copies = W.device_copies(M, T)
+    stream = torch.cuda.current_stream(dev)
+    fe(waves[0], W.offs, W.lens, out=outs[0], stream=stream)
+    mlp = melt.melt_mlp_create(M, Hd, melt.pack_mlp_params(G.xavier_uniform(3, Hd, M, 0), np.zeros(Hd),
+                                                            G.xavier_uniform(3, M, Hd, 1), np.zeros(M)))
+    melt.melt_mlp_fit_stats(mlp, outs[0], T, stream)
+
+    def timed(fn):
+        for i in range(warmup):
+            fn(i)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(steps):
+            fn(i)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        fe.sync(stream)
+        return a.elapsed_time(b) / steps * 1e3
+
+    res = {"mlp": f"{M} -> {Hd} -> {M}, GELU", "frames_per_step": T}
+    res["plain_us"] = timed(lambda i: fe(waves[i % copies], W.offs, W.lens, out=outs[i % copies], stream=stream))
+
+    def separate(i):
+        o = outs[i % copies]
+        fe(waves[i % copies], W.offs, W.lens, out=o, stream=stream)
+        melt.melt_mlp_forward(mlp, o, o, T, stream)
+    res["separate_fp32_pass_us"] = timed(separate)
+    melt.melt_basis_set_correction(fe.handle, mlp)
+    res["fused_plan"] = melt.melt_plan_get(fe.handle)
+    res["fused_bf16_us"] = timed(lambda i: fe(waves[i % copies], W.offs, W.lens, out=outs[i % copies], stream=stream))
+    for k in ("plain", "separate_fp32_pass", "fused_bf16"):
+        res[k + "_frames_per_s"] = T / (res[k + "_us"] / 1e6)
+    melt.melt_basis_set_correction(fe.handle, None)
+    fe.close()
+    melt.melt_mlp_destroy(mlp)
+    return res
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -541,6 +593,12 @@ def main():
             res["cpu_baseline"] = cpu_oracle_baseline(W.clips, W.cfg, args.mfcc, args.cpu_seconds)
             ok = {k: v for k, v in forms.items() if "error" not in v}
             res["accuracy_db"], res["accuracy_sample"] = accuracy_vs_oracle(W, ok, W.cfg, args.mfcc)
+        if args.correction:
+            import torch
+            try:
+                res["correction"] = time_correction(args, W, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
+            except Exception as e:  # reported, not fatal: the headline line above stands
+                res["correction"] = {"error": str(e)}
         if args.grouped:
             import torch
             try:

@@ -432,7 +432,7 @@ namespace melt {
 // MP/2*16 bytes apart).
 bool mlp_fused_shape_ok(int M, int Hd) {
   const int MP = (M + 15) / 16 * 16;
-  return M >= 1 && M <= 128 && Hd >= 32 && Hd <= 256 && Hd % 32 == 0 && MP <= Hd / 2 &&
+  return M >= 1 && MP <= 80 && Hd >= 64 && Hd <= 256 && Hd % 32 == 0 && MP <= Hd / 2 &&
          (MP / 2) % 8 == 0;
 }
 

@@ -168,16 +168,17 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
   // accumulator in TMEM and the MLP's operands beside it
   p.Hd = tb->mlp_hd;
   if (p.Hd > 0) {
-    // TMEM: accumulator [0, NC), x-hat [192, 192 + MP/2), H [256, 256 + Hd)
-    if (n_mfcc != 0 || p.NC > 192 || 256 + p.Hd > 512) return false;
+    if (n_mfcc != 0 || p.NC > 160 || 160 + p.MP > 256 || 256 + p.Hd > 512) return false;
     p.mlp_half = (uint32_t)tb->mlp_half;
     p.w1_step = (uint32_t)(p.Hd / 2) * 32;
     p.w2_step = (uint32_t)(p.MP / 2) * 32;
     p.mlp_w2_off = (uint32_t)(p.MP / 16) * p.w1_step;
     p.mlp_vec_off = p.mlp_w2_off + (uint32_t)(p.Hd / 16) * p.w2_step;
+    // TMEM: accumulator [0, NC), Y [160, 160 + MP) (over x-hat [192, 192 + MP/2),
+    // which GEMM1 has consumed by then), H and, in place, GELU(H) [256, 256 + Hd)
     p.a1_col = 192;
     p.h_col = 256;
-    p.y_col = 256 + (uint32_t)p.Hd / 2;
+    p.y_col = 160;
     p.idesc1 = idesc_f32acc(1u, 2 * kF, (uint32_t)p.Hd);
     p.idesc2 = idesc_f32acc(1u, 2 * kF, (uint32_t)p.MP);
   }
@@ -468,7 +469,7 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
   attr[1].val.clusterDim.x = 2;
   attr[1].val.clusterDim.y = 1;
   attr[1].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(kPThreads, 1, 1);
+  cfg.blockDim = dim3(pair_threads(fused), 1, 1);
   cfg.numAttrs = 2;
   TcBasis* mtb = const_cast<TcBasis*>(tb);
   if (mtb->pair_clusters < 0 || mtb->pair_smem != smem) {

@@ -11,21 +11,23 @@
 // Each CTA's TMEM receives R and I of its own frames, so the epilogue is the
 // single-CTA one.
 //
-// Warp roles per CTA (11 warps):
-//   warps 0-3   epilogue: TMEM -> registers, R^2 + I^2, log, (DCT), store
-//   warp  4     TMEM allocation for the pair; in the even CTA, the MMA issuer
-//   warp  5     basis producer: this CTA's half of the basis, once
-//   warp  6     waveform producer: bulk copies of the tile's FP32 span into a ring
-//   warps 7-10  converters: staged FP32 samples -> polyphase Z rows (BF16)
+// Warp roles per CTA (11 warps; 15 with the fused MLP):
+//   warps 0-3   epilogue: TMEM -> registers, R^2 + I^2, log, (DCT), store (with
+//               the fused MLP, warps 0-7: warps e and e+4 read the same 32 TMEM
+//               lanes (frames) and split the columns, bands and hidden units)
+//   next warp   TMEM allocation for the pair; in the even CTA, the MMA issuer
+//   next warp   basis producer: this CTA's half of the basis, once
+//   next warp   waveform producer: bulk copies of the tile's FP32 span into a ring
+//   last four   converters: staged FP32 samples -> polyphase Z rows (BF16)
 //
 // Fused correction MLP (template flag MLP).  After the log-Mel of a tile the
 // epilogue writes x-hat = (x - mu)/sd as BF16 into TMEM and the even CTA
-// issues two more 2-SM MMAs with the A operand in TMEM: H = x-hat W1^T
-// (W1 rows split between the CTAs like the basis) and, after the epilogue has
-// replaced H in place by GELU(H + b1) in BF16, Y = GELU(H) W2^T.  The
-// epilogue then stores x + Y + b2.  TMEM per CTA: the projection accumulator
-// (one, columns [0, NC)), x-hat at a1_col, H (and, in place, GELU(H)) at
-// h_col, Y at y_col inside H's upper half.  The next tile's projection MMAs
+// issues two more 2-SM MMAs with the A operand in TMEM: H = x-hat W1^T (W1
+// rows split between the CTAs like the basis) and, after the epilogue has
+// written GELU(H + b1) in BF16 over H, Y = GELU(H) W2^T.  The epilogue stores
+// x + Y + b2.  TMEM per CTA: the projection accumulator (one, columns
+// [0, NC)), Y at y_col over x-hat at a1_col (consumed by then), H and GELU(H)
+// at h_col.  The next tile's projection MMAs
 // run while the epilogue works through the MLP of this one.
 //
 // Synchronisation.  Barriers that gate the pair's MMAs live in the even CTA
@@ -40,14 +42,13 @@
 namespace melt {
 namespace tc {
 
-constexpr int kPEpiWarps = 4;
-constexpr int kPMmaWarp = 4;
-constexpr int kPBWarp = 5;
-constexpr int kPProdWarp = 6;
-constexpr int kPCvtWarp0 = 7;
+// Warp layout of a pair kernel with `epw` epilogue warps (4, or 8 with the
+// fused MLP): epilogue 0..epw-1, MMA epw, basis epw+1, waveform epw+2,
+// converters epw+3 .. epw+6.
 constexpr int kPCvtWarps = 4;
-constexpr int kPThreads = 32 * (kPCvtWarp0 + kPCvtWarps);  // 352
-constexpr int kPCvtThreads = 32 * kPCvtWarps;              // 128
+constexpr int kPCvtThreads = 32 * kPCvtWarps;  // 128
+__host__ __device__ constexpr int pair_epi_warps(bool mlp) { return mlp ? 8 : 4; }
+__host__ __device__ constexpr int pair_threads(bool mlp) { return 32 * (pair_epi_warps(mlp) + 7); }
 constexpr int kPQuads = 8;  // float4s per converter thread per staged chunk (<= 16 KB)
 
 struct PairBars {
@@ -156,25 +157,40 @@ static __device__ void pair_basis_producer(const TcParams& p, const PairCtx& c, 
   if (c.rank == 1) mbar_arrive_cluster(mapa_shared(pbar(p, c, B.peer_b), 0));
 }
 
-// Fused MLP of the tile with ordinal j (even CTA's MMA thread): H = x-hat W1^T,
-// then, once both epilogues have written GELU(H) back, Y = GELU(H) W2^T.
-// x-hat of tile j is in TMEM: the caller has seen the epilogues' release of
-// tile j's accumulator, which follows the x-hat stores.
-static __device__ bool pair_mlp_gemms(const TcParams& p, const PairCtx& c, const PairBars& B,
-                                      uint32_t tmem_base, int j) {
+// TMEM column of the packed GELU(H) of hidden chunk cc (16 units) in the
+// fused MLP.  GELU(H) is written over H itself: the two epilogue warps of a
+// lane quarter take hidden chunks [0, F) and [F, nH) (F = ceil(nH/2)), in
+// order, and each stores chunk cc only into H columns it has already read:
+// 8 cc for the first warp, 8 cc + 8 F for the second.
+static __device__ __forceinline__ uint32_t gelu_col(const TcParams& p, int cc) {
+  const int nh = p.Hd / 16, first = (nh + 1) / 2;
+  return p.h_col + 8u * cc + (cc >= first ? 8u * first : 0u);
+}
+
+// Fused MLP (even CTA's MMA thread), hidden layer: H = x-hat W1^T.  The
+// caller has seen the epilogues' release of the tile's accumulator, which
+// follows the x-hat stores.
+static __device__ void pair_mlp_gemm1(const TcParams& p, const PairCtx& c, const PairBars& B,
+                                      uint32_t tmem_base) {
   const uint64_t hi = (uint64_t)p.desc_hi << 32;
   const uint32_t w1 = ((c.sbase + p.off_mlp) >> 4) | ((((uint32_t)p.Hd / 2 * 16) >> 4) << 16);
-  const uint32_t w2 = ((c.sbase + p.off_mlp + p.mlp_w2_off) >> 4) | ((((uint32_t)p.MP / 2 * 16) >> 4) << 16);
-  const int ks1 = p.MP / 16, ks2 = p.Hd / 16;
   tc_fence_after();
-  for (int s = 0; s < ks1; ++s)
+  for (int s = 0; s < p.MP / 16; ++s)
     mma_f16_pair_ts(tmem_base + p.h_col, tmem_base + p.a1_col + 8 * s, hi | (w1 + s * (p.w1_step >> 4)),
                     p.idesc1, s > 0);
   mma_commit_pair_mc(pbar(p, c, B.h_full), 3);
+}
+
+// Fused MLP, output layer of the tile with ordinal j: once both CTAs'
+// epilogues have written GELU(H + b1) back, Y = GELU(H) W2^T.
+static __device__ bool pair_mlp_gemm2(const TcParams& p, const PairCtx& c, const PairBars& B,
+                                      uint32_t tmem_base, int j) {
+  const uint64_t hi = (uint64_t)p.desc_hi << 32;
+  const uint32_t w2 = ((c.sbase + p.off_mlp + p.mlp_w2_off) >> 4) | ((((uint32_t)p.MP / 2 * 16) >> 4) << 16);
   if (!mbar_wait_cluster(pbar(p, c, B.a2_full), j & 1, c.abort, p.err, kErrTimeout)) return false;
   tc_fence_after();
-  for (int s = 0; s < ks2; ++s)
-    mma_f16_pair_ts(tmem_base + p.y_col, tmem_base + p.h_col + 8 * s, hi | (w2 + s * (p.w2_step >> 4)),
+  for (int s = 0; s < p.Hd / 16; ++s)
+    mma_f16_pair_ts(tmem_base + p.y_col, tmem_base + gelu_col(p, s), hi | (w2 + s * (p.w2_step >> 4)),
                     p.idesc2, s > 0);
   mma_commit_pair_mc(pbar(p, c, B.y_full), 3);
   return true;
@@ -194,10 +210,16 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
   for (int q = c.cluster; q < p.n_pairs; q += c.n_clusters, ++k) {
     const int zb = p.ZB == 2 ? (k & 1) : 0;
     const int acc = k % nacc;
-    ok = mbar_wait_cluster(pbar(p, c, B.z_full + zb), (p.ZB == 2 ? (k >> 1) : k) & 1, c.abort, p.err,
-                           kErrTimeout) &&
-         mbar_wait_cluster(pbar(p, c, B.t_empty + acc), ((k / nacc) & 1) ^ 1, c.abort, p.err,
+    ok = mbar_wait_cluster(pbar(p, c, B.t_empty + acc), ((k / nacc) & 1) ^ 1, c.abort, p.err,
                            kErrTimeout);
+    if constexpr (MLP) {
+      // the previous tile's x-hat is in TMEM (its accumulator was just
+      // released): its hidden layer goes to the tensor cores first, so the
+      // epilogue can start on GELU while this tile's projection runs
+      if (ok && k > 0) pair_mlp_gemm1(p, c, B, tmem_base);
+    }
+    ok = ok && mbar_wait_cluster(pbar(p, c, B.z_full + zb), (p.ZB == 2 ? (k >> 1) : k) & 1, c.abort,
+                                 p.err, kErrTimeout);
     if (ok && k == 0)
       ok = mbar_wait(pbar(p, c, B.b_full), 0, c.abort, p.err, kErrTimeout) &&
            mbar_wait_cluster(pbar(p, c, B.peer_b), 0, c.abort, p.err, kErrTimeout);
@@ -221,8 +243,8 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
     mma_commit_pair_mc(pbar(p, c, B.z_empty + zb), 3);
     mma_commit_pair_mc(pbar(p, c, B.t_full + acc), 3);
     if constexpr (MLP) {
-      // the MLP of the previous tile, while this tile's projection runs
-      if (k > 0 && !pair_mlp_gemms(p, c, B, tmem_base, k - 1)) {
+      // the previous tile's output layer, once its GELU(H) is written
+      if (k > 0 && !pair_mlp_gemm2(p, c, B, tmem_base, k - 1)) {
         ok = false;
         break;
       }
@@ -231,8 +253,10 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
   if constexpr (MLP) {
     // the last tile's MLP: wait for its x-hat (the release of its accumulator)
     if (ok && k > 0 &&
-        mbar_wait_cluster(pbar(p, c, B.t_empty), (k - 1) & 1, c.abort, p.err, kErrTimeout))
-      pair_mlp_gemms(p, c, B, tmem_base, k - 1);
+        mbar_wait_cluster(pbar(p, c, B.t_empty), (k - 1) & 1, c.abort, p.err, kErrTimeout)) {
+      pair_mlp_gemm1(p, c, B, tmem_base);
+      pair_mlp_gemm2(p, c, B, tmem_base, k - 1);
+    }
   }
   // no pair MMA may still be running when either CTA releases TMEM
   mma_commit_pair_mc(pbar(p, c, B.drain), 3);
@@ -243,8 +267,8 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
 // (lanes read consecutive quads: conflict-free); quad hq is the low or high
 // half (hq & 1) of the Z row segment (row ul, 8-sample group kc) with
 // 8 * (hq >> 1) = (ul - ch*CH) H + 8 kc.
-static __device__ void pair_convert(const TcParams& p, const PairCtx& c, const PairBars& B) {
-  const int ct = threadIdx.x - 32 * kPCvtWarp0;
+static __device__ void pair_convert(const TcParams& p, const PairCtx& c, const PairBars& B, int cvt0) {
+  const int ct = threadIdx.x - 32 * cvt0;
   const int H8 = p.H >> 3;
   const int nq_full = p.CH * (p.H >> 2);
   uint32_t qoff[kPQuads];
@@ -310,14 +334,26 @@ static __device__ void pair_convert(const TcParams& p, const PairCtx& c, const P
   }
 }
 
-template <int NCH, bool MFCC>
+// Columns of a row split between the warps that share a lane quarter: with
+// two, 16-column chunks [lo, hi) of n for half h (the first half takes the
+// odd one); with one, all of them.
+static __device__ __forceinline__ void half_chunks(int n, int halves, int h, int& lo, int& hi) {
+  const int first = halves == 2 ? (n + 1) / 2 : n;
+  lo = h ? first : 0;
+  hi = h ? n : first;
+}
+
+template <int NCH, bool MFCC, int EPW>
 __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& c, const PairBars& B,
                               uint32_t tmem_base) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = 32 * warp + lane;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int row = 32 * quarter + lane;
   const float* dct = reinterpret_cast<const float*>(gbase + p.off_dct);
   const bool vec8 = ((p.n_out & 7) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 31) == 0);
   const int nch = p.MP >> 4;
+  int c_lo, c_hi;
+  half_chunks(nch, EPW / 4, half, c_lo, c_hi);
   int k = 0;
   for (int q = c.cluster; q < p.n_pairs; q += c.n_clusters, ++k) {
     const int acc = k & 1;
@@ -325,20 +361,21 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
     if (!warp_wait_cl(pbar(p, c, B.t_full + acc), (k >> 1) & 1, c.abort, p.err)) break;
     tc_fence_after();
     const bool valid = row < td.n_frames;
-    const uint32_t t0 = tmem_base + ((uint32_t)(32 * warp) << 16) + acc * p.acc_stride;
+    const uint32_t t0 = tmem_base + ((uint32_t)(32 * quarter) << 16) + acc * p.acc_stride;
     float* orow = p.out + (size_t)(td.out_row + row) * p.n_out;
-    if (td.n_frames == 0) {  // empty tile: nothing to read
+    // an empty tile, or the second half of the MFCC epilogue (the DCT needs whole rows): no reads
+    if (td.n_frames == 0 || (MFCC && half == 1)) {
       tc_fence_before();
       warp_arrive_leader(pbar(p, c, B.t_empty + acc));
       continue;
     }
     if constexpr (!MFCC) {
 #pragma unroll 1
-      for (int c0 = 0; c0 < nch; c0 += kEpiGroup) {
+      for (int c0 = c_lo; c0 < c_hi; c0 += kEpiGroup) {
         float re[kEpiGroup][16], im[kEpiGroup][16];
 #pragma unroll
         for (int g = 0; g < kEpiGroup; ++g) {
-          if (c0 + g < nch) {
+          if (c0 + g < c_hi) {
             tmem_ld16(t0 + 16 * (c0 + g), re[g]);
             tmem_ld16(t0 + p.MP + 16 * (c0 + g), im[g]);
           }
@@ -349,14 +386,14 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
           reg_fence16(re[g]);
           reg_fence16(im[g]);
         }
-        if (c0 + kEpiGroup >= nch) {
+        if (c0 + kEpiGroup >= c_hi) {
           tc_fence_before();
           warp_arrive_leader(pbar(p, c, B.t_empty + acc));
         }
 #pragma unroll
         for (int g = 0; g < kEpiGroup; ++g) {
           const int cc = c0 + g;
-          if (cc < nch) {
+          if (cc < c_hi) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
               const float r = re[g][e], i = im[g][e];
@@ -374,6 +411,10 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
             }
           }
         }
+      }
+      if (c_lo >= c_hi) {  // nothing to read (a single-chunk row goes to the first half)
+        tc_fence_before();
+        warp_arrive_leader(pbar(p, c, B.t_empty + acc));
       }
     } else {
       float lm[16 * NCH];
@@ -407,96 +448,119 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
   }
 }
 
+// GELU(h) = h Phi(h) = 0.5 h (1 + erf(h / sqrt 2)) (exact-erf form, as trained).
+static __device__ __forceinline__ float gelu_erf(float h) {
+  return 0.5f * h * (1.f + erff(h * 0.70710678118654752f));
+}
+
 // Epilogue with the fused correction MLP: log-Mel of the row (kept in
-// registers), x-hat to TMEM, GELU of the hidden layer in place, then
-// y = x + Y + b2 stored.  Every step is taken for an empty tile too (without
+// registers), x-hat to TMEM, GELU of the hidden layer over H, then
+// y = x + Y + b2 stored.  The two warps of a lane quarter split the bands and
+// the hidden units.  Every step is taken for an empty tile too (without
 // loads or stores) so that both CTAs keep the barrier phases in step.
 template <int NCH>
 __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairCtx& c, const PairBars& B,
                                   uint32_t tmem_base) {
+  constexpr int NV = (NCH + 1) / 2;  // band chunks of the larger half
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = 32 * warp + lane;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int row = 32 * quarter + lane;
   const float* vec = reinterpret_cast<const float*>(gbase + p.off_mlp + p.mlp_vec_off);
   const float* b1 = vec;                 // [Hd]
   const float* b2 = vec + p.Hd;          // [MP]
   const float* mu = b2 + p.MP;           // [MP]
   const float* isd = mu + p.MP;          // [MP]
   const bool vec8 = ((p.n_out & 7) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 31) == 0);
-  const uint32_t tl = tmem_base + ((uint32_t)(32 * warp) << 16);  // this warp's lanes
+  const uint32_t tl = tmem_base + ((uint32_t)(32 * quarter) << 16);  // this warp's lanes
+  int c_lo, c_hi, h_lo, h_hi;
+  half_chunks(NCH, 2, half, c_lo, c_hi);
+  half_chunks(p.Hd / 16, 2, half, h_lo, h_hi);
   int k = 0;
   for (int q = c.cluster; q < p.n_pairs; q += c.n_clusters, ++k) {
     const TileDesc td = pair_tile(p, c, q);
     const bool live = td.n_frames > 0;
     const bool valid = row < td.n_frames;
     float* orow = p.out + (size_t)(td.out_row + row) * p.n_out;
-    // 1. log-Mel (Eq. 8) of the row, and x-hat in BF16 into TMEM
+    // 1. log-Mel (Eq. 8) of this half of the row, and its x-hat in BF16 into TMEM
     if (!warp_wait_cl(pbar(p, c, B.t_full), k & 1, c.abort, p.err)) break;
     tc_fence_after();
-    float v[16 * NCH];
+    float v[16 * NV];
     if (live) {
 #pragma unroll
-      for (int cc = 0; cc < NCH; ++cc) {
-        float re[16], im[16];
-        tmem_ld16(tl + 16 * cc, re);
-        tmem_ld16(tl + p.MP + 16 * cc, im);
-        tmem_ld_wait(re, im);
+      for (int g = 0; g < NV; ++g) {
+        if (c_lo + g < c_hi) {  // one chunk per wait: the row's log values stay in registers
+          const int cc = c_lo + g;
+          float re[16], im[16];
+          tmem_ld16(tl + 16 * cc, re);
+          tmem_ld16(tl + p.MP + 16 * cc, im);
+          tmem_ld_wait(re, im);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) v[16 * cc + e] = __logf(fmaf(re[e], re[e], fmaf(im[e], im[e], p.eps)));
-        uint32_t w[8];
+          for (int e = 0; e < 16; ++e) v[16 * g + e] = __logf(fmaf(re[e], re[e], fmaf(im[e], im[e], p.eps)));
+          uint32_t w[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int m = 16 * cc + 2 * e;
-          w[e] = pack_bf16((v[2 * e + 16 * cc] - mu[m]) * isd[m], (v[2 * e + 1 + 16 * cc] - mu[m + 1]) * isd[m + 1]);
+          for (int e = 0; e < 8; ++e) {
+            const int m = 16 * cc + 2 * e;
+            w[e] = pack_bf16((v[16 * g + 2 * e] - mu[m]) * isd[m], (v[16 * g + 2 * e + 1] - mu[m + 1]) * isd[m + 1]);
+          }
+          tmem_st8(tl + p.a1_col + 8 * cc, w);
         }
-        tmem_st8(tl + p.a1_col + 8 * cc, w);
       }
       tmem_st_wait();
     }
     tc_fence_before();
     warp_arrive_leader(pbar(p, c, B.t_empty));
-    // 2. hidden layer: GELU(H + b1) in BF16, written over H's lower half
+    // 2. hidden layer: GELU(H + b1) in BF16, written over H (see gelu_col), two chunks per wait
     if (!warp_wait_cl(pbar(p, c, B.h_full), k & 1, c.abort, p.err)) break;
     tc_fence_after();
     if (live) {
 #pragma unroll 1
-      for (int cc = 0; cc < p.Hd / 16; ++cc) {
-        float h[16];
-        tmem_ld16(tl + p.h_col + 16 * cc, h);
-        tmem_ld_wait();
-        reg_fence16(h);
-        uint32_t w[8];
+      for (int c0 = h_lo; c0 < h_hi; c0 += 2) {
+        float h[2][16];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const float h0 = h[2 * e] + b1[16 * cc + 2 * e], h1 = h[2 * e + 1] + b1[16 * cc + 2 * e + 1];
-          w[e] = pack_bf16(0.5f * h0 * (1.f + erff(h0 * 0.70710678118654752f)),
-                           0.5f * h1 * (1.f + erff(h1 * 0.70710678118654752f)));
+        for (int t = 0; t < 2; ++t)
+          if (c0 + t < h_hi) tmem_ld16(tl + p.h_col + 16 * (c0 + t), h[t]);
+        tmem_ld_wait();
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          reg_fence16(h[t]);
+          const int cc = c0 + t;
+          if (cc < h_hi) {
+            uint32_t w[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              w[e] = pack_bf16(gelu_erf(h[t][2 * e] + b1[16 * cc + 2 * e]),
+                               gelu_erf(h[t][2 * e + 1] + b1[16 * cc + 2 * e + 1]));
+            tmem_st8(tl + gelu_col(p, cc), w);
+          }
         }
-        tmem_st8(tl + p.h_col + 8 * cc, w);
       }
       tmem_st_wait();
     }
     tc_fence_before();
     warp_arrive_leader(pbar(p, c, B.a2_full));
-    // 3. y = x + Y + b2
+    // 3. y = x + Y + b2 for this half's bands
     if (!warp_wait_cl(pbar(p, c, B.y_full), k & 1, c.abort, p.err)) break;
     tc_fence_after();
     if (live) {
 #pragma unroll
-      for (int cc = 0; cc < NCH; ++cc) {
-        float y[16];
-        tmem_ld16(tl + p.y_col + 16 * cc, y);
-        tmem_ld_wait();
-        reg_fence16(y);
+      for (int g = 0; g < NV; ++g) {
+        const int cc = c_lo + g;
+        if (cc < c_hi) {
+          float y[16];
+          tmem_ld16(tl + p.y_col + 16 * cc, y);
+          tmem_ld_wait();
+          reg_fence16(y);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) y[e] = v[16 * cc + e] + y[e] + b2[16 * cc + e];
-        if (valid) {
-          if (vec8 && 16 * cc + 16 <= p.M) {
-            stg256(orow + 16 * cc, y);
-            stg256(orow + 16 * cc + 8, y + 8);
-          } else {
+          for (int e = 0; e < 16; ++e) y[e] = v[16 * g + e] + y[e] + b2[16 * cc + e];
+          if (valid) {
+            if (vec8 && 16 * cc + 16 <= p.M) {
+              stg256(orow + 16 * cc, y);
+              stg256(orow + 16 * cc + 8, y + 8);
+            } else {
 #pragma unroll
-            for (int e = 0; e < 16; ++e)
-              if (16 * cc + e < p.M) orow[16 * cc + e] = y[e];
+              for (int e = 0; e < 16; ++e)
+                if (16 * cc + e < p.M) orow[16 * cc + e] = y[e];
+            }
           }
         }
       }
@@ -505,7 +569,9 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
 }
 
 template <int NCH, bool MFCC, bool MLP>
-__global__ void __launch_bounds__(kPThreads, 1) melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
+  constexpr int EPW = pair_epi_warps(MLP);
+  constexpr int kPMmaWarp = EPW, kPBWarp = EPW + 1, kPProdWarp = EPW + 2, kPCvtWarp0 = EPW + 3;
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 127u) & ~127u;
@@ -534,10 +600,10 @@ __global__ void __launch_bounds__(kPThreads, 1) melt_tc_pair_kernel(const __grid
     mbar_init(bar(B.peer_b), 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(bar(B.t_full + i), 1);
-      mbar_init(bar(B.t_empty + i), 2 * kPEpiWarps);  // epilogues of both CTAs
+      mbar_init(bar(B.t_empty + i), 2 * EPW);  // epilogues of both CTAs
     }
     mbar_init(bar(B.h_full), 1);
-    mbar_init(bar(B.a2_full), 2 * kPEpiWarps);
+    mbar_init(bar(B.a2_full), 2 * EPW);
     mbar_init(bar(B.y_full), 1);
     mbar_init(bar(B.drain), 1);
     *c.abort = 0;
@@ -560,9 +626,9 @@ __global__ void __launch_bounds__(kPThreads, 1) melt_tc_pair_kernel(const __grid
     tmem_relinquish_pair();
   }
   if constexpr (MFCC) {
-    if (warp < kPEpiWarps) {
+    if (warp < EPW) {
       float* dct = reinterpret_cast<float*>(gbase + p.off_dct);
-      for (int i = threadIdx.x; i < p.n_mfcc * p.MP; i += 32 * kPEpiWarps) {
+      for (int i = threadIdx.x; i < p.n_mfcc * p.MP; i += 32 * EPW) {
         const int kk = i / p.MP, m = i - kk * p.MP;
         dct[i] = m < p.M ? p.dct[kk * p.M + m] : 0.f;
       }
@@ -593,14 +659,14 @@ __global__ void __launch_bounds__(kPThreads, 1) melt_tc_pair_kernel(const __grid
     __syncwarp();
   } else if (warp >= kPCvtWarp0) {
     pdl_wait();
-    pair_convert(p, c, B);
+    pair_convert(p, c, B, kPCvtWarp0);
     __syncwarp();
   } else {
     pdl_wait();
     if constexpr (MLP)
       pair_epilogue_mlp<NCH>(p, gbase, c, B, tmem_base);
     else
-      pair_epilogue<NCH, MFCC>(p, gbase, c, B, tmem_base);
+      pair_epilogue<NCH, MFCC, EPW>(p, gbase, c, B, tmem_base);
     __syncwarp();
   }
   tc_fence_before();
@@ -632,8 +698,8 @@ KernelFn pick_pair_kernel(int nch) {
   }
 }
 
-// Fused-MLP instantiations: log-Mel rows of 16 * nch bands (the fused shape
-// needs 2 MP <= Hd <= 256, so nch <= 8).
+// Fused-MLP instantiations: log-Mel rows of 16 * nch bands (the fused TMEM
+// layout holds M <= 80, so nch <= 5).
 inline KernelFn pick_pair_mlp_kernel(int nch) {
   switch (nch) {
     case 1: return melt_tc_pair_kernel<1, false, true>;
@@ -641,9 +707,6 @@ inline KernelFn pick_pair_mlp_kernel(int nch) {
     case 3: return melt_tc_pair_kernel<3, false, true>;
     case 4: return melt_tc_pair_kernel<4, false, true>;
     case 5: return melt_tc_pair_kernel<5, false, true>;
-    case 6: return melt_tc_pair_kernel<6, false, true>;
-    case 7: return melt_tc_pair_kernel<7, false, true>;
-    case 8: return melt_tc_pair_kernel<8, false, true>;
     default: return nullptr;
   }
 }
