@@ -134,7 +134,7 @@ melt_status melt_basis_get_fp64(const melt_basis* basis, double* freqs, double* 
  *                    spent on them)
  *   basis_slots      streamed-basis ring slots (ignored when resident)
  *   ksteps_per_slot  basis K-steps (16 samples each; FP8: 32) per streamed slot
- *   cta_pair         1 (BF16 only): clusters of two CTAs share each MMA
+ *   cta_pair         1 (BF16 and FP8): clusters of two CTAs share each MMA
  *                    (tcgen05 cta_group::2, 256 frames); each CTA keeps half
  *                    of the basis resident (basis_resident must be 1) and
  *                    stages its waveform span through a ring of bulk copies

@@ -153,7 +153,10 @@ bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) 
 // CTA's half of the basis (resident), then barriers and tables.  The ring
 // takes every slot that still fits (2..8).
 bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) {
-  if (c.cta_pair != 1 || tb->precision != MELT_BF16 || !tb->d_b2) return false;
+  const bool fp8 = tb->precision == MELT_FP8E4M3;
+  if (c.cta_pair != 1 || (tb->precision != MELT_BF16 && !fp8) || !tb->d_b2) return false;
+  // FP8: a frame's 16-sample groups must not straddle staged chunks
+  if (fp8 && (p.H % 16) != 0) return false;
   if (c.basis_resident != 1 || c.a_buffers < 1 || c.a_buffers > 2) return false;
   if (c.prefetch_tiles < 0 || c.prefetch_tiles > kMaxPrefetch) return false;
   p.b_resident = 1;
@@ -166,7 +169,7 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
   p.b_lbo = (uint32_t)(p.NC / 2) * 16;
   // fused correction MLP: its weight half in shared memory, one projection
   // accumulator in TMEM and the MLP's operands beside it
-  p.Hd = tb->mlp_hd;
+  p.Hd = fp8 ? 0 : tb->mlp_hd;
   if (p.Hd > 0) {
     if (n_mfcc != 0 || p.NC > 160 || 160 + p.MP > 256 || 256 + p.Hd > 512) return false;
     p.mlp_half = (uint32_t)tb->mlp_half;
@@ -192,7 +195,8 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
   p.CH = ch;
   p.NCHUNK = (p.zrows + ch - 1) / ch;
   p.st_bytes = row_bytes * ch;
-  for (int ns = 8; ns >= 2; --ns) {
+  if (fp8 && ch < p.J - 1) return false;  // the streaming FP8 converter frees chunk ch-1 after chunk ch
+  for (int ns = 8; ns >= (fp8 ? 3 : 2); --ns) {
     const PairBars B(ns, p.ZB, p.KS);
     uint32_t off = 0;
     p.off_a = off;
@@ -209,7 +213,10 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
     off += align_up(8 * p.KS, 128);
     p.off_misc = off;
     off += 128;
-    p.off_scale = p.off_rowmax = off;
+    p.off_scale = off;  // FP8: per-frame scale ring, then row maxima and frame multipliers
+    off += fp8 ? kScaleRing * kF * 4 : 0u;
+    p.off_rowmax = off;
+    off += fp8 ? align_up((2 * p.zrows + kF) * 4, 128) : 0u;
     p.off_dct = off;
     off += align_up(4 * n_mfcc * p.MP, 128);
     if (off + 128 > kSmemLimit) continue;
@@ -217,7 +224,7 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
     p.smem_total = off + 128;
     p.tmem_cols = p.NC <= 32 ? 64 : p.NC <= 64 ? 128 : p.NC <= 128 ? 256 : 512;
     p.acc_stride = p.tmem_cols / 2;
-    p.idesc = idesc_f32acc(1u, 2 * kF, p.NC);  // M = 256 over the pair
+    p.idesc = idesc_f32acc(fp8 ? 0u : 1u, 2 * kF, p.NC);  // M = 256 over the pair
     p.desc_hi = (128u >> 4) | (1u << 14);
     return true;
   }
@@ -242,13 +249,17 @@ int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap
   if (tb->precision == MELT_BF16 && tb->d_b2) {
     // CTA pairs first where the staging ring keeps >= 4 slots (measured on the
     // 64 x 30 s batch: 44 us vs 50 us single-CTA at M = 80; with 2 slots at
-    // M = 128 the pair is slower than a single CTA, 71 vs 62 us)
+    // M = 128 the pair is slower than a single CTA, 71 vs 62 us).  FP8 pairs
+    // are a plan a caller may set: their four converter warps quantise every
+    // frame separately (per-frame scales) and are latency bound, 470 us vs
+    // 161 us for the single-CTA FP8 kernel on the same batch.
     for (int zb = 2; zb >= 1; --zb) {
       const melt_plan pc{1, zb, 0, p.KS, 1, 1};
       TcParams q = p;
       // with the correction fused, a pair layout with fewer slots still beats
       // a separate pass of the MLP over the features
-      if (n < cap && try_layout_pair(tb, q, pc, tb->n_mfcc) && q.NS >= (tb->mlp_hd ? 2 : 4))
+      if (n < cap && try_layout_pair(tb, q, pc, tb->n_mfcc) &&
+          q.NS >= (tb->mlp_hd && tb->precision == MELT_BF16 ? 2 : 4))
         out[n++] = pc;
     }
   }
@@ -333,7 +344,7 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
   if (cudaMalloc(&tb->d_b, img.size()) != cudaSuccess) return MELT_ERR_OOM;
   if (cudaMemcpy(tb->d_b, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return MELT_ERR_CUDA;
-  if (P == MELT_BF16) {
+  if (P == MELT_BF16 || P == MELT_FP8E4M3) {
     // CTA-pair image: the K-step blocks of basis rows [0, MP) (W_r), then those
     // of rows [MP, 2 MP) (W_i); each block is 2 core columns x MP rows x 16 B
     const size_t half_step = (size_t)MP * 32;
@@ -422,7 +433,8 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
   const bool fused = pair && p.Hd > 0 && L.mlp != nullptr;
   if (pair && p.Hd > 0 && !L.mlp) p.Hd = 0;  // plan made for a correction that is not passed
   KernelFn fn = fused ? kernel_for_pair_mlp(p.MP / 16)
-                : pair ? kernel_for_pair(L.n_mfcc > 0, p.MP / 16)
+                : pair ? (tb->precision == MELT_FP8E4M3 ? kernel_for_pair_fp8(L.n_mfcc > 0, p.MP / 16)
+                                                        : kernel_for_pair(L.n_mfcc > 0, p.MP / 16))
                        : (L.n_mfcc ? kernel_for_mfcc(tb->precision, p.MP / 16)
                                    : kernel_for_plain(tb->precision, p.MP / 16));
   if (!fn) return cudaErrorInvalidValue;

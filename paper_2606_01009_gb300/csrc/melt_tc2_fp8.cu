@@ -1,0 +1,11 @@
+// Instantiations of the CTA-pair tensor-core MelT kernel with FP8 e4m3
+// operands and per-frame scales.
+#include "melt_tc2_kernel.cuh"
+
+namespace melt {
+namespace tc {
+
+KernelFn kernel_for_pair_fp8(bool mfcc, int nch) { return pick_pair_fp8_kernel<>(mfcc, nch); }
+
+}  // namespace tc
+}  // namespace melt

@@ -1,7 +1,8 @@
 // Device side of the CTA-pair tensor-core MelT kernel (BF16), included by
 // melt_tc2.cu.
 #pragma once
-// The pair kernel runs as clusters of two CTAs on neighbouring SMs.  The even
+// The pair kernel (BF16 and FP8 e4m3) runs as clusters of two CTAs on
+// neighbouring SMs.  The even
 // CTA issues 2-SM MMAs (tcgen05 cta_group::2, M = 256): each CTA supplies the
 // A operand of its own 128-frame tile, and the basis B is split by its rows
 // between the two, so each CTA keeps only half of it (W_r rows in the even
@@ -53,7 +54,7 @@ constexpr int kPQuads = 8;  // float4s per converter thread per staged chunk (<=
 
 struct PairBars {
   int s_full, s_empty, z_full, z_empty, b_full, peer_b, t_full, t_empty, h_full, a2_full, y_full,
-      drain, total;
+      sc_full, drain, total;
   __host__ __device__ PairBars(int NS, int ZB, int KS) {
     s_full = 0;
     s_empty = s_full + NS;
@@ -66,7 +67,8 @@ struct PairBars {
     h_full = t_empty + 2;  // fused MLP: hidden layer in TMEM
     a2_full = h_full + 1;  //            GELU(H) written back (both CTAs' epilogues)
     y_full = a2_full + 1;  //            MLP output in TMEM
-    drain = y_full + 1;
+    sc_full = y_full + 1;  // FP8: per-frame scales of a tile ready (kScaleRing deep)
+    drain = sc_full + kScaleRing;
     total = drain + 1;
   }
 };
@@ -197,7 +199,7 @@ static __device__ bool pair_mlp_gemm2(const TcParams& p, const PairCtx& c, const
 }
 
 // Even CTA only: one thread issues every pair MMA.
-template <bool MLP>
+template <bool MLP, int PREC>
 static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx& c,
                                 const PairBars& B, uint32_t tmem_base) {
   const uint2* tab = reinterpret_cast<const uint2*>(gbase + p.off_tab);
@@ -238,7 +240,12 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
                      : "r"(tab_s + 8u * min(s0 + u, p.KS - 1)));
 #pragma unroll
       for (int u = 0; u < 8; ++u)
-        if (s0 + u < p.KS) mma_f16_pair(d, hi | (alo + tx[u]), hi | ty[u], p.idesc, s0 + u > 0);
+        if (s0 + u < p.KS) {
+          if constexpr (PREC == MELT_FP8E4M3)
+            mma_f8_pair(d, hi | (alo + tx[u]), hi | ty[u], p.idesc, s0 + u > 0);
+          else
+            mma_f16_pair(d, hi | (alo + tx[u]), hi | ty[u], p.idesc, s0 + u > 0);
+        }
     }
     mma_commit_pair_mc(pbar(p, c, B.z_empty + zb), 3);
     mma_commit_pair_mc(pbar(p, c, B.t_full + acc), 3);
@@ -334,6 +341,118 @@ static __device__ void pair_convert(const TcParams& p, const PairCtx& c, const P
   }
 }
 
+// FP8 converter: staged FP32 chunks -> quantised frame rows (im2col inside
+// shared memory only), with the frame's scale 448 / amax(frame).
+//
+// Frame f uses Z rows f .. f+J-1 (the last only up to KL = N - (J-1) H).  As
+// chunk ch of the span (Z rows [ch CH, (ch+1) CH)) arrives, the warps reduce
+// max |x| of its rows, then scale and quantise every frame whose rows are all
+// present (f < (ch+1) CH - J + 1, or all at the last chunk), and release chunk
+// ch-1, which no remaining frame needs (CH >= J - 1).  A warp takes one frame
+// at a time: lane l converts float4 number l + 32 i of the frame's samples
+// (consecutive lanes, consecutive 16 bytes) and stores its 4 e4m3 bytes at
+// core column (l + 32 i) / 4 of the frame's row, byte 4 ((l + 32 i) % 4); the
+// core-column pitch lbo_a = 2064 bytes puts the 32 lanes on 32 banks.  A
+// frame lies in at most two chunks, whose ring slots it looks up once.
+// Named barriers take the AND of the warps' wait results, so all four warps
+// leave together when a wait gives up.
+static __device__ void pair_convert_fp8(const TcParams& p, uint8_t* gbase, const PairCtx& c,
+                                        const PairBars& B, int cvt0) {
+  const int ct = threadIdx.x - 32 * cvt0;
+  const int cw = ct >> 5, lane = threadIdx.x & 31;
+  const int KL = p.N - (p.J - 1) * p.H;
+  const int nq = p.KS * 8;                    // float4s per frame row, zero past N
+  const int h4 = p.H >> 2;
+  const int chunk_samples = p.CH * p.H;
+  unsigned* rowmax = reinterpret_cast<unsigned*>(gbase + p.off_rowmax);  // [zrows] float bits
+  unsigned* rowpre = rowmax + p.zrows;                                   // [zrows]
+  float* scales = reinterpret_cast<float*>(gbase + p.off_scale);
+  const uint32_t st0 = c.sbase + p.off_st;
+  int g = 0;  // chunks consumed so far (ring position)
+  int k = 0;
+  for (int qp = c.cluster; qp < p.n_pairs; qp += c.n_clusters, ++k) {
+    const int zb = p.ZB == 2 ? (k & 1) : 0;
+    bool ok = warp_wait_cl(pbar(p, c, B.z_empty + zb), ((p.ZB == 2 ? (k >> 1) : k) & 1) ^ 1, c.abort, p.err);
+    if (!named_barrier_and(1, kPCvtThreads, ok)) break;
+    const TileDesc td = pair_tile(p, c, qp);
+    const int nsamp = td.n_samples;
+    const uint32_t abase = c.sbase + p.off_a + zb * p.abuf_bytes;
+    if (td.n_frames > 0) {
+      int f_done = 0;
+      for (int ch = 0; ch < p.NCHUNK; ++ch) {
+        const int slot = (g + ch) % p.NS;
+        ok = warp_wait(pbar(p, c, B.s_full + slot), ((g + ch) / p.NS) & 1, c.abort, p.err);
+        ok = named_barrier_and(1, kPCvtThreads, ok);  // every warp takes the same decision
+        if (!ok) break;
+        // 1. max |x| over each row of the chunk and over its first KL samples
+        const uint32_t sp = st0 + (uint32_t)slot * p.st_bytes;
+        const int r0 = ch * p.CH, rows = min(p.CH, p.zrows - r0);
+        for (int rl = cw; rl < rows; rl += kPCvtWarps) {
+          unsigned mf = 0u, mp = 0u;
+          for (int j = lane; j < h4; j += 32) {
+            float4 v;
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                         : "r"(sp + 16u * (uint32_t)(rl * h4 + j)));
+            clip_quad(v, (r0 + rl) * p.H + 4 * j, nsamp);
+            const unsigned m = __float_as_uint(fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+            mf = max(mf, m);
+            if (4 * j < KL) mp = max(mp, m);
+          }
+          mf = __reduce_max_sync(0xffffffffu, mf);
+          mp = __reduce_max_sync(0xffffffffu, mp);
+          if (lane == 0) {
+            rowmax[r0 + rl] = mf;
+            rowpre[r0 + rl] = mp;
+          }
+        }
+        named_barrier(1, kPCvtThreads);
+        // 2. the frames whose rows are all present now: scale and quantised row
+        const int f_hi = ch == p.NCHUNK - 1 ? kF : min(kF, (ch + 1) * p.CH - p.J + 1);
+        for (int f = f_done + cw; f < f_hi; f += kPCvtWarps) {
+          unsigned am = rowpre[f + p.J - 1];
+          for (int j = 0; j < p.J - 1; ++j) am = max(am, rowmax[f + j]);
+          const float amax = __uint_as_float(am);
+          const bool pos = amax > 0.f;
+          const float inv = pos ? 448.f / amax : 1.f;
+          if (lane == 0) scales[(k % kScaleRing) * kF + f] = (pos ? amax / 448.f : 1.f) / 448.f;
+          // the frame's samples: [s0, s0 + N) of the span, in chunks c0 and c0 + 1
+          const int s0 = f * p.H;
+          const int c0 = s0 / chunk_samples;
+          const int split = (c0 + 1) * chunk_samples - s0;  // samples before the next chunk
+          const uint32_t base0 = st0 + (uint32_t)((g + c0) % p.NS) * p.st_bytes + 4u * (uint32_t)(s0 - c0 * chunk_samples);
+          const uint32_t base1 = st0 + (uint32_t)((g + c0 + 1) % p.NS) * p.st_bytes;
+          const uint32_t arow = abase + (uint32_t)f * 16u;
+#pragma unroll 4
+          for (int j = lane; j < nq; j += 32) {
+            const int n = 4 * j;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (n < p.N) {
+              const uint32_t a = n < split ? base0 + 4u * (uint32_t)n : base1 + 4u * (uint32_t)(n - split);
+              asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                           : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                           : "r"(a));
+              clip_quad(v, s0 + n, nsamp);
+            }
+            const uint32_t w = pack_e4m3x4(v.x * inv, v.y * inv, v.z * inv, v.w * inv);
+            asm volatile("st.shared.b32 [%0], %1;" ::"r"(arow + (uint32_t)(j >> 2) * p.lbo_a + 4u * (uint32_t)(j & 3)),
+                         "r"(w));
+          }
+        }
+        named_barrier(1, kPCvtThreads);
+        if (ch > 0) warp_arrive(pbar(p, c, B.s_empty + (g + ch - 1) % p.NS));
+        f_done = f_hi;
+      }
+      if (!ok) break;
+      warp_arrive(pbar(p, c, B.s_empty + (g + p.NCHUNK - 1) % p.NS));
+      g += p.NCHUNK;
+    }
+    fence_proxy_async();
+    warp_arrive_leader(pbar(p, c, B.z_full + zb));
+    warp_arrive(pbar(p, c, B.sc_full + (k % kScaleRing)));
+  }
+}
+
 // Columns of a row split between the warps that share a lane quarter: with
 // two, 16-column chunks [lo, hi) of n for half h (the first half takes the
 // odd one); with one, all of them.
@@ -343,9 +462,10 @@ static __device__ __forceinline__ void half_chunks(int n, int halves, int h, int
   hi = h ? n : first;
 }
 
-template <int NCH, bool MFCC, int EPW>
+template <int NCH, bool MFCC, int EPW, int PREC>
 __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& c, const PairBars& B,
                               uint32_t tmem_base) {
+  const float* scales = reinterpret_cast<const float*>(gbase + p.off_scale);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3, half = warp >> 2;
   const int row = 32 * quarter + lane;
@@ -359,6 +479,12 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
     const int acc = k & 1;
     const TileDesc td = pair_tile(p, c, q);
     if (!warp_wait_cl(pbar(p, c, B.t_full + acc), (k >> 1) & 1, c.abort, p.err)) break;
+    float sc = 1.f;  // FP8: s_t / 448 of the frame (sample and basis scales)
+    if constexpr (PREC == MELT_FP8E4M3) {
+      if (!warp_wait(pbar(p, c, B.sc_full + (k % kScaleRing)), (k / kScaleRing) & 1, c.abort, p.err))
+        break;
+      sc = scales[(k % kScaleRing) * kF + row];
+    }
     tc_fence_after();
     const bool valid = row < td.n_frames;
     const uint32_t t0 = tmem_base + ((uint32_t)(32 * quarter) << 16) + acc * p.acc_stride;
@@ -396,7 +522,7 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
           if (cc < c_hi) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-              const float r = re[g][e], i = im[g][e];
+              const float r = re[g][e] * sc, i = im[g][e] * sc;
               re[g][e] = __logf(fmaf(r, r, fmaf(i, i, p.eps)));
             }
             if (valid) {
@@ -426,7 +552,8 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
         tmem_ld_wait(re, im);
 #pragma unroll
         for (int e = 0; e < 16; ++e)
-          lm[16 * cc + e] = (16 * cc + e < p.M) ? __logf(fmaf(re[e], re[e], im[e] * im[e]) + p.eps) : 0.f;
+          lm[16 * cc + e] =
+              (16 * cc + e < p.M) ? __logf(fmaf(re[e] * sc, re[e] * sc, (im[e] * sc) * (im[e] * sc)) + p.eps) : 0.f;
       }
       tc_fence_before();
       warp_arrive_leader(pbar(p, c, B.t_empty + acc));
@@ -568,7 +695,7 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
   }
 }
 
-template <int NCH, bool MFCC, bool MLP>
+template <int NCH, bool MFCC, bool MLP, int PREC = MELT_BF16>
 __global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
   constexpr int EPW = pair_epi_warps(MLP);
   constexpr int kPMmaWarp = EPW, kPBWarp = EPW + 1, kPProdWarp = EPW + 2, kPCvtWarp0 = EPW + 3;
@@ -605,6 +732,7 @@ __global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(cons
     mbar_init(bar(B.h_full), 1);
     mbar_init(bar(B.a2_full), 2 * EPW);
     mbar_init(bar(B.y_full), 1);
+    for (int i = 0; i < kScaleRing; ++i) mbar_init(bar(B.sc_full + i), kPCvtWarps);
     mbar_init(bar(B.drain), 1);
     *c.abort = 0;
     fence_mbar_init();
@@ -614,11 +742,16 @@ __global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(cons
     uint2* tab = reinterpret_cast<uint2*>(gbase + p.off_tab);
     const uint32_t b_lo0 = ((sbase + p.off_b) >> 4) | ((p.b_lbo >> 4) << 16);
     const uint32_t step16 = p.step_bytes >> 4;
-    for (int j = 0, s0 = 0; j < p.J; ++j) {
-      const int steps = (min(p.H, p.N - j * p.H) + 15) / 16;
-      for (int kk = lane; kk < steps; kk += 32)
-        tab[s0 + kk] = make_uint2((2u * kk * p.lbo_a + 16u * j) >> 4, b_lo0 + (s0 + kk) * step16);
-      s0 += steps;
+    if constexpr (PREC == MELT_FP8E4M3) {
+      // frame rows (im2col in shared memory): K-step s starts 2 s core columns in
+      for (int s = lane; s < p.KS; s += 32) tab[s] = make_uint2((2u * s * p.lbo_a) >> 4, b_lo0 + s * step16);
+    } else {
+      for (int j = 0, s0 = 0; j < p.J; ++j) {
+        const int steps = (min(p.H, p.N - j * p.H) + 15) / 16;
+        for (int kk = lane; kk < steps; kk += 32)
+          tab[s0 + kk] = make_uint2((2u * kk * p.lbo_a + 16u * j) >> 4, b_lo0 + (s0 + kk) * step16);
+        s0 += steps;
+      }
     }
   }
   if (warp == kPMmaWarp) {
@@ -646,7 +779,7 @@ __global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(cons
   // previous kernel of the stream first (programmatic dependent launch).
   if (warp == kPMmaWarp) {
     if (lane == 0) {
-      if (c.rank == 0) pair_mma<MLP>(p, gbase, c, B, tmem_base);
+      if (c.rank == 0) pair_mma<MLP, PREC>(p, gbase, c, B, tmem_base);
       drain_wait(pbar(p, c, B.drain), 0, p.err);
     }
     __syncwarp();
@@ -659,14 +792,17 @@ __global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(cons
     __syncwarp();
   } else if (warp >= kPCvtWarp0) {
     pdl_wait();
-    pair_convert(p, c, B, kPCvtWarp0);
+    if constexpr (PREC == MELT_FP8E4M3)
+      pair_convert_fp8(p, gbase, c, B, kPCvtWarp0);
+    else
+      pair_convert(p, c, B, kPCvtWarp0);
     __syncwarp();
   } else {
     pdl_wait();
     if constexpr (MLP)
       pair_epilogue_mlp<NCH>(p, gbase, c, B, tmem_base);
     else
-      pair_epilogue<NCH, MFCC, EPW>(p, gbase, c, B, tmem_base);
+      pair_epilogue<NCH, MFCC, EPW, PREC>(p, gbase, c, B, tmem_base);
     __syncwarp();
   }
   tc_fence_before();
@@ -698,9 +834,29 @@ KernelFn pick_pair_kernel(int nch) {
   }
 }
 
+// FP8 e4m3 instantiations (log-Mel, and MFCC by chunk count).  The pickers are
+// templates so that only the translation unit that calls one instantiates
+// its kernels.
+template <int = 0>
+KernelFn pick_pair_fp8_kernel(bool mfcc, int nch) {
+  if (!mfcc) return melt_tc_pair_kernel<1, false, false, MELT_FP8E4M3>;
+  switch (nch) {
+    case 1: return melt_tc_pair_kernel<1, true, false, MELT_FP8E4M3>;
+    case 2: return melt_tc_pair_kernel<2, true, false, MELT_FP8E4M3>;
+    case 3: return melt_tc_pair_kernel<3, true, false, MELT_FP8E4M3>;
+    case 4: return melt_tc_pair_kernel<4, true, false, MELT_FP8E4M3>;
+    case 5: return melt_tc_pair_kernel<5, true, false, MELT_FP8E4M3>;
+    case 6: return melt_tc_pair_kernel<6, true, false, MELT_FP8E4M3>;
+    case 7: return melt_tc_pair_kernel<7, true, false, MELT_FP8E4M3>;
+    case 8: return melt_tc_pair_kernel<8, true, false, MELT_FP8E4M3>;
+    default: return nullptr;
+  }
+}
+
 // Fused-MLP instantiations: log-Mel rows of 16 * nch bands (the fused TMEM
 // layout holds M <= 80, so nch <= 5).
-inline KernelFn pick_pair_mlp_kernel(int nch) {
+template <int = 0>
+KernelFn pick_pair_mlp_kernel(int nch) {
   switch (nch) {
     case 1: return melt_tc_pair_kernel<1, false, true>;
     case 2: return melt_tc_pair_kernel<2, false, true>;

@@ -5,7 +5,7 @@
 namespace melt {
 namespace tc {
 
-KernelFn kernel_for_pair_mlp(int nch) { return pick_pair_mlp_kernel(nch); }
+KernelFn kernel_for_pair_mlp(int nch) { return pick_pair_mlp_kernel<>(nch); }
 
 }  // namespace tc
 }  // namespace melt

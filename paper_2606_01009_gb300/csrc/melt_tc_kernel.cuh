@@ -876,6 +876,8 @@ KernelFn kernel_for_mfcc(int prec, int nch);
 KernelFn kernel_for_pair(bool mfcc, int nch);
 // Defined in melt_tc2_mlp.cu: the CTA-pair kernel with the fused correction MLP.
 KernelFn kernel_for_pair_mlp(int nch);
+// Defined in melt_tc2_fp8.cu: the CTA-pair kernel with FP8 e4m3 operands.
+KernelFn kernel_for_pair_fp8(bool mfcc, int nch);
 
 }  // namespace tc
 }  // namespace melt

@@ -44,7 +44,7 @@ static __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint3
                : "memory");
 }
 
-static __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+static __device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -56,19 +56,33 @@ static __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t pari
   return ok != 0;
 }
 
+// Potentially blocking test: the thread may be suspended (not issuing) until
+// the phase completes or a hardware time limit passes.
+static __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Wait for the phase with parity `parity` of barrier `bar` to complete.
-// Polls with the non-blocking test_wait: a suspended try_wait was measured
-// to resume microseconds after the phase completed (notably for arrivals
-// from the peer CTA), which stalls every hand-off of the pipeline.
-// Returns false (after latching `err_bit` in *err and setting *abort) when
-// the wait ran past the limit or another thread of the CTA aborted.
+// A completed phase is seen by one non-blocking test; otherwise the thread
+// waits in try_wait, suspended between polls so that its warp does not take
+// issue slots from the warps doing the work.  Returns false (after latching
+// `err_bit` in *err and setting *abort) when the wait ran past the limit or
+// another thread of the CTA aborted.
 static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort,
                                           int* err, int err_bit) {
-  if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_test_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63) == 0) {
+    if ((it & 15) == 0) {
       if (*abort) return false;
       if (globaltimer() - t0 > kWaitLimitNs) {
         atomicOr(err, err_bit);
@@ -291,7 +305,7 @@ static __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr
   asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 
-static __device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+static __device__ __forceinline__ bool mbar_test_wait_cluster(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -303,15 +317,27 @@ static __device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint3
   return ok != 0;
 }
 
+static __device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait with cluster-scope acquire (barriers that the peer CTA or the
-// pair's MMAs arrive on); same contract as mbar_wait.
+// pair's MMAs arrive on); same contract and polling as mbar_wait.
 static __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
                                                          volatile int* abort, int* err, int err_bit) {
-  if (mbar_try_wait_cluster(bar, parity)) return true;
+  if (mbar_test_wait_cluster(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait_cluster(bar, parity)) return true;
-    if ((it & 63) == 0) {
+    if ((it & 15) == 0) {
       if (*abort) return false;
       if (globaltimer() - t0 > kWaitLimitNs) {
         atomicOr(err, err_bit);
@@ -355,6 +381,17 @@ static __device__ __forceinline__ void mma_f16_pair(uint32_t d_tmem, uint64_t ad
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// 2-SM MMA with e4m3 operands (kind::f8f6f4, K = 32 per instruction); operand
+// split as for mma_f16_pair.
+static __device__ __forceinline__ void mma_f8_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                                   uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
