@@ -138,8 +138,17 @@ melt_status melt_basis_get_fp64(const melt_basis* basis, double* freqs, double* 
  *                    (tcgen05 cta_group::2, 256 frames); each CTA keeps half
  *                    of the basis resident (basis_resident must be 1) and
  *                    stages its waveform span through a ring of bulk copies
- *                    (as many ~14 KB slots as fit; prefetch_tiles, basis_slots
- *                    and ksteps_per_slot are ignored).  0: one CTA per MMA.
+ *                    (as many ~14 KB slots as fit; prefetch_tiles is how many
+ *                    tiles ahead the spans are prefetched into L2 besides;
+ *                    basis_slots and ksteps_per_slot are ignored).  0: one
+ *                    CTA per MMA.
+ *   schedule         CTA pairs only.  0: static, cluster c takes pairs c,
+ *                    c + C, c + 2C, ... (C clusters).  1: dynamic, cluster c
+ *                    takes pair c, then claims each next pair from a
+ *                    launch-wide counter one pair ahead, so clusters that
+ *                    run faster take more (prefetch_tiles is then ignored).
+ *                    The counter lives in the basis (one per launch, 16
+ *                    launches of one basis may be in flight at once).
  */
 typedef struct {
   int basis_resident;
@@ -148,6 +157,7 @@ typedef struct {
   int basis_slots;
   int ksteps_per_slot;
   int cta_pair;
+  int schedule;
 } melt_plan;
 
 /* melt_plan_get - the layout the next forward will use (host struct out).

@@ -106,7 +106,7 @@ namespace {
 
 bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) {
   const int P = tb->precision;
-  if (c.cta_pair != 0) return false;
+  if (c.cta_pair != 0 || c.schedule != 0) return false;
   p.Hd = 0;
   p.NS = p.CH = p.NCHUNK = 0;
   p.st_bytes = p.off_st = 0;
@@ -159,9 +159,11 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
   if (fp8 && (p.H % 16) != 0) return false;
   if (c.basis_resident != 1 || c.a_buffers < 1 || c.a_buffers > 2) return false;
   if (c.prefetch_tiles < 0 || c.prefetch_tiles > kMaxPrefetch) return false;
+  if (c.schedule != 0 && c.schedule != 1) return false;
+  p.dyn = c.schedule;
   p.b_resident = 1;
   p.ZB = c.a_buffers;
-  p.pf = 0;
+  p.pf = c.schedule ? 0 : c.prefetch_tiles;  // L2 prefetch stream of the waveform producer (static schedule)
   p.kps = 1;
   p.NB = p.KS;
   p.step_bytes = p.kstep_bytes / 2;  // one K-step block of this CTA's N/2 basis rows
@@ -239,28 +241,40 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
 // When the basis does not fit beside two A buffers (M > 80 at N = 400, or
 // BF16x3), the basis is streamed from L2 through a ring of the largest slots
 // that fit; the single-buffer layouts come last.
+constexpr int kDefaultSchedule = 0;  // pair schedule of the default plans (0 static, 1 dynamic)
+
 int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap) {
   (void)tb;
   int n = 0;
   auto add = [&](int res, int zb, int pf, int nb, int kps) {
-    if (n < cap) out[n++] = melt_plan{res, zb, pf, nb, kps, 0};
+    if (n < cap) out[n++] = melt_plan{res, zb, pf, nb, kps, 0, 0};
   };
   const int sb = (int)std::max(1u, p.kstep_bytes * (tb->precision == MELT_BF16X3 ? 2u : 1u));
+  melt_plan alts[2];
+  int n_alt = 0;
   if (tb->precision == MELT_BF16 && tb->d_b2) {
-    // CTA pairs first where the staging ring keeps >= 4 slots (measured on the
-    // 64 x 30 s batch: 44 us vs 50 us single-CTA at M = 80; with 2 slots at
-    // M = 128 the pair is slower than a single CTA, 71 vs 62 us).  FP8 pairs
-    // are a plan a caller may set: their four converter warps quantise every
-    // frame separately (per-frame scales) and are latency bound, 470 us vs
-    // 161 us for the single-CTA FP8 kernel on the same batch.
+    // CTA pairs first (measured on the 64 x 30 s batch at M = 80: 41 us
+    // against 50 us single-CTA).  A staging ring of fewer than 4 slots keeps
+    // too few bytes in flight; an L2 prefetch stream one tile ahead makes up
+    // for it (M = 128, two A buffers, 2 slots: 58 us against 66 us without,
+    // and 63 us with one A buffer and more slots), but costs time where the
+    // ring is deep enough (M = 80, 5 slots: 42.5 against 42.1 us) and with
+    // the correction fused (167 against 164 us).  FP8 pairs are a plan a
+    // caller may set: their four converter warps quantise every frame
+    // separately (per-frame scales) and are latency bound, 470 us vs 161 us
+    // for the single-CTA FP8 kernel on the same batch.
     for (int zb = 2; zb >= 1; --zb) {
-      const melt_plan pc{1, zb, 0, p.KS, 1, 1};
+      melt_plan pc{1, zb, 0, p.KS, 1, 1, kDefaultSchedule};
       TcParams q = p;
-      // with the correction fused, a pair layout with fewer slots still beats
-      // a separate pass of the MLP over the features
-      if (n < cap && try_layout_pair(tb, q, pc, tb->n_mfcc) &&
-          q.NS >= (tb->mlp_hd && tb->precision == MELT_BF16 ? 2 : 4))
+      if (n < cap && try_layout_pair(tb, q, pc, tb->n_mfcc) && q.NS >= 2) {
+        if (q.NS < 4 && !tb->mlp_hd) pc.prefetch_tiles = kDefaultSchedule ? 0 : 1;
         out[n++] = pc;
+        // the other pair schedule, for melt_autotune (after every default layout)
+        melt_plan alt = pc;
+        alt.schedule = 1 - kDefaultSchedule;
+        alt.prefetch_tiles = alt.schedule ? 0 : (q.NS < 4 && !tb->mlp_hd ? 1 : 0);
+        if (n_alt < 2) alts[n_alt++] = alt;
+      }
     }
   }
   add(1, 2, 2, p.KS, 1);
@@ -270,6 +284,7 @@ int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap
   add(1, 1, 2, p.KS, 1);
   for (int kps = kps_hi; kps >= 1; --kps) add(0, 1, 2, 2, kps);
   for (int nb = 24; nb >= 2; nb -= 2) add(0, 1, 2, nb, 1);
+  for (int i = 0; i < n_alt && n < cap; ++i) out[n++] = alts[i];
   return n;
 }
 
@@ -359,6 +374,10 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
     if (cudaMalloc(&tb->d_b2, img2.size()) != cudaSuccess) return MELT_ERR_OOM;
     if (cudaMemcpy(tb->d_b2, img2.data(), img2.size(), cudaMemcpyHostToDevice) != cudaSuccess)
       return MELT_ERR_CUDA;
+    // counters of the dynamic pair schedule (each launch leaves its pair at zero)
+    const size_t sb = sizeof(unsigned long long) * 2 * kSchedWords;
+    if (cudaMalloc(&tb->d_sched, sb) != cudaSuccess) return MELT_ERR_OOM;
+    if (cudaMemset(tb->d_sched, 0, sb) != cudaSuccess) return MELT_ERR_CUDA;
   }
   return MELT_OK;
 }
@@ -367,8 +386,10 @@ void tc_free(TcBasis* tb) {
   cudaFree(tb->d_b);
   cudaFree(tb->d_b2);
   cudaFree(tb->d_mlp_img);
+  cudaFree(tb->d_sched);
   tb->d_b = tb->d_b2 = nullptr;
   tb->d_mlp_img = nullptr;
+  tb->d_sched = nullptr;
 }
 
 int tc_max_mfcc() { return kMaxMfccTc; }
@@ -412,6 +433,20 @@ bool tc_current_plan(const TcBasis* tb, melt_plan* out) {
   if (tc_candidates(tb, c, 1) < 1) return false;
   *out = c[0];
   return true;
+}
+
+int tc_workers(const TcBasis* tb, long long n_tiles, int sm_count, int* unit) {
+  *unit = 1;
+  if (n_tiles < 1 || sm_count < 1) return 1;
+  TcParams p;
+  std::memset(&p, 0, sizeof(p));
+  if (plan_smem(tb, p, tb->n_mfcc) && p.NS > 0) {
+    // the launch below: as many two-CTA clusters as are resident, at most one per pair
+    *unit = 2;
+    const int clusters = tb->pair_clusters > 0 ? tb->pair_clusters : std::max(1, sm_count / 2);
+    return (int)std::min<long long>((n_tiles + 1) / 2, clusters);
+  }
+  return (int)std::min<long long>(n_tiles, sm_count);
 }
 
 cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream) {
@@ -477,6 +512,11 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
   }
   // CTA pairs: clusters of two, as many as can be resident at once (persistent)
   p.n_pairs = (L.n_tiles + 1) / 2;
+  if (p.dyn) {
+    if (!tb->d_sched) return cudaErrorInvalidValue;
+    TcBasis* sb = const_cast<TcBasis*>(tb);
+    p.sched = tb->d_sched + 2 * (sb->sched_next++ % kSchedWords);
+  }
   attr[1].id = cudaLaunchAttributeClusterDimension;
   attr[1].val.clusterDim.x = 2;
   attr[1].val.clusterDim.y = 1;

@@ -54,7 +54,7 @@ constexpr int kPQuads = 8;  // float4s per converter thread per staged chunk (<=
 
 struct PairBars {
   int s_full, s_empty, z_full, z_empty, b_full, peer_b, t_full, t_empty, h_full, a2_full, y_full,
-      sc_full, drain, total;
+      sc_full, drain, sched_full, sched_empty, total;
   __host__ __device__ PairBars(int NS, int ZB, int KS) {
     s_full = 0;
     s_empty = s_full + NS;
@@ -69,7 +69,9 @@ struct PairBars {
     y_full = a2_full + 1;  //            MLP output in TMEM
     sc_full = y_full + 1;  // FP8: per-frame scales of a tile ready (kScaleRing deep)
     drain = sc_full + kScaleRing;
-    total = drain + 1;
+    sched_full = drain + 1;              // dynamic schedule: ring entry published (per CTA)
+    sched_empty = sched_full + kSchedRing;  //               ring entry read by both epilogues
+    total = sched_empty + kSchedRing;
   }
 };
 
@@ -88,6 +90,74 @@ static __device__ __forceinline__ uint32_t pbar(const TcParams& p, const PairCtx
 static __device__ __forceinline__ void warp_arrive_leader(uint32_t local_bar) {
   __syncwarp();
   if ((threadIdx.x & 31) == 0) mbar_arrive_cluster(mapa_shared(local_bar, 0));
+}
+
+// ---- pair schedule
+// Every role walks the same pair sequence: the cluster's own pair first, then
+// either (static) every n_clusters-th pair, or (dynamic) the pairs the even
+// CTA's waveform producer claims, one pair ahead of itself, from the
+// launch's counter and publishes to both CTAs through a ring of kSchedRing
+// entries in shared memory (a pair index >= n_pairs ends the sequence).
+static __device__ __forceinline__ uint32_t sched_slot(const TcParams& p, const PairCtx& c, int r) {
+  return c.sbase + p.off_misc + 64 + 4 * (r % kSchedRing);
+}
+
+// Pair of ordinal k >= 1, read by one thread (dynamic: ring entry k - 1).
+// ok turns false if the wait for the entry timed out.
+static __device__ int pair_next_thread(const TcParams& p, const PairCtx& c, const PairBars& B, int k,
+                                       bool& ok) {
+  if (!p.dyn) return c.cluster + k * c.n_clusters;
+  const int r = k - 1;
+  ok = mbar_wait(pbar(p, c, B.sched_full + r % kSchedRing), (r / kSchedRing) & 1, c.abort, p.err,
+                 kErrTimeout);
+  if (!ok) return p.n_pairs;
+  int q;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(q) : "r"(sched_slot(p, c, r)) : "memory");
+  return q;
+}
+
+// The same for a whole warp (lane 0 waits and reads).
+static __device__ int pair_next_warp(const TcParams& p, const PairCtx& c, const PairBars& B, int k,
+                                     bool& ok) {
+  int q = 0, good = 1;
+  if ((threadIdx.x & 31) == 0) {
+    bool o = true;
+    q = pair_next_thread(p, c, B, k, o);
+    good = o ? 1 : 0;
+  }
+  q = __shfl_sync(0xffffffffu, q, 0);
+  good = __shfl_sync(0xffffffffu, good, 0);
+  ok = good != 0;
+  return q;
+}
+
+// An epilogue warp counts itself out of the ring entry of its pair ordinal
+// k >= 1 on the even CTA's barrier.  It does so once the pair's accumulator
+// is full: by then both producers, both CTAs' converters and the MMA thread
+// have read the entry, so once both epilogues have, the slot may be reused.
+static __device__ __forceinline__ void sched_release(const TcParams& p, const PairCtx& c,
+                                                     const PairBars& B, int k) {
+  if (p.dyn && k > 0) warp_arrive_leader(pbar(p, c, B.sched_empty + (k - 1) % kSchedRing));
+}
+
+// Even CTA's producer: publish pair q as ring entry r to both CTAs, a plain
+// store and arrival here, an asynchronous store completing on the barrier
+// there.  Entry r reuses the slot of entry r - kSchedRing once both CTAs'
+// epilogues have read that one.
+static __device__ bool sched_publish(const TcParams& p, const PairCtx& c, const PairBars& B, int r,
+                                     int q) {
+  const int s = r % kSchedRing;
+  if (r >= kSchedRing &&
+      !mbar_wait(pbar(p, c, B.sched_empty + s), ((r / kSchedRing) - 1) & 1, c.abort, p.err, kErrTimeout))
+    return false;
+  const uint32_t slot = sched_slot(p, c, r);
+  const uint32_t full = pbar(p, c, B.sched_full + s);
+  asm volatile("st.shared.b32 [%0], %1;" ::"r"(slot), "r"(q) : "memory");
+  mbar_arrive(full);
+  const uint32_t peer_full = mapa_shared(full, 1);
+  mbar_arrive_expect_tx_cluster(peer_full, 4);
+  st_async_u32(mapa_shared(slot, 1), (uint32_t)q, peer_full);
+  return true;
 }
 
 static __device__ __forceinline__ bool warp_wait_cl(uint32_t bar, uint32_t parity, volatile int* abort,
@@ -111,15 +181,46 @@ static __device__ __forceinline__ TileDesc pair_tile(const TcParams& p, const Pa
   return td;
 }
 
+// Bulk prefetch of a tile's sample span into L2 (pieces of <= 32 KB).
+static __device__ __forceinline__ void pair_prefetch_span(const TcParams& p, const TileDesc& td) {
+  if (td.n_frames == 0) return;
+  const long long avail = tile_avail(p, td);
+  const float* src = p.wave + td.in_off;
+  for (long long o = 0; o < avail; o += 8192)
+    prefetch_l2(src + o, (uint32_t)(min(8192ll, avail - o) * 4));
+}
+
+// Waveform producer.  Besides the staging copies it keeps (static schedule)
+// an L2 prefetch stream `pf` tiles ahead: when it starts tile k it
+// prefetches the span of tile k + pf, so the DRAM reads in flight per SM are
+// not limited to the staging ring.  The next descriptor to prefetch is read
+// one tile early.  In the dynamic schedule the even CTA's producer is the
+// one that claims and publishes the pairs.
 static __device__ void pair_wave_producer(const TcParams& p, const PairCtx& c, const PairBars& B) {
   const uint64_t pol = policy_evict_first();
   int g = 0;
   bool ok = true;
-  for (int q = c.cluster; ok && q < p.n_pairs; q += c.n_clusters) {
+  int qn = c.cluster + p.pf * c.n_clusters;  // pair whose span is prefetched next
+  TileDesc pend = pair_tile(p, c, p.pf > 0 && qn < p.n_pairs ? qn : p.n_pairs);
+  for (int i = 1; i < p.pf; ++i) {
+    const int qi = c.cluster + i * c.n_clusters;
+    if (qi < p.n_pairs) pair_prefetch_span(p, pair_tile(p, c, qi));
+  }
+  int q = c.cluster;
+  for (int k = 0; q < p.n_pairs; ++k) {
+    // dynamic schedule, even CTA: claim the pair after this one now; the
+    // counter's answer is used after this pair's copies are issued
+    unsigned long long claim = 0;
+    if (p.dyn && c.rank == 0) claim = atomicAdd(p.sched, 1ull);
+    if (p.pf > 0 && qn < p.n_pairs) {
+      pair_prefetch_span(p, pend);
+      qn += c.n_clusters;
+      if (qn < p.n_pairs) pend = pair_tile(p, c, qn);
+    }
     const TileDesc td = pair_tile(p, c, q);
-    if (td.n_frames == 0) continue;  // empty tile: the converters skip it too
     const long long avail = tile_avail(p, td);
-    for (int ch = 0; ch < p.NCHUNK; ++ch, ++g) {
+    // (an empty tile issues nothing: the converters skip it too)
+    for (int ch = 0; td.n_frames > 0 && ch < p.NCHUNK; ++ch, ++g) {
       const int slot = g % p.NS;
       const uint32_t full = pbar(p, c, B.s_full + slot);
       if (!mbar_wait(pbar(p, c, B.s_empty + slot), ((g / p.NS) & 1) ^ 1, c.abort, p.err,
@@ -137,6 +238,19 @@ static __device__ void pair_wave_producer(const TcParams& p, const PairCtx& c, c
         mbar_arrive(full);
       }
     }
+    if (!ok) break;
+    if (!p.dyn) {
+      q += c.n_clusters;
+    } else if (c.rank == 0) {
+      // claims count from zero in every launch; the first n_clusters pairs are the clusters' own
+      const long long ord = (long long)claim;
+      const int nq = ord >= (long long)(p.n_pairs - c.n_clusters) ? p.n_pairs : c.n_clusters + (int)ord;
+      if (!sched_publish(p, c, B, k, nq)) break;
+      q = nq;
+    } else {
+      q = pair_next_thread(p, c, B, k + 1, ok);
+      if (!ok) break;
+    }
   }
   // every issued copy has landed before the CTA can exit
   for (int k = max(0, g - p.NS); k < g; ++k)
@@ -152,6 +266,9 @@ static __device__ void pair_basis_producer(const TcParams& p, const PairCtx& c, 
   mbar_arrive_expect_tx(full, total + mlp);
   for (uint32_t o = 0; o < total; o += 32768u)
     bulk_g2s_hint(c.sbase + p.off_b + o, src + o, min(32768u, total - o), full, pol);
+  // the weight image is repacked by the kernel just before this one on the
+  // stream: read it only once that kernel's writes are visible
+  if (mlp > 0) pdl_wait();
   const uint8_t* msrc = p.mlp_img + (size_t)c.rank * mlp;
   for (uint32_t o = 0; o < mlp; o += 32768u)
     bulk_g2s_hint(c.sbase + p.off_mlp + o, msrc + o, min(32768u, mlp - o), full, pol);
@@ -209,7 +326,9 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
   constexpr int nacc = MLP ? 1 : 2;  // the fused MLP's TMEM leaves room for one accumulator
   int k = 0;
   bool ok = true;
-  for (int q = c.cluster; q < p.n_pairs; q += c.n_clusters, ++k) {
+  for (;; ++k) {
+    const int q = k == 0 ? c.cluster : pair_next_thread(p, c, B, k, ok);
+    if (!ok || q >= p.n_pairs) break;
     const int zb = p.ZB == 2 ? (k & 1) : 0;
     const int acc = k % nacc;
     ok = mbar_wait_cluster(pbar(p, c, B.t_empty + acc), ((k / nacc) & 1) ^ 1, c.abort, p.err,
@@ -292,8 +411,10 @@ static __device__ void pair_convert(const TcParams& p, const PairCtx& c, const P
   const uint32_t st0 = c.sbase + p.off_st;
   int slot = 0;
   uint32_t sphase = 0;
-  int k = 0;
-  for (int qp = c.cluster; qp < p.n_pairs; qp += c.n_clusters, ++k) {
+  for (int k = 0;; ++k) {
+    bool okq = true;
+    const int qp = k == 0 ? c.cluster : pair_next_warp(p, c, B, k, okq);
+    if (!okq || qp >= p.n_pairs) break;
     const int zb = p.ZB == 2 ? (k & 1) : 0;
     if (!warp_wait_cl(pbar(p, c, B.z_empty + zb), ((p.ZB == 2 ? (k >> 1) : k) & 1) ^ 1, c.abort,
                       p.err))
@@ -369,8 +490,11 @@ static __device__ void pair_convert_fp8(const TcParams& p, uint8_t* gbase, const
   float* scales = reinterpret_cast<float*>(gbase + p.off_scale);
   const uint32_t st0 = c.sbase + p.off_st;
   int g = 0;  // chunks consumed so far (ring position)
-  int k = 0;
-  for (int qp = c.cluster; qp < p.n_pairs; qp += c.n_clusters, ++k) {
+  for (int k = 0;; ++k) {
+    bool okq = true;
+    const int qp = k == 0 ? c.cluster : pair_next_warp(p, c, B, k, okq);
+    // every converter warp reads the same entry; a timeout in any of them stops all
+    if (!named_barrier_and(1, kPCvtThreads, okq) || qp >= p.n_pairs) break;
     const int zb = p.ZB == 2 ? (k & 1) : 0;
     bool ok = warp_wait_cl(pbar(p, c, B.z_empty + zb), ((p.ZB == 2 ? (k >> 1) : k) & 1) ^ 1, c.abort, p.err);
     if (!named_barrier_and(1, kPCvtThreads, ok)) break;
@@ -474,11 +598,14 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
   const int nch = p.MP >> 4;
   int c_lo, c_hi;
   half_chunks(nch, EPW / 4, half, c_lo, c_hi);
-  int k = 0;
-  for (int q = c.cluster; q < p.n_pairs; q += c.n_clusters, ++k) {
+  for (int k = 0;; ++k) {
+    bool okq = true;
+    const int q = k == 0 ? c.cluster : pair_next_warp(p, c, B, k, okq);
+    if (!okq || q >= p.n_pairs) break;
     const int acc = k & 1;
     const TileDesc td = pair_tile(p, c, q);
     if (!warp_wait_cl(pbar(p, c, B.t_full + acc), (k >> 1) & 1, c.abort, p.err)) break;
+    sched_release(p, c, B, k);
     float sc = 1.f;  // FP8: s_t / 448 of the frame (sample and basis scales)
     if constexpr (PREC == MELT_FP8E4M3) {
       if (!warp_wait(pbar(p, c, B.sc_full + (k % kScaleRing)), (k / kScaleRing) & 1, c.abort, p.err))
@@ -602,14 +729,17 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
   int c_lo, c_hi, h_lo, h_hi;
   half_chunks(NCH, 2, half, c_lo, c_hi);
   half_chunks(p.Hd / 16, 2, half, h_lo, h_hi);
-  int k = 0;
-  for (int q = c.cluster; q < p.n_pairs; q += c.n_clusters, ++k) {
+  for (int k = 0;; ++k) {
+    bool okq = true;
+    const int q = k == 0 ? c.cluster : pair_next_warp(p, c, B, k, okq);
+    if (!okq || q >= p.n_pairs) break;
     const TileDesc td = pair_tile(p, c, q);
     const bool live = td.n_frames > 0;
     const bool valid = row < td.n_frames;
     float* orow = p.out + (size_t)(td.out_row + row) * p.n_out;
     // 1. log-Mel (Eq. 8) of this half of the row, and its x-hat in BF16 into TMEM
     if (!warp_wait_cl(pbar(p, c, B.t_full), k & 1, c.abort, p.err)) break;
+    sched_release(p, c, B, k);
     tc_fence_after();
     float v[16 * NV];
     if (live) {
@@ -734,6 +864,10 @@ __global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(cons
     mbar_init(bar(B.y_full), 1);
     for (int i = 0; i < kScaleRing; ++i) mbar_init(bar(B.sc_full + i), kPCvtWarps);
     mbar_init(bar(B.drain), 1);
+    for (int i = 0; i < kSchedRing; ++i) {
+      mbar_init(bar(B.sched_full + i), 1);           // the even CTA's producer (here or remote)
+      mbar_init(bar(B.sched_empty + i), 2 * EPW);    // epilogues of both CTAs (even CTA's copy is used)
+    }
     *c.abort = 0;
     fence_mbar_init();
   }
@@ -774,7 +908,8 @@ __global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(cons
   const uint32_t tmem_base = *tmem_slot;
   if (threadIdx.x == 0) pdl_launch_dependents();
 
-  // MMA issuer and basis producer start at once (own data only); the roles
+  // MMA issuer and basis producer start at once (own data only; the basis
+  // producer waits before it reads the fused MLP's weight image); the roles
   // that read tiles or the waveform, or write features, wait for the
   // previous kernel of the stream first (programmatic dependent launch).
   if (warp == kPMmaWarp) {
@@ -807,6 +942,15 @@ __global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(cons
   }
   tc_fence_before();
   __syncthreads();
+  if (p.dyn && threadIdx.x == 0) {
+    // every claim of this CTA is settled: the last CTA of the launch to get
+    // here leaves the launch's counter at zero for the next launch that uses it
+    __threadfence();
+    if (atomicAdd(p.sched + 1, 1ull) == (unsigned long long)gridDim.x - 1) {
+      atomicExch(p.sched, 0ull);
+      atomicExch(p.sched + 1, 0ull);
+    }
+  }
   cluster_sync_all();  // neither CTA leaves (or frees TMEM) while its peer may still use it
   if (warp == kPMmaWarp) {
     tc_fence_after();

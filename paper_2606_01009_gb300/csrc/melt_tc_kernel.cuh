@@ -65,6 +65,8 @@ constexpr int kCvtThreads = 32 * kCvtWarps;             // 384
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kF = kTileFrames;  // 128 = UMMA M
 constexpr int kScaleRing = 4;    // FP8 per-frame scale buffers in flight
+constexpr int kSchedRing = 16;   // dynamic pair schedule: published pair indices in flight
+constexpr int kSchedWords = 16;  // dynamic pair schedule: counters, one per launch in flight
 constexpr int kQuadBatch = 8;    // float4 loads per converter thread per batch (two batches in flight)
 constexpr int kItemBatch = 3;    // FP8 frame-row items (16 samples each) per batch
 constexpr int kEpiGroup = 2;     // 16-column chunks per TMEM wait in the epilogue
@@ -105,6 +107,11 @@ struct TcParams {
   uint32_t off_st;
   uint32_t b_lbo;        // B operand: bytes between the two K core columns of a K-step block
   int n_pairs;           // tile pairs (tile 2q + rank of pair q goes to CTA `rank`)
+  // CTA-pair kernel, dynamic schedule (dyn = 1): after its first pair, each
+  // cluster claims the next ones from sched[0] (a launch-wide counter that
+  // the last CTA to finish, counted in sched[1], resets to zero)
+  int dyn;
+  unsigned long long* sched;
   // CTA-pair kernel with the correction MLP fused in its epilogue (Hd > 0)
   const uint8_t* mlp_img;  // two halves of mlp_half bytes (W1 blocks, W2 blocks, vectors)
   uint32_t mlp_half;

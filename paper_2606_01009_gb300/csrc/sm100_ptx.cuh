@@ -305,6 +305,22 @@ static __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr
   asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 
+// Arrive on a (possibly remote) mbarrier and raise the transaction bytes its
+// current phase waits for (shared::cluster address).
+static __device__ __forceinline__ void mbar_arrive_expect_tx_cluster(uint32_t cluster_bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cluster.b64 _, [%0], %1;" ::"r"(cluster_bar), "r"(bytes)
+               : "memory");
+}
+
+// Asynchronous 4-byte store into a (possibly remote) CTA's shared memory
+// that completes 4 transaction bytes on an mbarrier of the same CTA; the
+// value is visible to threads that see that barrier phase complete.
+static __device__ __forceinline__ void st_async_u32(uint32_t cluster_addr, uint32_t v, uint32_t cluster_bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.u32 [%0], %1, [%2];" ::"r"(cluster_addr),
+               "r"(v), "r"(cluster_bar)
+               : "memory");
+}
+
 static __device__ __forceinline__ bool mbar_test_wait_cluster(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(

@@ -84,7 +84,8 @@ class MeltPlan(C.Structure):
     """melt_plan: layout of the tensor-core pipeline in shared memory."""
     _fields_ = [("basis_resident", C.c_int), ("a_buffers", C.c_int), ("prefetch_tiles", C.c_int),
                 ("basis_slots", C.c_int), ("ksteps_per_slot", C.c_int),
-                ("cta_pair", C.c_int)]
+                ("cta_pair", C.c_int),
+                ("schedule", C.c_int)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

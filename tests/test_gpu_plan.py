@@ -31,9 +31,11 @@ def _plans():
         out.append(dict(basis_resident=0, a_buffers=2, prefetch_tiles=pf, basis_slots=nb, ksteps_per_slot=kps,
                         cta_pair=0))
     out.append(dict(basis_resident=0, a_buffers=1, prefetch_tiles=2, basis_slots=12, ksteps_per_slot=1, cta_pair=0))
-    for zb in (1, 2):   # CTA pairs (BF16 only): half of the basis per CTA, 2-SM MMAs
-        out.append(dict(basis_resident=1, a_buffers=zb, prefetch_tiles=0, basis_slots=0, ksteps_per_slot=1,
-                        cta_pair=1))
+    for zb, pf, sched in ((1, 0, 0), (2, 0, 0), (2, 1, 0), (2, 2, 0), (2, 0, 1), (1, 0, 1)):
+        # CTA pairs (BF16 and FP8): half of the basis per CTA, 2-SM MMAs; static
+        # or dynamic pair schedule
+        out.append(dict(basis_resident=1, a_buffers=zb, prefetch_tiles=pf, basis_slots=0, ksteps_per_slot=1,
+                        cta_pair=1, schedule=sched))
     return out
 
 
@@ -74,13 +76,18 @@ def test_every_plan_is_bit_identical(melt, prec, n_mels):
 
 def test_plan_round_trip_and_rejections(melt):
     fe = melt.Frontend(precision="bf16")
-    pl = dict(basis_resident=0, a_buffers=2, prefetch_tiles=3, basis_slots=3, ksteps_per_slot=4, cta_pair=0)
+    pl = dict(basis_resident=0, a_buffers=2, prefetch_tiles=3, basis_slots=3, ksteps_per_slot=4, cta_pair=0,
+              schedule=0)
     melt.melt_plan_set(fe.handle, pl)
     assert melt.melt_plan_get(fe.handle) == pl
+    pair = dict(basis_resident=1, a_buffers=2, prefetch_tiles=0, basis_slots=0, ksteps_per_slot=1, cta_pair=1,
+                schedule=1)
     for bad in [dict(pl, a_buffers=3), dict(pl, prefetch_tiles=-1), dict(pl, prefetch_tiles=5),
                 dict(pl, basis_slots=1), dict(pl, ksteps_per_slot=0),
                 dict(pl, basis_slots=32, ksteps_per_slot=40), dict(pl, cta_pair=2),
-                dict(pl, cta_pair=1)]:          # a pair plan needs the resident basis
+                dict(pl, cta_pair=1),           # a pair plan needs the resident basis
+                dict(pl, schedule=1),           # the dynamic schedule is for CTA pairs only
+                dict(pair, schedule=2), dict(pair, schedule=-1)]:
         with pytest.raises(melt.MeltError) as ei:
             melt.melt_plan_set(fe.handle, bad)
         assert ei.value.status == melt.MELT_ERR_UNSUPPORTED
@@ -105,4 +112,54 @@ def test_autotune_keeps_output(melt):
     got = fe(wave, pk.offsets, pk.lengths).cpu().numpy()
     fe.sync()
     assert np.array_equal(got, ref)
+    fe.close()
+
+
+def _ragged_batch(n_clips, seed):
+    """Clips of 0.2 to 30 s (log-uniform) with an odd total tile count."""
+    rng = np.random.default_rng(seed)
+    lens = np.exp(rng.uniform(np.log(3200), np.log(480000), size=n_clips)).astype(np.int64)
+    tiles = lambda L: -(-max(0, (int(L) - 400) // 160 + 1) // 128) if L >= 400 else 0
+    if sum(tiles(L) for L in lens) % 2 == 0:
+        lens[0] = 400 + 160 * 10   # one more single-tile clip makes the count odd
+    return [G.rich_clip(seed, i, int(L)) for i, L in enumerate(lens)]
+
+
+@pytest.mark.parametrize("batch", ["rich_64x30s", "ragged_300"])
+def test_dynamic_pair_schedule_matches_static(melt, batch):
+    """Dynamic and static pair schedules give the same features, launch after launch.
+
+    The batches hold several rounds of pairs per cluster, so most pairs are
+    claimed from the launch counter; back-to-back launches check that every
+    launch leaves its counter at zero for the next one that uses it, and
+    launches on two unordered streams that concurrent launches do not share
+    a counter.
+    """
+    import torch
+    clips = G.workload("rich_64x30s")[0] if batch == "rich_64x30s" else _ragged_batch(300, 99)
+    pk = G.pack_clips(clips)
+    wave = torch.from_numpy(pk.wave).cuda()
+    fe = melt.Frontend(precision="bf16")
+    T = fe.total_frames(pk.lengths)
+    base = dict(basis_resident=1, a_buffers=2, prefetch_tiles=0, basis_slots=0, ksteps_per_slot=1, cta_pair=1)
+    melt.melt_plan_set(fe.handle, dict(base, schedule=0))
+    ref = fe(wave, pk.offsets, pk.lengths).cpu().numpy()
+    fe.sync()
+    melt.melt_plan_set(fe.handle, dict(base, schedule=1))
+    outs = [torch.full((T, fe.n_out), float("nan"), device="cuda") for _ in range(3)]
+    for i in range(7):
+        fe(wave, pk.offsets, pk.lengths, out=outs[i % 3])
+    fe.sync()
+    for o in outs:
+        assert np.array_equal(o.cpu().numpy(), ref), batch
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for o in outs[:2]:
+        o.fill_(float("nan"))
+    torch.cuda.synchronize()
+    for s, o in zip(streams, outs[:2]):
+        fe(wave, pk.offsets, pk.lengths, out=o, stream=s)
+    for s in streams:
+        fe.sync(s)
+    for o in outs[:2]:
+        assert np.array_equal(o.cpu().numpy(), ref), batch
     fe.close()
