@@ -217,8 +217,8 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
     off += 128;
     p.off_scale = off;  // FP8: per-frame scale ring, then row maxima and frame multipliers
     off += fp8 ? kScaleRing * kF * 4 : 0u;
-    p.off_rowmax = off;
-    off += fp8 ? align_up((2 * p.zrows + kF) * 4, 128) : 0u;
+    p.off_rowmax = off;  // row maxima (2 zrows), then per-frame multiplier and sample locations (4 kF)
+    off += fp8 ? align_up((2 * p.zrows + 4 * kF) * 4, 128) : 0u;
     p.off_dct = off;
     off += align_up(4 * n_mfcc * p.MP, 128);
     if (off + 128 > kSmemLimit) continue;
@@ -521,7 +521,7 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
   attr[1].val.clusterDim.x = 2;
   attr[1].val.clusterDim.y = 1;
   attr[1].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(pair_threads(fused), 1, 1);
+  cfg.blockDim = dim3(pair_threads(fused, tb->precision), 1, 1);
   cfg.numAttrs = 2;
   TcBasis* mtb = const_cast<TcBasis*>(tb);
   if (mtb->pair_clusters < 0 || mtb->pair_smem != smem) {

@@ -49,7 +49,15 @@ namespace tc {
 constexpr int kPCvtWarps = 4;
 constexpr int kPCvtThreads = 32 * kPCvtWarps;  // 128
 __host__ __device__ constexpr int pair_epi_warps(bool mlp) { return mlp ? 8 : 4; }
-__host__ __device__ constexpr int pair_threads(bool mlp) { return 32 * (pair_epi_warps(mlp) + 7); }
+// Converter warps: 4 (BF16, polyphase: each sample converted once), 8 for
+// FP8, whose frames are quantised one by one (2.5x the samples, more work
+// per sample): two warps per SM sub-partition hide each other's latency.
+__host__ __device__ constexpr int pair_cvt_warps(int prec) { return prec == MELT_FP8E4M3 ? 8 : 4; }
+__host__ __device__ constexpr int pair_threads(bool mlp, int prec = MELT_BF16) {
+  return 32 * (pair_epi_warps(mlp) + 3 + pair_cvt_warps(prec));
+}
+constexpr int kPCvtWarpsF8 = pair_cvt_warps(MELT_FP8E4M3);
+constexpr int kPCvtThreadsF8 = 32 * kPCvtWarpsF8;
 constexpr int kPQuads = 8;  // float4s per converter thread per staged chunk (<= 16 KB)
 
 struct PairBars {
@@ -462,6 +470,42 @@ static __device__ void pair_convert(const TcParams& p, const PairCtx& c, const P
   }
 }
 
+// Shared-memory float4 load under a predicate (zeros otherwise), without a branch.
+static __device__ __forceinline__ float4 lds128_if(uint32_t addr, bool pred) {
+  float4 v;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %5, 0;\n\t"
+      "mov.b32 %0, 0;\n\tmov.b32 %1, 0;\n\tmov.b32 %2, 0;\n\tmov.b32 %3, 0;\n\t"
+      "@p ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n\t}"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "r"(addr), "r"((uint32_t)pred));
+  return v;
+}
+
+// Shared-memory 4-byte store under a predicate, without a branch.
+static __device__ __forceinline__ void sts32_if(uint32_t addr, uint32_t v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %2, 0;\n\t"
+      "@p st.shared.b32 [%0], %1;\n\t}" ::"r"(addr),
+      "r"(v), "r"((uint32_t)pred)
+      : "memory");
+}
+
+// The samples of a quad at or past the clip end set to zero, by selects (s =
+// span index of x.x).
+static __device__ __forceinline__ float4 clip_quad_sel(float4 x, int s, int nsamp) {
+  x.x = s < nsamp ? x.x : 0.f;
+  x.y = s + 1 < nsamp ? x.y : 0.f;
+  x.z = s + 2 < nsamp ? x.z : 0.f;
+  x.w = s + 3 < nsamp ? x.w : 0.f;
+  return x;
+}
+
+constexpr int kFRows = 4;    // FP8 pair converter: Z rows per warp per row-maximum batch
+constexpr int kFFrames = 4;  // FP8 pair converter: frames per warp per quantisation batch
+
 // FP8 converter: staged FP32 chunks -> quantised frame rows (im2col inside
 // shared memory only), with the frame's scale 448 / amax(frame).
 //
@@ -487,83 +531,138 @@ static __device__ void pair_convert_fp8(const TcParams& p, uint8_t* gbase, const
   const int chunk_samples = p.CH * p.H;
   unsigned* rowmax = reinterpret_cast<unsigned*>(gbase + p.off_rowmax);  // [zrows] float bits
   unsigned* rowpre = rowmax + p.zrows;                                   // [zrows]
+  float* finv = reinterpret_cast<float*>(rowpre + p.zrows);              // [kF] 448 / amax
+  int* fsplit = reinterpret_cast<int*>(finv + kF);                        // [kF]
+  uint32_t* fbase0 = reinterpret_cast<uint32_t*>(fsplit + kF);            // [kF]
+  uint32_t* fbase1 = fbase0 + kF;                                         // [kF]
   float* scales = reinterpret_cast<float*>(gbase + p.off_scale);
   const uint32_t st0 = c.sbase + p.off_st;
+  // float4 j of a frame row goes to core column j / 4, byte 4 (j % 4) of it:
+  // for j = lane + 32 m that is column lane / 4 + 8 m
+  const uint32_t lane_col = (uint32_t)(lane >> 2) * p.lbo_a + 4u * (uint32_t)(lane & 3);
   int g = 0;  // chunks consumed so far (ring position)
   for (int k = 0;; ++k) {
     bool okq = true;
     const int qp = k == 0 ? c.cluster : pair_next_warp(p, c, B, k, okq);
     // every converter warp reads the same entry; a timeout in any of them stops all
-    if (!named_barrier_and(1, kPCvtThreads, okq) || qp >= p.n_pairs) break;
+    if (!named_barrier_and(1, kPCvtThreadsF8, okq) || qp >= p.n_pairs) break;
     const int zb = p.ZB == 2 ? (k & 1) : 0;
     bool ok = warp_wait_cl(pbar(p, c, B.z_empty + zb), ((p.ZB == 2 ? (k >> 1) : k) & 1) ^ 1, c.abort, p.err);
-    if (!named_barrier_and(1, kPCvtThreads, ok)) break;
+    if (!named_barrier_and(1, kPCvtThreadsF8, ok)) break;
     const TileDesc td = pair_tile(p, c, qp);
     const int nsamp = td.n_samples;
+    const bool tail = nsamp < p.zrows * p.H;  // the clip ends inside the span: clip samples past it
     const uint32_t abase = c.sbase + p.off_a + zb * p.abuf_bytes;
     if (td.n_frames > 0) {
       int f_done = 0;
       for (int ch = 0; ch < p.NCHUNK; ++ch) {
         const int slot = (g + ch) % p.NS;
         ok = warp_wait(pbar(p, c, B.s_full + slot), ((g + ch) / p.NS) & 1, c.abort, p.err);
-        ok = named_barrier_and(1, kPCvtThreads, ok);  // every warp takes the same decision
+        ok = named_barrier_and(1, kPCvtThreadsF8, ok);  // every warp takes the same decision
         if (!ok) break;
-        // 1. max |x| over each row of the chunk and over its first KL samples
+        // 1. max |x| over each row of the chunk and over its first KL samples.
+        //    A warp takes rows cw, cw + 4, ... in batches of kFRows rows and
+        //    issues all of a batch's loads before its reductions.
         const uint32_t sp = st0 + (uint32_t)slot * p.st_bytes;
         const int r0 = ch * p.CH, rows = min(p.CH, p.zrows - r0);
-        for (int rl = cw; rl < rows; rl += kPCvtWarps) {
-          unsigned mf = 0u, mp = 0u;
+        for (int rb = cw; rb < rows; rb += kPCvtWarpsF8 * kFRows) {
+          unsigned mf[kFRows], mp[kFRows];
+#pragma unroll
+          for (int r = 0; r < kFRows; ++r) mf[r] = mp[r] = 0u;
           for (int j = lane; j < h4; j += 32) {
-            float4 v;
-            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                         : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                         : "r"(sp + 16u * (uint32_t)(rl * h4 + j)));
-            clip_quad(v, (r0 + rl) * p.H + 4 * j, nsamp);
-            const unsigned m = __float_as_uint(fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
-            mf = max(mf, m);
-            if (4 * j < KL) mp = max(mp, m);
-          }
-          mf = __reduce_max_sync(0xffffffffu, mf);
-          mp = __reduce_max_sync(0xffffffffu, mp);
-          if (lane == 0) {
-            rowmax[r0 + rl] = mf;
-            rowpre[r0 + rl] = mp;
-          }
-        }
-        named_barrier(1, kPCvtThreads);
-        // 2. the frames whose rows are all present now: scale and quantised row
-        const int f_hi = ch == p.NCHUNK - 1 ? kF : min(kF, (ch + 1) * p.CH - p.J + 1);
-        for (int f = f_done + cw; f < f_hi; f += kPCvtWarps) {
-          unsigned am = rowpre[f + p.J - 1];
-          for (int j = 0; j < p.J - 1; ++j) am = max(am, rowmax[f + j]);
-          const float amax = __uint_as_float(am);
-          const bool pos = amax > 0.f;
-          const float inv = pos ? 448.f / amax : 1.f;
-          if (lane == 0) scales[(k % kScaleRing) * kF + f] = (pos ? amax / 448.f : 1.f) / 448.f;
-          // the frame's samples: [s0, s0 + N) of the span, in chunks c0 and c0 + 1
-          const int s0 = f * p.H;
-          const int c0 = s0 / chunk_samples;
-          const int split = (c0 + 1) * chunk_samples - s0;  // samples before the next chunk
-          const uint32_t base0 = st0 + (uint32_t)((g + c0) % p.NS) * p.st_bytes + 4u * (uint32_t)(s0 - c0 * chunk_samples);
-          const uint32_t base1 = st0 + (uint32_t)((g + c0 + 1) % p.NS) * p.st_bytes;
-          const uint32_t arow = abase + (uint32_t)f * 16u;
-#pragma unroll 4
-          for (int j = lane; j < nq; j += 32) {
-            const int n = 4 * j;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (n < p.N) {
-              const uint32_t a = n < split ? base0 + 4u * (uint32_t)n : base1 + 4u * (uint32_t)(n - split);
-              asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                           : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                           : "r"(a));
-              clip_quad(v, s0 + n, nsamp);
+            float4 v[kFRows];
+#pragma unroll
+            for (int r = 0; r < kFRows; ++r) {
+              const int rl = rb + kPCvtWarpsF8 * r;
+              v[r] = lds128_if(sp + 16u * (uint32_t)(rl * h4 + j), rl < rows);
             }
-            const uint32_t w = pack_e4m3x4(v.x * inv, v.y * inv, v.z * inv, v.w * inv);
-            asm volatile("st.shared.b32 [%0], %1;" ::"r"(arow + (uint32_t)(j >> 2) * p.lbo_a + 4u * (uint32_t)(j & 3)),
-                         "r"(w));
+#pragma unroll
+            for (int r = 0; r < kFRows; ++r) {
+              const float4 x = tail ? clip_quad_sel(v[r], (r0 + rb + kPCvtWarpsF8 * r) * p.H + 4 * j, nsamp) : v[r];
+              const unsigned m = __float_as_uint(fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+              mf[r] = max(mf[r], m);
+              mp[r] = 4 * j < KL ? max(mp[r], m) : mp[r];
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < kFRows; ++r) {
+            const int rl = rb + kPCvtWarpsF8 * r;
+            const unsigned a = __reduce_max_sync(0xffffffffu, mf[r]);
+            const unsigned b = __reduce_max_sync(0xffffffffu, mp[r]);
+            if (lane == 0 && rl < rows) {
+              rowmax[r0 + rl] = a;
+              rowpre[r0 + rl] = b;
+            }
           }
         }
-        named_barrier(1, kPCvtThreads);
+        named_barrier(1, kPCvtThreadsF8);
+        // 2. the frames whose rows are all present now.  Each converter thread
+        //    sets up one frame: its multiplier 448 / amax and where its samples
+        //    are.  Such a frame starts in this chunk or in the previous one
+        //    (CH >= J - 1) and, if in the previous one, ends in this one.
+        const int f_hi = ch == p.NCHUNK - 1 ? kF : min(kF, (ch + 1) * p.CH - p.J + 1);
+        {
+          const int f = f_done + ct;  // at most kF frames per chunk
+          if (f < f_hi) {
+            unsigned am = rowpre[f + p.J - 1];
+            for (int j = 0; j < p.J - 1; ++j) am = max(am, rowmax[f + j]);
+            const float amax = __uint_as_float(am);
+            const bool pos = amax > 0.f;
+            finv[f] = pos ? 448.f / amax : 1.f;
+            scales[(k % kScaleRing) * kF + f] = (pos ? amax / 448.f : 1.f) / 448.f;
+            const bool here = f >= ch * p.CH;
+            const int c0 = here ? ch : ch - 1;
+            const int s0 = f * p.H;
+            const int prev = (g + ch + p.NS - 1) % p.NS;
+            fsplit[f] = (c0 + 1) * chunk_samples - s0;  // samples before chunk c0 + 1
+            fbase0[f] = st0 + (uint32_t)(here ? slot : prev) * p.st_bytes + 4u * (uint32_t)(s0 - c0 * chunk_samples);
+            fbase1[f] = sp;  // chunk ch: only a frame that started in chunk ch - 1 reaches it
+          }
+        }
+        named_barrier(1, kPCvtThreadsF8);
+        // 3. quantised frame rows.  A warp takes kFFrames frames at a time
+        //    (frames f0, f0 + 4, ...) and issues two float4 loads per frame
+        //    before converting; loads, clipping and stores are predicated.
+        for (int f0 = f_done + cw; f0 < f_hi; f0 += kPCvtWarpsF8 * kFFrames) {
+          float inv[kFFrames];
+          uint32_t base0[kFFrames], base1[kFFrames], arow[kFFrames];
+          int split[kFFrames], s0v[kFFrames];
+          bool live[kFFrames];
+#pragma unroll
+          for (int u = 0; u < kFFrames; ++u) {
+            const int f = f0 + kPCvtWarpsF8 * u;
+            live[u] = f < f_hi;
+            const int fc = live[u] ? f : f0;
+            inv[u] = finv[fc];
+            split[u] = fsplit[fc];
+            base0[u] = fbase0[fc];
+            base1[u] = fbase1[fc];
+            s0v[u] = fc * p.H;
+            arow[u] = abase + (uint32_t)fc * 16u;
+          }
+          for (int jb = lane, i = 0; jb < nq; jb += 64, ++i) {
+            const uint32_t col = lane_col + (uint32_t)(16 * i) * p.lbo_a;  // core column of j = jb, byte in it
+            float4 v[2][kFFrames];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int u = 0; u < kFFrames; ++u) {
+                const int n = 4 * (jb + 32 * h);
+                const uint32_t a = n < split[u] ? base0[u] + 4u * (uint32_t)n : base1[u] + 4u * (uint32_t)(n - split[u]);
+                v[h][u] = lds128_if(a, live[u] && n < p.N);
+              }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int u = 0; u < kFFrames; ++u) {
+                const int j = jb + 32 * h;
+                const float4 x = tail ? clip_quad_sel(v[h][u], s0v[u] + 4 * j, nsamp) : v[h][u];
+                const uint32_t w = pack_e4m3x4(x.x * inv[u], x.y * inv[u], x.z * inv[u], x.w * inv[u]);
+                sts32_if(arow[u] + col + (uint32_t)(8 * h) * p.lbo_a, w, live[u] && j < nq);
+              }
+          }
+        }
+        named_barrier(1, kPCvtThreadsF8);
         if (ch > 0) warp_arrive(pbar(p, c, B.s_empty + (g + ch - 1) % p.NS));
         f_done = f_hi;
       }
@@ -826,7 +925,7 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
 }
 
 template <int NCH, bool MFCC, bool MLP, int PREC = MELT_BF16>
-__global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(pair_threads(MLP, PREC), 1) melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
   constexpr int EPW = pair_epi_warps(MLP);
   constexpr int kPMmaWarp = EPW, kPBWarp = EPW + 1, kPProdWarp = EPW + 2, kPCvtWarp0 = EPW + 3;
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -847,10 +946,10 @@ __global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(cons
     auto bar = [&](int i) { return sbase + p.off_bar + 8 * i; };
     for (int i = 0; i < p.NS; ++i) {
       mbar_init(bar(B.s_full + i), 1);
-      mbar_init(bar(B.s_empty + i), kPCvtWarps);
+      mbar_init(bar(B.s_empty + i), pair_cvt_warps(PREC));
     }
     for (int i = 0; i < p.ZB; ++i) {
-      mbar_init(bar(B.z_full + i), 2 * kPCvtWarps);  // converters of both CTAs (even CTA's copy is used)
+      mbar_init(bar(B.z_full + i), 2 * pair_cvt_warps(PREC));  // converters of both CTAs (even CTA's copy is used)
       mbar_init(bar(B.z_empty + i), 1);
     }
     mbar_init(bar(B.b_full), 1);
@@ -862,7 +961,7 @@ __global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(cons
     mbar_init(bar(B.h_full), 1);
     mbar_init(bar(B.a2_full), 2 * EPW);
     mbar_init(bar(B.y_full), 1);
-    for (int i = 0; i < kScaleRing; ++i) mbar_init(bar(B.sc_full + i), kPCvtWarps);
+    for (int i = 0; i < kScaleRing; ++i) mbar_init(bar(B.sc_full + i), pair_cvt_warps(PREC));
     mbar_init(bar(B.drain), 1);
     for (int i = 0; i < kSchedRing; ++i) {
       mbar_init(bar(B.sched_full + i), 1);           // the even CTA's producer (here or remote)
