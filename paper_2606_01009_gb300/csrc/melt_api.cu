@@ -38,7 +38,6 @@ struct Staging {
   int key_batch = -1;
   std::vector<int64_t> key_offsets, key_lengths;
   int64_t rows = 0;            // output rows of the batch
-  int sched_w = 0, sched_unit = 0;  // schedule the tile order was balanced for
 };
 
 }  // namespace
@@ -59,8 +58,6 @@ struct melt_basis {
   Staging staging[kStagingSlots];
   int next_slot = 0;
   std::vector<TileDesc> plan;  // host scratch for planning
-  std::vector<TileDesc> plan_tmp;     // balancing scratch
-  std::vector<int32_t> plan_order;    // balancing scratch
   int64_t plan_rows = 0;       // output rows of the planned batch
   const melt_mlp* correction = nullptr;  // applied in place after the log-Mel (not owned)
   HostPipe* host_pipe = nullptr;         // melt_forward_host buffers and streams
@@ -281,27 +278,12 @@ melt_status forward_impl(melt_basis* b, const float* wave, const int64_t* offset
   if (batch == 0) return MELT_OK;
   cudaStream_t stream = (cudaStream_t)stream_v;
   Staging* slot = cached_plan(b, offsets, lengths, batch);
-  int unit = 1;
-  if (slot) {
-    const int W = tile_workers(b, (long long)slot->n, mode, &unit);
-    if (W != slot->sched_w || unit != slot->sched_unit) {
-      slot->key_batch = -1;  // ordered for another schedule (the plan or the mode changed)
-      slot = nullptr;
-    }
-  }
   if (!slot) {
     melt_status st = plan_tiles(b, offsets, lengths, batch);
     if (st != MELT_OK) return st;
     if (b->plan.empty()) return MELT_OK;
-    const long long n = (long long)b->plan.size();
-    const int W = tile_workers(b, n, mode, &unit);
-    b->plan_tmp.resize(b->plan.size());
-    b->plan_order.resize(b->plan.size());
-    balance_tiles(b->plan.data(), n, unit, W, b->plan_tmp.data(), b->plan_order.data());
     st = stage_plan(b, offsets, lengths, batch, stream, &slot);
     if (st != MELT_OK) return st;
-    slot->sched_w = W;
-    slot->sched_unit = unit;
   }
   if (slot->n == 0) return MELT_OK;
   const int n_tiles = (int)slot->n;
@@ -373,13 +355,6 @@ long long plan_tiles_into(const melt_basis* b, const int64_t* offsets, const int
     row += frames_of(b, L);
   }
   return n;
-}
-
-int tile_workers(const melt_basis* b, long long n_tiles, int mode, int* unit) {
-  *unit = 1;
-  if (b->precision == MELT_FP32 || mode == 1)  // the SIMT kernel: one CTA per tile, grid <= SMs
-    return (int)std::max<long long>(1, std::min<long long>(n_tiles, b->sm_count));
-  return tc_workers(&b->tc, n_tiles, b->sm_count, unit);
 }
 
 melt_status launch_forward_tiles(melt_basis* b, const float* wave, const TileDesc* d_tiles,

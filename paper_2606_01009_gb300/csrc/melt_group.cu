@@ -59,8 +59,6 @@ struct melt_group {
   unsigned long long tick = 0;
   cudaStream_t capture = nullptr;  // private stream the graphs are captured on
   std::vector<TileDesc> host;      // planning scratch
-  std::vector<TileDesc> tmp;       // balancing scratch
-  std::vector<int32_t> order;      // balancing scratch
   std::vector<int64_t> rows;       // planning scratch: first output row of each clip
 };
 
@@ -129,13 +127,6 @@ melt_status make_entry(melt_group* g, const float* wave, const int64_t* offsets,
       delete e;
       return MELT_ERR_ARG;
     }
-    // this basis's tiles in its kernel's balanced work order
-    int unit = 1;
-    const int W = tile_workers(g->bases[k], e->count[k], 0, &unit);
-    g->tmp.resize((size_t)e->count[k]);
-    g->order.resize((size_t)e->count[k]);
-    balance_tiles(g->host.data() + e->first[k], e->count[k], unit, W, g->tmp.data(),
-                  g->order.data());
   }
   e->wave = wave;
   e->out = out;

@@ -139,18 +139,6 @@ melt_status plan_host(melt_basis* b, HostPipe* hp, const int64_t* offsets, const
   }
   for (auto& t : hp->h_tiles)
     if (t.n_frames > kTileFrames || t.n_frames < 1) return MELT_ERR_ARG;
-  // each chunk's tiles in the kernels' balanced work order
-  {
-    std::vector<TileDesc> tmp;
-    std::vector<int32_t> order;
-    for (const Chunk& ch : hp->chunks) {
-      int unit = 1;
-      const int W = tile_workers(b, ch.tiles, 0, &unit);
-      tmp.resize((size_t)ch.tiles);
-      order.resize((size_t)ch.tiles);
-      balance_tiles(hp->h_tiles.data() + ch.tile0, ch.tiles, unit, W, tmp.data(), order.data());
-    }
-  }
   // device buffers: synchronise the slots before replacing anything they may use
   for (int i = 0; i < kHostSlots; ++i) HCUDA(cudaStreamSynchronize(hp->streams[i]));
   if (wave_max > hp->wave_cap) {

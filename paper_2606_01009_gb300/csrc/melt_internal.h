@@ -62,28 +62,6 @@ long long plan_tiles_into(const melt_basis* b, const int64_t* offsets, const int
 melt_status launch_forward_tiles(melt_basis* b, const float* wave, const TileDesc* d_tiles,
                                  int n_tiles, float* out, int64_t rows, cudaStream_t stream);
 
-// Work order of the persistent kernels.  Every kernel walks its tile list
-// on a static schedule: worker w (a CTA, or a two-CTA cluster in the pair
-// layout) takes units w, w + W, w + 2W, ..., a unit being one tile, or two
-// consecutive tiles for CTA pairs.  In clip order a clip's short last tile
-// shares a pair with a full one, and some workers run a whole round more
-// than others.  tile_workers gives (W, unit) for n_tiles tiles under the
-// basis's current plan (mode 1: the raw-component SIMT launch).
-// balance_tiles permutes t[0..n) for that schedule: tiles sorted by length,
-// so short tiles share pairs; units handed out longest first, each to the
-// worker with the lowest projected load; each worker's units in the order
-// handed out, so its short units come last.  Every tile carries its own
-// input offset and output row, so the features do not depend on the order.
-// tmp and order are caller scratch of n entries; nothing is allocated.
-// W above kMaxBalanceWorkers leaves the list as it is.
-constexpr int kMaxBalanceWorkers = 1024;
-// Cost of a tile in frames beyond its own: the MMAs and the hand-offs of a
-// tile do not shrink with its frame count (a 54-frame tile costs about 0.55
-// of a full one).
-constexpr int kTileFixedFrames = 40;
-int tile_workers(const melt_basis* b, long long n_tiles, int mode, int* unit);
-void balance_tiles(TileDesc* t, long long n, int unit, int W, TileDesc* tmp, int32_t* order);
-
 // Frames of a clip of `len` samples under basis b: floor((len - N)/H) + 1, 0 if len < N.
 int64_t basis_frames(const melt_basis* b, int64_t len);
 

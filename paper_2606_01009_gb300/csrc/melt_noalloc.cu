@@ -15,9 +15,8 @@
 // library holds until the process exits.  Its device address is looked up
 // once per device with cudaGetSymbolAddress; host code never passes the
 // symbol itself to a kernel.  The tiles are planned into a file-scope host
-// array, put in the kernels' balanced work order with file-scope scratch, and
-// copied with cudaMemcpyAsync from that pageable buffer (the call returns once
-// the driver has staged the bytes).
+// array and copied with cudaMemcpyAsync from that pageable buffer (the call
+// returns once the driver has staged the bytes).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -36,8 +35,6 @@ static __device__ __align__(256) TileDesc g_noalloc_tiles[kMaxTiles];
 std::mutex g_mu;                           // guards the host array and the per-device table
 TileDesc* g_dev_tiles[kMaxDevices] = {};   // device address of g_noalloc_tiles, per device
 TileDesc g_host_tiles[kMaxTiles];          // host-side plan of the current call
-TileDesc g_host_tmp[kMaxTiles];            // balancing scratch
-int32_t g_host_order[kMaxTiles];           // balancing scratch
 
 }  // namespace
 
@@ -63,9 +60,6 @@ extern "C" melt_status melt_forward_noalloc(melt_basis* basis, const float* wave
   if (n == 0) return MELT_OK;
   const TileDesc& last = g_host_tiles[n - 1];  // planned in output-row order
   const int64_t rows = last.out_row + last.n_frames;
-  int unit = 1;
-  const int W = tile_workers(basis, n, 0, &unit);
-  balance_tiles(g_host_tiles, n, unit, W, g_host_tmp, g_host_order);
   cudaStream_t stream = (cudaStream_t)stream_v;
   // Every field of the n descriptors is written here; nothing in the array
   // has to start at zero.

@@ -435,20 +435,6 @@ bool tc_current_plan(const TcBasis* tb, melt_plan* out) {
   return true;
 }
 
-int tc_workers(const TcBasis* tb, long long n_tiles, int sm_count, int* unit) {
-  *unit = 1;
-  if (n_tiles < 1 || sm_count < 1) return 1;
-  TcParams p;
-  std::memset(&p, 0, sizeof(p));
-  if (plan_smem(tb, p, tb->n_mfcc) && p.NS > 0) {
-    // the launch below: as many two-CTA clusters as are resident, at most one per pair
-    *unit = 2;
-    const int clusters = tb->pair_clusters > 0 ? tb->pair_clusters : std::max(1, sm_count / 2);
-    return (int)std::min<long long>((n_tiles + 1) / 2, clusters);
-  }
-  return (int)std::min<long long>(n_tiles, sm_count);
-}
-
 cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream) {
   TcParams p;
   std::memset(&p, 0, sizeof(p));

@@ -63,10 +63,5 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64);
 int tc_max_mfcc();  // largest n_mfcc the tensor-core epilogue supports
 void tc_free(TcBasis* tb);
 cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream);
-// Static schedule tc_launch uses for n_tiles tiles under the current plan:
-// returns the number of workers W (CTAs, or two-CTA clusters) and sets
-// *unit to the tiles per work unit (1, or 2 for CTA pairs).  Worker w takes
-// units w, w + W, w + 2W, ...
-int tc_workers(const TcBasis* tb, long long n_tiles, int sm_count, int* unit);
 
 }  // namespace melt
