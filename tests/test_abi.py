@@ -61,3 +61,27 @@ def test_host_only_calls(lib):
     assert lib.lib.melt_basis_create(16000.0, 400, 160, 0, 0.0, 8000.0, 0, ctypes.byref(h)) == lib.MELT_ERR_ARG
     assert lib.lib.melt_basis_create(16000.0, 400, 160, 80, 0.0, 9000.0, 0, ctypes.byref(h)) == lib.MELT_ERR_ARG
     assert lib.lib.melt_basis_create(16000.0, 400, 160, 80, 0.0, 8000.0, 0, None) == lib.MELT_ERR_ARG
+
+
+def test_plan_struct_matches_binding(lib, tmp_path):
+    """melt_plan in include/melt.h and the binding's MeltPlan agree field by field."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in lib.MeltPlan._fields_]
+    src = tmp_path / "plan_layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "melt.h"\n'
+        "int main(void) {\n"
+        '  printf("size %zu\\n", sizeof(melt_plan));\n'
+        + "".join(f'  printf("{f} %zu\\n", offsetof(melt_plan, {f}));\n' for f in fields)
+        + "  return 0;\n}\n")
+    exe = tmp_path / "plan_layout"
+    subprocess.run([cc, "-std=c99", "-I", HEADER_DIR, str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    assert int(got["size"]) == ctypes.sizeof(lib.MeltPlan)
+    for f in fields:
+        assert int(got[f]) == getattr(lib.MeltPlan, f).offset, f
