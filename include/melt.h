@@ -252,6 +252,33 @@ melt_status melt_forward_host(melt_basis* basis, const float* wave, const int64_
                               const int64_t* lengths, int batch, float* out, void* stream);
 
 /*
+ * melt_pad_reflect - centred framing.  The paper frames each clip from its
+ *   first sample (Sec. III-A, Eq. 6: no padding).  Frontends built on a
+ *   centred STFT pad each clip with N/2 samples of reflection at both ends,
+ *   so that frame t is centred on sample t*H and a clip of L samples gives
+ *   floor(L/H) + 1 frames (for even N).  This call writes that padded batch;
+ *   melt_forward on it (lengths + 2*pad) gives the centred features.
+ *   Clip b of L = lengths[b] samples becomes y[0 .. L + 2 pad) with
+ *   y[i] = x[r(i - pad)], r(j) = -j for j < 0, 2 (L-1) - j for j >= L, j
+ *   otherwise (reflection without repeating the edge sample).
+ *   wave         device float[], clip b at wave[offsets[b] ..] (NULL offsets:
+ *                packed at 4-float alignment, as for melt_forward)
+ *   lengths      host int64[batch]; every clip needs lengths[b] > pad
+ *   pad          samples added at each end (N/2 for centred frames), >= 0
+ *   out          device float[], padded clip b at out[out_offsets[b] ..],
+ *                lengths[b] + 2 pad floats; it must not overlap wave
+ *   out_offsets  host int64[batch] (NULL: packed at 4-float alignment, which
+ *                keeps every padded clip's start 16-byte aligned for
+ *                melt_forward)
+ *   Asynchronous on `stream`; allocates nothing (the clip descriptors travel
+ *   in the kernels' parameters, 1000 clips per launch).  Errors:
+ *   MELT_ERR_ARG for bad arguments or a clip of at most pad samples (nothing
+ *   is launched), MELT_ERR_CUDA for a failed launch.
+ */
+melt_status melt_pad_reflect(const float* wave, const int64_t* offsets, const int64_t* lengths,
+                             int batch, int pad, float* out, const int64_t* out_offsets, void* stream);
+
+/*
  * melt_forward_components - debug form: the raw projection (Eq. 6) for every
  * frame, out = device float[sum_b T_b * 2M]: per frame M values of R then M of I.
  * Only MELT_FP32 bases.  Arguments otherwise as melt_forward.

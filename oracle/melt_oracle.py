@@ -31,6 +31,10 @@ Readings where the paper is silent or ambiguous (each listed in the design doc):
 * Framing: no centring or padding; T = floor((L - N)/H) + 1 frames, 0 if
   L < N; frame t holds samples tH .. tH+N-1; the phase origin n = 0 is the
   frame start.
+* Centred framing (an option beyond the paper, as in frontends built on a
+  centred STFT): the clip is first padded with N/2 samples of reflection at
+  both ends (no repeated edge sample), then framed as above, so frame t is
+  centred on sample tH and there are floor(L/H) + 1 frames for even N.
 * eps is additive (Eq. 8 as written), natural log.
 * No normalisation of the basis (Eq. 5 has none).
 * DCT-II: D[k, m] = sqrt((2 - [k = 0]) / M) cos(pi k (2m + 1) / (2M)).
@@ -93,6 +97,16 @@ def frame_signal(x: np.ndarray, n_fft: int, hop: int, frames=None) -> np.ndarray
     if idx.size and (idx.min() < 0 or idx.max() >= T):
         raise IndexError("frame index out of range")
     return x[idx[:, None] * hop + np.arange(n_fft)[None, :]] if idx.size else np.zeros((0, n_fft))
+
+
+def reflect_pad(x: np.ndarray, pad: int) -> np.ndarray:
+    """x padded with ``pad`` samples of reflection at both ends: y[i] = x[|i - pad|]
+    on the left, mirrored about the last sample on the right (no repeated edge
+    sample).  Needs pad < len(x)."""
+    x = np.asarray(x, dtype=np.float64)
+    if pad >= x.shape[0]:
+        raise ValueError("reflection needs pad < len(x)")
+    return np.pad(x, (pad, pad), mode="reflect")
 
 
 # --------------------------------------------------------------------------
@@ -167,6 +181,12 @@ def melt_clip(x, spec: MelTSpec, frames=None) -> np.ndarray:
     R, I = melt_components(x, spec, frames)
     out = melt_log(dmp_energy(R, I), spec.eps)
     return mfcct(out, spec.D) if spec.D is not None else out
+
+
+def melt_clip_centred(x, spec: MelTSpec) -> np.ndarray:
+    """The features of one clip with centred framing: reflection padding of N/2
+    samples at both ends, then Eq. 8 / Eq. 9 on the padded clip."""
+    return melt_clip(reflect_pad(x, spec.n_fft // 2), spec)
 
 
 def melt_batch(clips, spec: MelTSpec) -> np.ndarray:

@@ -54,6 +54,7 @@ SIGNATURES = {
     "melt_forward_components": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
     "melt_forward_noalloc": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
     "melt_forward_host": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
+    "melt_pad_reflect": (C.c_int, [_VP, _I64P, _I64P, C.c_int, C.c_int, _VP, _I64P, _VP]),
     "melt_plan_get": (C.c_int, [_VP, _VP]),
     "melt_plan_set": (C.c_int, [_VP, _VP]),
     "melt_autotune": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP, C.c_int, _VP]),
@@ -210,6 +211,25 @@ def melt_forward_noalloc(basis, wave, offsets, lengths, out, stream=None):
     outp = out if isinstance(out, int) else out.data_ptr()
     _check(lib.melt_forward_noalloc(basis, C.c_void_p(wp), op, lp, int(lens.shape[0]), C.c_void_p(outp),
                                     _stream_ptr(stream)), "melt_forward_noalloc")
+
+
+def melt_pad_reflect(wave, offsets, lengths, pad, out, out_offsets=None, stream=None):
+    """Reflection-pad every clip by ``pad`` samples at both ends (centred framing)."""
+    lens, lp = _i64(lengths)
+    offs, op = _i64(offsets)
+    oo, oop = _i64(out_offsets)
+    wp = wave if isinstance(wave, int) else wave.data_ptr()
+    outp = out if isinstance(out, int) else out.data_ptr()
+    _check(lib.melt_pad_reflect(C.c_void_p(wp), op, lp, int(lens.shape[0]), int(pad), C.c_void_p(outp), oop,
+                                _stream_ptr(stream)), "melt_pad_reflect")
+
+
+def padded_layout(lengths, pad):
+    """Lengths, packed offsets and total floats of a batch after melt_pad_reflect."""
+    lens = np.asarray(lengths, dtype=np.int64) + 2 * int(pad)
+    sizes = (lens + 3) // 4 * 4
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64) if len(lens) else lens
+    return lens, offs, int(sizes.sum())
 
 
 def melt_forward_host(basis, wave, offsets, lengths, out, stream=None):
@@ -399,16 +419,23 @@ class Frontend:
     """
 
     def __init__(self, sr=16000.0, n_fft=400, hop=160, n_mels=80, fmin=0.0, fmax=8000.0,
-                 window=MELT_WIN_HANN_PERIODIC, precision="fp32", n_mfcc=0, eps=1e-10, freqs=None):
+                 window=MELT_WIN_HANN_PERIODIC, precision="fp32", n_mfcc=0, eps=1e-10, freqs=None,
+                 center=False):
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         if freqs is None:
             self.handle = melt_basis_create_ex(sr, n_fft, hop, n_mels, fmin, fmax, window, p, n_mfcc, eps)
         else:
             self.handle = melt_basis_create_freqs(sr, n_fft, hop, freqs, window, p, n_mfcc, eps)
         self.n_out = melt_num_outputs(self.handle)
+        # centred framing: every clip reflection-padded by n_fft // 2 first
+        # (melt_pad_reflect into one buffer the Frontend keeps; calls on one
+        # Frontend must then be ordered on one stream)
+        self.center = bool(center)
+        self.pad = int(n_fft) // 2 if center else 0
+        self._pad_buf = None
 
     def num_frames(self, length) -> int:
-        return melt_num_frames(self.handle, length)
+        return melt_num_frames(self.handle, int(length) + 2 * self.pad)
 
     def total_frames(self, lengths) -> int:
         return sum(self.num_frames(int(L)) for L in lengths)
@@ -418,6 +445,13 @@ class Frontend:
         if out is None:
             out = torch.empty((self.total_frames(lengths), self.n_out), device=wave.device,
                               dtype=torch.float32)
+        if self.center:
+            lens, offs, total = padded_layout(lengths, self.pad)
+            if self._pad_buf is None or self._pad_buf.numel() < total or self._pad_buf.device != wave.device:
+                self._pad_buf = torch.empty(max(total, 4), device=wave.device, dtype=torch.float32)
+            melt_pad_reflect(wave, offsets, lengths, self.pad, self._pad_buf, offs, stream)
+            melt_forward(self.handle, self._pad_buf, offs, lens, out, stream)
+            return out
         melt_forward(self.handle, wave, offsets, lengths, out, stream)
         return out
 
@@ -441,6 +475,8 @@ class GroupedFrontend:
 
     def __init__(self, frontends, graphs=True):
         self.frontends = list(frontends)
+        if any(fe.center for fe in self.frontends):
+            raise ValueError("grouped launches frame clips from their first sample (center=False)")
         self.n_out = self.frontends[0].n_out
         self.handle = melt_group_create(self.frontends, 0 if graphs else MELT_GROUP_NO_GRAPH)
 

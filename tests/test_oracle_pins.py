@@ -299,3 +299,46 @@ def test_golden_paper_figures():
     assert round(O.gemm_flops_per_frame(g["n_fft"], g["n_mels"])
                  / O.materialised_bytes_per_frame(g["n_fft"], g["n_mels"])) == g["ai_melt_flop_per_byte"]
     assert O.rmse_db(np.full(4, g["delta_nat"]), np.zeros(4)) == pytest.approx(g["delta_db"], abs=0.005)
+
+
+# ------------------------------------------------- centred framing (option)
+def test_reflect_pad_hand_example():
+    # reflection about the first and the last sample, which are not repeated
+    np.testing.assert_array_equal(O.reflect_pad(np.array([1.0, 2, 3, 4, 5]), 2),
+                                  [3.0, 2, 1, 2, 3, 4, 5, 4, 3])
+    np.testing.assert_array_equal(O.reflect_pad(np.array([7.0, 8]), 1), [8.0, 7, 8, 7])
+    with pytest.raises(ValueError):
+        O.reflect_pad(np.array([1.0, 2]), 2)
+
+
+def test_centred_frame_count():
+    # floor(L/H) + 1 frames for even N: a centred 30 s clip at 16 kHz, hop 160,
+    # has 3001 frames (frontends that keep 3000 drop the last one)
+    spec = O.MelTSpec()
+    assert O.melt_clip_centred(np.zeros(480000), spec).shape == (3001, 80)
+    for L in (201, 400, 1000, 16000, 16159):
+        assert O.melt_clip_centred(np.ones(L), spec).shape[0] == L // 160 + 1
+
+
+def test_centred_impulse_closed_form():
+    # an impulse at sample tH sits at the centre n = N/2 of centred frame t,
+    # where the periodic Hann window is exactly 1: S = 1 in every band; frames
+    # t -+ 1 see it at n = N/2 +- H, so S = w[N/2 +- H]^2 exactly
+    spec = O.MelTSpec(eps=0.0)
+    t, H, N = 20, 160, 400
+    x = np.zeros(8000)
+    x[t * H] = 1.0
+    out = O.melt_clip_centred(x, spec)
+    np.testing.assert_allclose(out[t], 0.0, atol=1e-12)
+    w = O.hann(N, True)
+    np.testing.assert_allclose(out[t - 1], 2 * math.log(w[N // 2 + H]), atol=1e-12)
+    np.testing.assert_allclose(out[t + 1], 2 * math.log(w[N // 2 - H]), atol=1e-12)
+
+
+def test_centring_is_a_shift_when_half_frame_is_a_hop():
+    # with N = 2H the padding is exactly one hop: centred frame t + 1 is
+    # uncentred frame t wherever both are defined
+    spec = O.MelTSpec(n_fft=320, hop=160)
+    x = np.random.default_rng(12).standard_normal(5000)
+    c, u = O.melt_clip_centred(x, spec), O.melt_clip(x, spec)
+    np.testing.assert_allclose(c[1:1 + u.shape[0]], u, atol=1e-12)
