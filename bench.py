@@ -94,6 +94,8 @@ def parse():
                     help="also time the correction MLP: fused in the epilogue vs a separate pass")
     ap.add_argument("--forms", action=argparse.BooleanOptionalAction, default=True,
                     help="also time every other operand form")
+    ap.add_argument("--stft", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time torch.stft + Mel matmul on the same GPU (context)")
     return ap.parse_args()
 
 
@@ -523,6 +525,66 @@ def time_grouped(args, dev, steps=20, warmup=3, per_clip_steps=2):
     return res
 
 
+def htk_mel_filterbank(sr, n_fft, n_mels, fmin, fmax):
+    """Triangular Mel filterbank on the HTK scale, [n_mels, n_fft // 2 + 1],
+    peak 1 at each of the M interior points of M + 2 Mel-uniform points: the
+    Mel step of the conventional pipeline timed as context."""
+    mel = lambda f: 2595.0 * np.log10(1.0 + f / 700.0)
+    hz = lambda m: 700.0 * (10.0 ** (m / 2595.0) - 1.0)
+    pts = hz(np.linspace(mel(fmin), mel(fmax), n_mels + 2))
+    bins = np.arange(n_fft // 2 + 1) * sr / n_fft
+    fb = np.zeros((n_mels, bins.size))
+    for m in range(n_mels):
+        lo, c, hi = pts[m], pts[m + 1], pts[m + 2]
+        fb[m] = np.clip(np.minimum((bins - lo) / (c - lo), (hi - bins) / (hi - c)), 0.0, None)
+    return fb
+
+
+def time_torch_stft(W, dev, steps=20, warmup=3, eps=1e-10):
+    """Context, not a product path: the conventional pipeline on the same GPU
+    and clips - torch.stft (cuFFT, no centring), |X|^2, a dense Mel matmul and
+    the log, in FP32 - timed like the headline (CUDA events around the loop,
+    two input copies rotated).  Its output is [B, M, T] rather than frame-major."""
+    import torch
+    cfg = W.cfg
+    n_fft, hop, M = cfg["n_fft"], cfg["hop"], cfg["n_mels"]
+    lens, offs = W.lens, W.offs
+    B, L = len(lens), int(lens[0])
+    if not (np.all(lens == L) and np.array_equal(offs, np.arange(B, dtype=np.int64) * L)):
+        return {"skipped": "the batch is not B clips of one length packed back to back"}
+    x = W.wave_h[: B * L].view(B, L)
+    xs = [x.to(dev) for _ in range(2)]
+    win = torch.hann_window(n_fft, periodic=True, dtype=torch.float32, device=dev)
+    fb = torch.from_numpy(htk_mel_filterbank(cfg["sr"], n_fft, M, cfg["fmin"], cfg["fmax"])).to(dev, torch.float32)
+
+    def step(i):
+        X = torch.stft(xs[i % 2], n_fft, hop_length=hop, win_length=n_fft, window=win, center=False,
+                       return_complex=True)
+        return torch.log(torch.matmul(fb, X.real.square() + X.imag.square()) + eps)
+
+    T = (L - n_fft) // hop + 1 if L >= n_fft else 0
+    for i in range(warmup):
+        step(i)
+    if dev.type == "cuda":
+        torch.cuda.synchronize(dev)
+        stream = torch.cuda.current_stream(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(steps):
+            step(i)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / steps
+    else:
+        t0 = time.perf_counter()
+        for i in range(steps):
+            step(i)
+        ms = (time.perf_counter() - t0) * 1e3 / steps
+    return {"pipeline": "torch.stft (cuFFT) + |X|^2 + dense HTK Mel matmul + log, FP32, no centring",
+            "frames_per_step": B * T, "ms_per_step": ms, "frames_per_s": B * T / (ms / 1e3),
+            "device": str(dev)}
+
+
 def time_correction(args, W, dev, steps=200, warmup=5):
     """BF16 log-Mel with the per-frame correction MLP (80 -> 256 -> 80) attached:
     plain, fused in the kernel's epilogue, and as a separate FP32 pass after it."""
@@ -605,6 +667,13 @@ def main():
                 res["grouped"] = time_grouped(args, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
             except Exception as e:  # reported, not fatal: the headline line above stands
                 res["grouped"] = {"error": str(e)}
+        if args.stft:
+            import torch
+            try:
+                res["torch_stft_context"] = time_torch_stft(
+                    W, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
+            except Exception as e:  # reported, not fatal: the headline line above stands
+                res["torch_stft_context"] = {"error": str(e)}
         print(json.dumps(res, default=_jsonable), flush=True)
     if world > 1:
         import torch.distributed as dist

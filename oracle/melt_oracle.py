@@ -20,7 +20,7 @@ the paper's Sec. III-A "Matmul-Native Mel Frontends":
     Eq. 8  MelT               log(S + eps)
     Eq. 9  MFCCT              log(S + eps) D^T, D orthonormal DCT-II [K x M]
 
-Readings where the paper is silent or ambiguous (each listed in the design doc):
+Readings where the paper is silent or ambiguous:
 
 * Frequencies: the M analysis frequencies are the M interior points of M+2
   Mel-uniform points on [f_min, f_max] (the centres of an HTK triangular
