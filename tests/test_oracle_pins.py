@@ -328,7 +328,8 @@ def test_centred_impulse_closed_form():
     t, H, N = 20, 160, 400
     x = np.zeros(8000)
     x[t * H] = 1.0
-    out = O.melt_clip_centred(x, spec)
+    with np.errstate(divide="ignore"):  # frames that miss the impulse have S = 0 and eps = 0
+        out = O.melt_clip_centred(x, spec)
     np.testing.assert_allclose(out[t], 0.0, atol=1e-12)
     w = O.hann(N, True)
     np.testing.assert_allclose(out[t - 1], 2 * math.log(w[N // 2 + H]), atol=1e-12)
