@@ -137,9 +137,13 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.seek(0)
-        sm, mx, reasons = [], [], set()
+        return self.parse(self.f.read())
+
+    @staticmethod
+    def parse(text):
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.f.read().splitlines():
+        for line in text.splitlines():
             p = [x.strip() for x in line.split(",")]
             if len(p) < 9:
                 continue
@@ -148,12 +152,17 @@ class ClockSampler:
                 mx.append(float(p[2]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(p[3]))
+            except ValueError:
+                pass
             for nm, v in zip(names, p[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(pw) if pw else None}
 
 
 # ------------------------------------------------------------ workload
@@ -370,6 +379,20 @@ def accuracy_vs_oracle(W, forms, cfg, mfcc, n_clips=2):
     return acc, f"first {n_clips} clips ({rows} frames) vs the FP64 oracle"
 
 
+def energy_estimate(r):
+    """Joules per frame from the board power sampled around the timed region
+    (median of the nvidia-smi power.draw samples x launch time / frames).  An
+    estimate, beside frames/s: the readings average over a window that takes
+    in the idle edges of a short region."""
+    w = (r.get("clocks") or {}).get("power_w_median")
+    if not w or not r.get("T"):
+        return None
+    j = w * (r["launch_ms"] / 1e3) / r["T"]
+    return {"watts_median": w, "joules_per_frame": j, "frames_per_joule": 1.0 / j,
+            "samples": r["clocks"].get("samples"),
+            "method": "median nvidia-smi power.draw over the timed region x launch time / frames (estimate)"}
+
+
 def run_melt(args, rank, world):
     import torch
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -409,6 +432,7 @@ def run_melt(args, rank, world):
         "gpu_launches": args.steps,
         "roofline": roofline(cfg, W, head, peaks, peak_kind),
         "clocks": {k: head["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples")},
+        "energy": energy_estimate(head),
     }
     if args.forms:
         res["forms"] = {}
@@ -420,7 +444,8 @@ def run_melt(args, rank, world):
             res["forms"][name] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "steps": r["steps"],
                                   "roofline_frac": rf["frac"], "bound": rf["bound"],
                                   "achieved": rf["achieved"], "unit": rf["unit"],
-                                  "clocks_sm_mhz": r["clocks"]["sm_mhz"]}
+                                  "clocks_sm_mhz": r["clocks"]["sm_mhz"],
+                                  "energy": energy_estimate(r)}
     return res, W, forms
 
 

@@ -58,3 +58,24 @@ def test_fp32_alu_roofline():
     peak = 152 * 128 * 2 * 2070e6 / 1e12  # 80.5 TFLOP/s
     assert out["bound"] == "alu" and out["peak"] == pytest.approx(peak)
     assert out["frac"] == pytest.approx(2 * 400 * 160 * 191872 / 0.885e-3 / 1e12 / peak)
+
+
+def test_clock_and_power_sample_parsing():
+    text = "\n".join([
+        "0, 2070, 2070, 612.50, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2070, 2070, 905.00, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 1980, 2070, [N/A], 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ])
+    ck = bench.ClockSampler.parse(text)
+    assert ck["samples"] == 3 and ck["sm_mhz"] == 2070.0 and ck["sm_max_mhz"] == 2070.0
+    assert ck["reasons"] == ["sw_power_cap"]
+    assert ck["power_w_median"] == pytest.approx((612.5 + 905.0) / 2)
+
+
+def test_energy_estimate():
+    r = {"T": 191872, "launch_ms": 0.041, "clocks": {"power_w_median": 800.0, "samples": 9}}
+    e = bench.energy_estimate(r)
+    assert e["joules_per_frame"] == pytest.approx(800.0 * 41e-6 / 191872)
+    assert e["frames_per_joule"] == pytest.approx(191872 / (800.0 * 41e-6))
+    assert bench.energy_estimate({"T": 5, "launch_ms": 1.0, "clocks": {"power_w_median": None}}) is None
