@@ -415,7 +415,9 @@ def melt_version() -> str:
 class Frontend:
     """Owns one melt_basis; calls melt_forward on torch tensors.
 
-    ``precision`` is one of "fp32", "bf16", "bf16x3", "fp8".
+    ``precision`` is one of "fp32", "bf16", "bf16x3", "fp8".  ``center=True``
+    reflection-pads every clip by n_fft // 2 first (melt_pad_reflect), giving
+    floor(L / hop) + 1 frames per clip, each centred on sample t * hop.
     """
 
     def __init__(self, sr=16000.0, n_fft=400, hop=160, n_mels=80, fmin=0.0, fmax=8000.0,
