@@ -85,3 +85,15 @@ def test_plan_struct_matches_binding(lib, tmp_path):
     assert int(got["size"]) == ctypes.sizeof(lib.MeltPlan)
     for f in fields:
         assert int(got[f]) == getattr(lib.MeltPlan, f).offset, f
+
+
+def test_padded_layout(lib):
+    """Lengths, packed offsets and size of a batch after melt_pad_reflect: every
+    padded clip starts on a 16-byte boundary, as melt_forward requires."""
+    lens, offs, total = lib.padded_layout([201, 5, 4000], 200)
+    assert lens.tolist() == [601, 405, 4400]
+    assert offs.tolist() == [0, 604, 1012]
+    assert total == 604 + 408 + 4400
+    assert all(o % 4 == 0 for o in offs)
+    lens, offs, total = lib.padded_layout([], 200)
+    assert lens.size == 0 and total == 0
