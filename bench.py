@@ -250,6 +250,20 @@ class Workload:
         return self.waves[:copies], outs, copies
 
 
+def whole_job(ms_total, frames_per_step, steps, world, dev):
+    """(slowest rank's timed region in ms, whole-job frames/s).  Every rank
+    times its own replica of the workload (weak scaling); the job takes as long
+    as its slowest rank, which processed world x frames_per_step x steps frames
+    in all.  With world > 1 this is a collective: every rank must call it."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms_total)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    return ms_total, world * frames_per_step * steps / (ms_total / 1e3)
+
+
 def time_form(args, W, precision, steps, warmup, world, want_e2e):
     """Time melt_forward for one operand form; returns a dict of measurements."""
     import ctypes as C
@@ -301,13 +315,10 @@ def time_form(args, W, precision, steps, warmup, world, want_e2e):
     fe.sync(stream)
     ms_total = e0.elapsed_time(e1)
     launch_ms = ms_total / steps
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total, value = whole_job(ms_total, T, steps, world, dev)
     res = {"precision": precision, "T": T, "n_out": n_out, "copies": copies, "steps": steps,
            "ms_total": ms_total, "ms_per_step": ms_total / steps, "launch_ms": launch_ms,
-           "value": world * T * steps / (ms_total / 1e3), "clocks": ck,
+           "value": value, "clocks": ck,
            "out_sample": outs[0], "fe": fe}
 
     if want_e2e:
