@@ -1,0 +1,32 @@
+/*
+ * melt_diag.h - diagnostics of libmelt, outside the feature path.
+ */
+#ifndef MELT_DIAG_H_
+#define MELT_DIAG_H_
+
+#include "melt.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * melt_diag_wait_timeout - exercises the failure path of the library's
+ *   bounded waits without faulting the GPU.  Every wait in the kernels (on an
+ *   mbarrier, for a copy, a peer or a pipeline stage) gives up after 1 s of
+ *   GPU time, latches MELT_ERR_TIMEOUT in the basis, lets its kernel finish
+ *   and leaves the context usable.  This call launches one thread that waits
+ *   on an mbarrier nothing arrives on, so that path runs: the next melt_sync
+ *   on the stream returns MELT_ERR_TIMEOUT (about 1 s later) and clears it.
+ *   basis   a basis of the current device (its error word receives the bit)
+ *   stream  cudaStream_t as void* (NULL = legacy default stream)
+ *   Errors: MELT_ERR_ARG for a NULL basis or one of another device,
+ *   MELT_ERR_CUDA if the launch fails.
+ */
+melt_status melt_diag_wait_timeout(melt_basis* basis, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MELT_DIAG_H_ */

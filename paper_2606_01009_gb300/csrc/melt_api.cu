@@ -14,8 +14,10 @@
 #include <new>
 #include <vector>
 
+#include "../../include/melt_diag.h"
 #include "melt_internal.h"
 #include "melt_tc.h"
+#include "sm100_ptx.cuh"
 
 using namespace melt;
 
@@ -556,6 +558,36 @@ melt_status melt_basis_set_correction(melt_basis* b, const melt_mlp* mlp) {
   }
   b->tc.pair_clusters = -1;  // the pair kernel's shared memory may have changed
   b->correction = mlp;
+  return MELT_OK;
+}
+
+namespace {
+
+// One thread waits on an mbarrier that nothing arrives on.  The wait is the
+// library's bounded one: after its limit it latches the timeout bit in the
+// basis's error word, raises the (local) abort flag and returns, and the
+// kernel ends; nothing faults and the context stays usable.
+__global__ void diag_wait_timeout_kernel(int* err) {
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    const uint32_t a = melt::ptx::smem_u32(&bar);
+    melt::ptx::mbar_init(a, 1);
+    melt::ptx::fence_mbar_init();
+    melt::ptx::mbar_wait(a, 0, &abort_flag, err, kErrTimeout);
+  }
+}
+
+}  // namespace
+
+melt_status melt_diag_wait_timeout(melt_basis* b, void* stream) {
+  if (!b) return MELT_ERR_ARG;
+  int dev = -1;
+  MELT_CUDA(cudaGetDevice(&dev));
+  if (dev != b->device) return MELT_ERR_ARG;
+  diag_wait_timeout_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(b->d_err);
+  MELT_CUDA(cudaGetLastError());
   return MELT_OK;
 }
 
