@@ -97,3 +97,18 @@ def test_padded_layout(lib):
     assert all(o % 4 == 0 for o in offs)
     lens, offs, total = lib.padded_layout([], 200)
     assert lens.size == 0 and total == 0
+
+
+def test_pad_and_diag_argument_checks_need_no_device(lib):
+    """melt_pad_reflect and melt_diag_wait_timeout reject bad arguments before any CUDA call."""
+    import numpy as np
+    L = lib.lib
+    lens = np.array([10, 3], dtype=np.int64)
+    lp = lens.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    buf = ctypes.c_void_p(16)  # never dereferenced: every case below fails its checks first
+    assert L.melt_pad_reflect(buf, None, lp, 0, 2, buf, None, None) == lib.MELT_OK        # empty batch
+    assert L.melt_pad_reflect(buf, None, None, 2, 2, buf, None, None) == lib.MELT_ERR_ARG  # no lengths
+    assert L.melt_pad_reflect(buf, None, lp, 2, -1, buf, None, None) == lib.MELT_ERR_ARG   # negative pad
+    assert L.melt_pad_reflect(buf, None, lp, 2, 3, buf, None, None) == lib.MELT_ERR_ARG    # clip of 3 <= pad
+    assert L.melt_pad_reflect(None, None, lp, 2, 2, buf, None, None) == lib.MELT_ERR_ARG   # no input
+    assert L.melt_diag_wait_timeout(None, None) == lib.MELT_ERR_ARG
