@@ -396,7 +396,7 @@ def energy_estimate(r):
     estimate, beside frames/s: the readings average over a window that takes
     in the idle edges of a short region."""
     w = (r.get("clocks") or {}).get("power_w_median")
-    if not w or not r.get("T"):
+    if not w or not r.get("T") or not r.get("launch_ms") or w <= 0 or r["launch_ms"] <= 0:
         return None
     j = w * (r["launch_ms"] / 1e3) / r["T"]
     return {"watts_median": w, "joules_per_frame": j, "frames_per_joule": 1.0 / j,

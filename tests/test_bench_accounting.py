@@ -79,3 +79,9 @@ def test_energy_estimate():
     assert e["joules_per_frame"] == pytest.approx(800.0 * 41e-6 / 191872)
     assert e["frames_per_joule"] == pytest.approx(191872 / (800.0 * 41e-6))
     assert bench.energy_estimate({"T": 5, "launch_ms": 1.0, "clocks": {"power_w_median": None}}) is None
+
+
+def test_energy_estimate_degenerate_inputs():
+    assert bench.energy_estimate({"T": 5, "launch_ms": 0.0, "clocks": {"power_w_median": 500.0}}) is None
+    assert bench.energy_estimate({"T": 0, "launch_ms": 1.0, "clocks": {"power_w_median": 500.0}}) is None
+    assert bench.energy_estimate({"T": 5, "launch_ms": 1.0}) is None
