@@ -112,3 +112,36 @@ def test_pad_and_diag_argument_checks_need_no_device(lib):
     assert L.melt_pad_reflect(buf, None, lp, 2, 3, buf, None, None) == lib.MELT_ERR_ARG    # clip of 3 <= pad
     assert L.melt_pad_reflect(None, None, lp, 2, 2, buf, None, None) == lib.MELT_ERR_ARG   # no input
     assert L.melt_diag_wait_timeout(None, None) == lib.MELT_ERR_ARG
+
+
+def test_plain_c_consumer(lib, tmp_path):
+    """A C99 program includes melt.h, links libmelt.so and calls host-only entry points."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "consumer.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "melt.h"
+#include "melt_diag.h"
+int main(void) {
+  melt_basis* b = 0;
+  if (strncmp(melt_version(), "melt", 4) != 0) return 1;
+  if (strcmp(melt_status_string(MELT_ERR_TIMEOUT), "kernel wait timed out") != 0) return 2;
+  if (melt_num_frames(0, 16000) != 0) return 3;
+  if (melt_basis_create(16000.0, 400, 160, 0, 0.0, 8000.0, MELT_WIN_HANN_PERIODIC, &b) != MELT_ERR_ARG) return 4;
+  if (melt_forward(0, 0, 0, 0, 1, 0, 0) != MELT_ERR_ARG) return 5;
+  if (melt_diag_wait_timeout(0, 0) != MELT_ERR_ARG) return 6;
+  printf("ok\n");
+  return 0;
+}
+''')
+    libdir = os.path.dirname(lib.LIB_PATH)
+    exe = tmp_path / "consumer"
+    subprocess.run([cc, "-std=c99", "-I", HEADER_DIR, str(src), "-o", str(exe), f"-L{libdir}", "-lmelt",
+                    f"-Wl,-rpath,{libdir}"], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stderr)
