@@ -247,6 +247,59 @@ def f32(a) -> np.ndarray:
     return np.asarray(a, dtype=np.float32).astype(np.float64)
 
 
+def fp8_row_exponents(amax) -> np.ndarray:
+    """Exponent e_u of each FP8 row scale 2^e_u: the least integer e with
+    amax_u * 2^-e <= 448 (the largest e4m3 value), so that the scaled row
+    fills (224, 448]; at least -127 (the smallest UE8M0 scale), and -127 for
+    an all-zero row.  amax_u is a float32 magnitude."""
+    a = np.asarray(amax, dtype=np.float64)
+    e = np.full(a.shape, -127, dtype=np.int64)
+    pos = a > 0
+    _, E = np.frexp(a[pos])                       # a = m 2^E, 0.5 <= m < 1
+    cand = E.astype(np.int64) - 9                 # a 2^-cand = m 2^9 in [256, 512)
+    cand += (np.ldexp(a[pos], -cand) > E4M3_MAX).astype(np.int64)
+    e[pos] = np.maximum(cand, -127)
+    return e
+
+
+def fp8_row_quantised(x, hop: int) -> np.ndarray:
+    """The sample values the FP8 form multiplies, for one clip.
+
+    The clip is cut into polyphase rows of H samples from its first sample
+    (row u = samples uH .. uH+H-1, the last one cut at the clip end); row u
+    gets the scale 2^e_u of ``fp8_row_exponents`` from max |x| over its
+    samples, its samples are rounded to e4m3 after division by 2^e_u, and
+    the result is multiplied back.  Returned as float64 (exact values)."""
+    x = np.asarray(x, dtype=np.float32).astype(np.float64)
+    L = x.shape[0]
+    U = -(-L // hop)
+    rows = np.zeros(U * hop)
+    rows[:L] = x
+    rows = rows.reshape(U, hop)
+    e = fp8_row_exponents(np.max(np.abs(rows), axis=1) if U else np.zeros(0))
+    q = np.ldexp(round_e4m3(np.ldexp(rows, -e[:, None])), e[:, None])
+    return q.reshape(-1)[:L]
+
+
+def fp8_frame_quantised(X) -> np.ndarray:
+    """Per-frame alternative of the FP8 operand rounding (the frame-level
+    amax scaling named with the precision sweep): each frame row of X gets
+    the power-of-two scale of ``fp8_row_exponents`` from max |x| over the
+    whole frame.  Kept to compare the two scalings; the FP8 form itself
+    scales polyphase rows (``fp8_row_quantised``)."""
+    X = np.asarray(X, dtype=np.float32).astype(np.float64)
+    e = fp8_row_exponents(np.max(np.abs(X), axis=1) if X.size else np.zeros(X.shape[0]))
+    return np.ldexp(round_e4m3(np.ldexp(X, -e[:, None])), e[:, None])
+
+
+FP8_BASIS_EXP = 8   # the e4m3 basis holds W * 2^8 (|W| <= 1, so at most 256 <= 448)
+
+
+def fp8_basis_quantised(W) -> np.ndarray:
+    """The basis values the FP8 form multiplies: e4m3(W 2^8) 2^-8 (exact)."""
+    return np.ldexp(round_e4m3(np.ldexp(np.asarray(W, np.float64), FP8_BASIS_EXP)), -FP8_BASIS_EXP)
+
+
 def melt_clip_rounded(x, spec: MelTSpec, precision: str, frames=None) -> np.ndarray:
     """MelT with the GEMM operands rounded as each reduced-precision form does.
 
@@ -256,36 +309,33 @@ def melt_clip_rounded(x, spec: MelTSpec, precision: str, frames=None) -> np.ndar
     * ``bf16``:   A = bf16(x), B = bf16(W).
     * ``bf16x3``: x = xh + xl, W = Wh + Wl (two-term bf16 splits), and the
       three products xh Wh + xh Wl + xl Wh (the xl Wl term is dropped).
-    * ``fp8``:    per-frame scale s_t = amax_n |x_t[n]| / 448 taken in float32
-      (inv_t = float32(448 / amax) for amax > 0, else inv_t = 1 and s_t = 1);
-      A = e4m3(float32(x * inv_t)); B = e4m3(W * 448); S = S_q (s_t/448)^2
-      with s_t = float32(amax / 448).
+    * ``fp8``:    every polyphase row of H samples (from the clip's first
+      sample) has its own power-of-two scale 2^e_u from its max |x|
+      (``fp8_row_quantised``); the basis is e4m3(W 2^8) 2^-8
+      (``fp8_basis_quantised``).  A frame's samples thus carry the scales of
+      the J rows they come from.
     * ``fp32``:   B = float32(W) (A is already float32).
     """
-    X = frame_signal(x, spec.n_fft, spec.hop, frames)
     W = np.concatenate([spec.Wr, spec.Wi], axis=0)
     M = spec.n_mels
-    if precision == "fp32":
-        Y = X @ f32(W).T
-    elif precision == "bf16":
-        Y = round_bf16(X) @ round_bf16(W).T
-    elif precision == "bf16x3":
-        xh, xl = split_bf16(X)
-        wh, wl = split_bf16(W)
-        Y = xh @ wh.T + xh @ wl.T + xl @ wh.T
-    elif precision == "fp8":
-        Xs = X.astype(np.float32)
-        amax = np.max(np.abs(Xs), axis=1) if Xs.size else np.zeros(0, np.float32)
-        pos = amax > 0
-        inv = np.ones_like(amax)
-        inv[pos] = (np.float32(E4M3_MAX) / amax[pos]).astype(np.float32)
-        st = np.ones_like(amax)
-        st[pos] = (amax[pos] / np.float32(E4M3_MAX)).astype(np.float32)
-        Aq = round_e4m3((Xs * inv[:, None]).astype(np.float32))
-        Bq = round_e4m3(W * E4M3_MAX)
-        Y = (Aq @ Bq.T) * (st.astype(np.float64) / E4M3_MAX)[:, None]
+    if precision == "fp8":
+        X = frame_signal(fp8_row_quantised(x, spec.hop), spec.n_fft, spec.hop, frames)
+        Y = X @ fp8_basis_quantised(W).T
+    elif precision == "fp8_frame":
+        X = fp8_frame_quantised(frame_signal(x, spec.n_fft, spec.hop, frames))
+        Y = X @ fp8_basis_quantised(W).T
     else:
-        raise ValueError(precision)
+        X = frame_signal(x, spec.n_fft, spec.hop, frames)
+        if precision == "fp32":
+            Y = X @ f32(W).T
+        elif precision == "bf16":
+            Y = round_bf16(X) @ round_bf16(W).T
+        elif precision == "bf16x3":
+            xh, xl = split_bf16(X)
+            wh, wl = split_bf16(W)
+            Y = xh @ wh.T + xh @ wl.T + xl @ wh.T
+        else:
+            raise ValueError(precision)
     S = dmp_energy(Y[:, :M], Y[:, M:])
     out = melt_log(S, spec.eps)
     return mfcct(out, spec.D) if spec.D is not None else out

@@ -77,3 +77,33 @@ def test_training_learns_per_band_affine_map():
             state[i] = (m, v)
     l1 = P.loss(P.forward(params, x, mu, sd)[0], tgt)
     assert l1 < 0.05 * l0
+
+
+def test_forward_bf16_hand_example():
+    """Which values the BF16 evaluation rounds, worked by hand.  mu = (0, 1),
+    sd = (1, 0.5); x = (1 + 2^-8, 2).  x-hat = (1 + 2^-8, 2) rounds to
+    (1, 2) (a tie goes to the even neighbour 1).  W1 = [[1.5 + 2^-8, 0],
+    [0, -0.75]] rounds to [[1.5, 0], [0, -0.75]] (tie, even), b1 = (0, 0.25):
+    h = (1.5, -1.25), not rounded.  GELU(1.5) = 1.5 Phi(1.5) = 1.39978920
+    rounds to 1.3984375 (179 steps of 2^-7), GELU(-1.25) = -1.25 Phi(-1.25)
+    = -0.13206222 rounds to -0.1318359375 (135 steps of 2^-10).  W2 =
+    [[2 + 2^-7, 0.5], [0, 1]] rounds to [[2, 0.5], [0, 1]] (tie, even); b2 =
+    (0, 0.5) and the residual x are not rounded."""
+    phi_15, phi_m125 = 0.9331927987311419, 0.10564977366685535   # standard normal table
+    assert P.gelu(1.5) == pytest.approx(1.5 * phi_15, rel=1e-14)
+    assert P.gelu(-1.25) == pytest.approx(-1.25 * phi_m125, rel=1e-13)
+    W1 = np.array([[1.5 + 2 ** -8, 0.0], [0.0, -0.75]])
+    b1 = np.array([0.0, 0.25])
+    W2 = np.array([[2.0 + 2 ** -7, 0.5], [0.0, 1.0]])
+    b2 = np.array([0.0, 0.5])
+    x = np.array([[1.0 + 2 ** -8, 2.0]])
+    y, (xh_b, h, a_b, W1_b, W2_b) = P.forward_bf16([W1, b1, W2, b2], x, np.array([0.0, 1.0]), np.array([1.0, 0.5]))
+    np.testing.assert_array_equal(xh_b, [[1.0, 2.0]])
+    np.testing.assert_array_equal(h, [[1.5, -1.25]])
+    np.testing.assert_array_equal(a_b, [[1.3984375, -0.1318359375]])
+    np.testing.assert_array_equal(W1_b, [[1.5, 0.0], [0.0, -0.75]])
+    np.testing.assert_array_equal(W2_b, [[2.0, 0.5], [0.0, 1.0]])
+    y0 = (1.0 + 2 ** -8) + 2.0 * 1.3984375 + 0.5 * -0.1318359375
+    y1 = 2.0 + 1.0 * -0.1318359375 + 0.5
+    np.testing.assert_array_equal(y, [[y0, y1]])
+    assert y0 == 3.73486328125 and y1 == 2.3681640625

@@ -363,3 +363,98 @@ def test_melt_vs_matched_stft_mel_on_synthetic_audio():
     print(f"MelT vs matched STFT-Mel, synthetic: cosine {np.mean(cos):.4f} CCC {np.mean(ccc):.4f} "
           f"RMSE {np.mean(rms):.2f} dB (paper, LibriSpeech: 0.9840 / 0.9541 / 6.03 dB)")
     assert np.mean(cos) > 0.85 and np.mean(ccc) > 0.7 and np.mean(rms) < 10.0
+
+
+# ------------------------------------------- conventional pipeline, whole
+@pytest.mark.parametrize("scale", ["htk", "slaney"])
+def test_stft_mel_matches_rfft_composition(scale):
+    """The whole conventional pipeline against the same steps built from
+    numpy.fft.rfft: window, |rfft|^2, the (separately pinned) triangular
+    filterbank, log(. + eps)."""
+    spec = O.MelTSpec(n_mels=40)
+    x = np.random.default_rng(21).standard_normal(400 + 7 * 160 + 33)
+    X = O.frame_signal(x, 400, 160) * O.hann(400, True)[None, :]
+    P = np.abs(np.fft.rfft(X, axis=1)) ** 2
+    F = O.triangular_filterbank(40, 400, 16000.0, 0.0, 8000.0, scale)
+    np.testing.assert_allclose(O.stft_mel_clip(x, spec, scale), np.log(P @ F.T + spec.eps),
+                               rtol=1e-12, atol=1e-11)
+
+
+@pytest.mark.parametrize("scale", ["htk", "slaney"])
+def test_stft_mel_bin_centred_tone_closed_form(scale):
+    """A cosine at FFT bin k0 through the periodic Hann window: |X[k0]|^2 =
+    (A N / 4)^2, |X[k0 +- 1]|^2 = (A N / 8)^2, every other bin 0.  So band m
+    holds exactly F[m, k0-1] (AN/8)^2 + F[m, k0] (AN/4)^2 + F[m, k0+1] (AN/8)^2.
+    A dropped window, magnitude instead of power, or a shifted bin grid fails."""
+    N, H, sr, A, k0 = 400, 160, 16000.0, 0.3, 50          # 2000 Hz
+    spec = O.MelTSpec(n_fft=N, hop=H, n_mels=40)
+    n = np.arange(N + 2 * H)
+    x = A * np.cos(2 * math.pi * k0 * n / N)
+    F = O.triangular_filterbank(40, N, sr, 0.0, 8000.0, scale)
+    band = (F[:, k0 - 1] + F[:, k0 + 1]) * (A * N / 8) ** 2 + F[:, k0] * (A * N / 4) ** 2
+    out = O.stft_mel_clip(x, spec, scale)
+    assert out.shape == (3, 40)
+    for t in range(3):   # the tone's phase moves with t; its power does not
+        np.testing.assert_allclose(out[t], np.log(band + spec.eps), atol=1e-8)
+    assert np.count_nonzero(band) >= 1
+
+
+# ----------------------------------------------------------- FP8 form
+def test_fp8_row_exponent_is_least_power_of_two():
+    """e_u is the least integer e with amax 2^-e <= 448 (brute force), clamped
+    at -127, on random float32 magnitudes and the edges of the rule."""
+    g = np.random.default_rng(31)
+    a = (g.uniform(0.5, 2.0, 4000) * 2.0 ** g.integers(-140, 120, 4000)).astype(np.float32)
+    edge = np.array([1.75, np.nextafter(np.float32(1.75), np.float32(2)), 1.0, 448.0, 449.0, 3.5,
+                     2.0 ** -126, 2.0 ** -130, 1e-45, 3.0e38], np.float32)
+    a = np.concatenate([a, edge]).astype(np.float64)
+    e = O.fp8_row_exponents(a)
+    for v, ev in zip(a, e):
+        best = next(k for k in range(-200, 200) if math.ldexp(v, -k) <= 448.0)
+        assert ev == max(best, -127), (v, ev, best)
+    assert O.fp8_row_exponents(np.array([0.0]))[0] == -127
+    assert O.fp8_row_exponents(np.array([1.75]))[0] == -8          # 1.75 * 2^8 = 448
+    assert O.fp8_row_exponents(np.array([1.7500001]))[0] == -7
+
+
+def test_fp8_rows_match_torch_e4m3_cast():
+    """Per-row scaling, then torch's float8_e4m3fn cast of float32(x 2^-e_u),
+    then 2^e_u back, equals the oracle's quantised samples."""
+    g = np.random.default_rng(32)
+    H = 160
+    x = (g.standard_normal(37 * H + 55) * 10.0 ** g.uniform(-4, 1)).astype(np.float32)
+    x[5 * H:6 * H] = 0.0                                  # an all-zero row
+    x[9 * H:10 * H] *= np.float32(1e-30)                   # a row of float32 subnormal / tiny values
+    q = O.fp8_row_quantised(x, H)
+    rows = np.zeros(38 * H, np.float64)
+    rows[:x.size] = x
+    rows = rows.reshape(38, H)
+    e = O.fp8_row_exponents(np.max(np.abs(rows), axis=1))
+    scaled = torch.from_numpy(np.ldexp(rows, -e[:, None]).astype(np.float32))
+    ref = np.ldexp(scaled.to(torch.float8_e4m3fn).to(torch.float64).numpy(), e[:, None]).reshape(-1)[:x.size]
+    np.testing.assert_array_equal(q, ref)
+
+
+def test_fp8_form_hand_example():
+    """Two rows of H = 4 samples worked by hand.  Row [1, 2, 3, 4]: amax 4,
+    e = -6 (4 * 64 = 256 <= 448, 512 is not), every value exact in e4m3.
+    Row [0.1, 0.2, 0.3, 0.45]: amax 0.45, e = -9 (0.45 * 512 = 230.4; 460.8
+    is too large); scaled 51.2, 102.4, 153.6, 230.4 round to 52, 104, 160,
+    224 (e4m3 steps 4, 8, 16, 16), i.e. 0.1015625, 0.203125, 0.3125, 0.4375."""
+    x = np.array([1, 2, 3, 4, 0.1, 0.2, 0.3, 0.45], np.float32)
+    q = O.fp8_row_quantised(x, 4)
+    np.testing.assert_array_equal(q, [1, 2, 3, 4, 0.1015625, 0.203125, 0.3125, 0.4375])
+    # the basis: W 2^8 in e4m3, then 2^-8: 0.3 -> 76.8 -> 80 (step 8 in [64, 128)) -> 0.3125
+    np.testing.assert_array_equal(O.fp8_basis_quantised(np.array([0.3, -1.0, 0.0])), [0.3125, -1.0, 0.0])
+
+
+def test_fp8_row_and_frame_scaling_agree_in_the_normal_range():
+    """With power-of-two scales, e4m3 rounding commutes with the scale for
+    values in e4m3's normal range, so the per-row form equals the per-frame
+    form wherever no sample is subnormal under either scale (a signal with
+    no sample near zero relative to its frame's amax)."""
+    spec = O.MelTSpec()
+    n = np.arange(400 + 5 * 160)
+    x = (0.6 + 0.3 * np.sin(2 * math.pi * 440 * n / 16000.0)).astype(np.float32)   # all in [0.3, 0.9]
+    np.testing.assert_allclose(O.melt_clip_rounded(x, spec, "fp8"), O.melt_clip_rounded(x, spec, "fp8_frame"),
+                               rtol=0, atol=1e-12)
