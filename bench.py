@@ -84,14 +84,18 @@ def measured_traffic(key: str):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="melt", choices=["melt", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "bf16x3", "fp8"])
     ap.add_argument("--workload", default="rich_64x30s", choices=sorted(WORKLOADS))
     ap.add_argument("--n-mels", type=int, default=None)
     ap.add_argument("--mfcc", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--trials", type=int, default=20,
+                    help="at least this many timed trials of --steps launches (median reported)")
+    ap.add_argument("--trial-seconds", type=float, default=1.0,
+                    help="add trials until the timed region holds about this much GPU time")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grouped", action=argparse.BooleanOptionalAction, default=True,
@@ -250,6 +254,29 @@ class Workload:
         return self.waves[:copies], outs, copies
 
 
+def trial_count(args, one_step, stream, dev, steps):
+    """Trials of `steps` launches to time: at least args.trials, and enough
+    for about args.trial_seconds of load so that the clock sampler (10 Hz)
+    sees the region; at most 5000."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(3):
+        one_step()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    est_ms = max(a.elapsed_time(b) / 3, 1e-3) * steps
+    return int(min(5000, max(args.trials, math.ceil(args.trial_seconds * 1e3 / est_ms))))
+
+
+def trial_stats(trial_ms, steps):
+    """Median, spread and count of the per-launch times of the trials (ms)."""
+    per = sorted(t / steps for t in trial_ms)
+    q = lambda f: per[min(len(per) - 1, int(f * (len(per) - 1) + 0.5))]
+    return {"count": len(per), "launches_per_trial": steps, "median_ms": statistics.median(per),
+            "min_ms": per[0], "p10_ms": q(0.1), "p90_ms": q(0.9), "max_ms": per[-1]}
+
+
 def whole_job(ms_total, frames_per_step, steps, world, dev):
     """(slowest rank's timed region in ms, whole-job frames/s).  Every rank
     times its own replica of the workload (weak scaling); the job takes as long
@@ -293,32 +320,37 @@ def time_form(args, W, precision, steps, warmup, world, want_e2e):
     for i in range(warmup):
         step(i)
     fe.sync(stream)
+    trials = trial_count(args, lambda: step(0), stream, dev, steps)
     clocks = ClockSampler(dev.index)
     clocks.start()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    # Only the forward kernels run between e0 and e1: an event recorded
-    # between two launches would cut the programmatic (early-launch) edge
-    # between them, so one kernel's average duration is the region / steps.
-    e0.record(stream)
-    for i in range(steps):
-        step(i)
-    e1.record(stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(trials + 1)]
+    # Trials of `steps` launches run back to back; only the forward kernels
+    # run between two events.  An event between two launches cuts the
+    # programmatic (early-launch) edge between them, so it is recorded only at
+    # trial boundaries, and one launch's average duration is a trial / steps.
+    ev[0].record(stream)
+    i = 0
+    for t in range(trials):
+        for _ in range(steps):
+            step(i)
+            i += 1
+        ev[t + 1].record(stream)
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     ck = clocks.stop()
     fe.sync(stream)
-    ms_total = e0.elapsed_time(e1)
+    trial_ms = [ev[t].elapsed_time(ev[t + 1]) for t in range(trials)]
+    ms_total = statistics.median(trial_ms)
     launch_ms = ms_total / steps
     ms_total, value = whole_job(ms_total, T, steps, world, dev)
     res = {"precision": precision, "T": T, "n_out": n_out, "copies": copies, "steps": steps,
            "ms_total": ms_total, "ms_per_step": ms_total / steps, "launch_ms": launch_ms,
-           "value": value, "clocks": ck,
+           "value": value, "clocks": ck, "trials": trial_stats(trial_ms, steps),
            "out_sample": outs[0], "fe": fe}
 
     if want_e2e:
@@ -443,6 +475,7 @@ def run_melt(args, rank, world):
         "gpu_launches": args.steps,
         "roofline": roofline(cfg, W, head, peaks, peak_kind),
         "clocks": {k: head["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples")},
+        "trials": head["trials"],
         "energy": energy_estimate(head),
     }
     if args.forms:
@@ -453,6 +486,7 @@ def run_melt(args, rank, world):
                 continue
             rf = roofline(cfg, W, r, peaks, peak_kind)
             res["forms"][name] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "steps": r["steps"],
+                                  "trials": r["trials"],
                                   "roofline_frac": rf["frac"], "bound": rf["bound"],
                                   "achieved": rf["achieved"], "unit": rf["unit"],
                                   "clocks_sm_mhz": r["clocks"]["sm_mhz"],

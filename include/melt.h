@@ -213,13 +213,20 @@ melt_status melt_forward(melt_basis* basis, const float* wave, const int64_t* of
  *     library until the process exits.  A batch that needs more tiles is
  *     rejected with MELT_ERR_ARG before anything is launched.
  *   The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.  The basis must belong to the current device.
+ *     (cudaGetSymbolAddress) with that device current.  The basis must
+ *     belong to the current device.
  *   All calls share the array, which keeps the previous call's descriptors;
  *     each call rewrites every entry it uses, so nothing needs clearing.
  *     Calls whose work overlaps on the GPU (different streams without
  *     ordering) race on the array: order them on one stream, or wait.
- *   Host-side planning uses a file-scope host array guarded by a mutex.
+ *   Host-side planning uses a file-scope host array guarded by a mutex; the
+ *     plan reaches the device array by a copy from that pageable host array,
+ *     which the driver stages before the call returns.  The call may
+ *     therefore block until the work already queued on `stream` has
+ *     finished, and it holds the mutex meanwhile, so concurrent calls from
+ *     other threads wait too.  A pageable copy cannot be replayed by a CUDA
+ *     graph: while `stream` is being captured the call returns
+ *     MELT_ERR_UNSUPPORTED and enqueues nothing.
  */
 melt_status melt_forward_noalloc(melt_basis* basis, const float* wave, const int64_t* offsets,
                                  const int64_t* lengths, int batch, float* out, void* stream);

@@ -25,6 +25,15 @@ extern "C" {
  */
 melt_status melt_diag_wait_timeout(melt_basis* basis, void* stream);
 
+/*
+ * melt_diag_alloc_count - number of device allocations (cudaMalloc) and
+ *   page-locked host allocations (cudaMallocHost) the library has made in
+ *   this process so far, over all devices and threads.  The paper has no
+ *   counterpart: it lets a test show that an entry point allocated nothing
+ *   (the count is the same before and after the call).  Never fails.
+ */
+long long melt_diag_alloc_count(void);
+
 #ifdef __cplusplus
 }
 #endif

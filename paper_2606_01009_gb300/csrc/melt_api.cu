@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -120,7 +121,7 @@ melt_status upload_fp32(melt_basis* b) {
       h[(size_t)n * 2 * b->mp + 2 * m] = (float)b->w64[(size_t)m * N + n];
       h[(size_t)n * 2 * b->mp + 2 * m + 1] = (float)b->w64[(size_t)(M + m) * N + n];
     }
-  MELT_CUDA(cudaMalloc(&b->d_w32, h.size() * sizeof(float)));
+  MELT_CUDA(melt::dev_alloc(&b->d_w32, h.size() * sizeof(float)));
   MELT_CUDA(cudaMemcpy(b->d_w32, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
   return MELT_OK;
 }
@@ -135,7 +136,7 @@ melt_status upload_dct(melt_basis* b) {
       if (k == 0) v *= std::sqrt(0.5);
       d[(size_t)k * M + m] = (float)v;
     }
-  MELT_CUDA(cudaMalloc(&b->d_dct, d.size() * sizeof(float)));
+  MELT_CUDA(melt::dev_alloc(&b->d_dct, d.size() * sizeof(float)));
   MELT_CUDA(cudaMemcpy(b->d_dct, d.data(), d.size() * sizeof(float), cudaMemcpyHostToDevice));
   return MELT_OK;
 }
@@ -183,7 +184,7 @@ melt_status create_common(double sr, int n_fft, int hop, const double* freqs, in
     st = tc_build(&b->tc, c, b->w64.data());
   }
   if (st == MELT_OK) {
-    cudaError_t e = cudaMalloc(&b->d_err, sizeof(int));
+    cudaError_t e = melt::dev_alloc(&b->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
     st = cuda_status(e);
   }
@@ -256,8 +257,8 @@ melt_status stage_plan(melt_basis* b, const int64_t* offsets, const int64_t* len
     cudaFree(s.dev);
     s.host = nullptr; s.dev = nullptr; s.cap = 0;
     const size_t cap = std::max<size_t>(n, 1024);
-    MELT_CUDA(cudaMallocHost(&s.host, cap * sizeof(TileDesc)));
-    MELT_CUDA(cudaMalloc(&s.dev, cap * sizeof(TileDesc)));
+    MELT_CUDA(melt::host_alloc_pinned(&s.host, cap * sizeof(TileDesc)));
+    MELT_CUDA(melt::dev_alloc(&s.dev, cap * sizeof(TileDesc)));
     s.cap = cap;
   }
   std::memcpy(s.host, b->plan.data(), b->plan.size() * sizeof(TileDesc));
@@ -321,6 +322,18 @@ melt_status forward_impl(melt_basis* b, const float* wave, const int64_t* offset
 }  // namespace
 
 namespace melt {
+
+static std::atomic<long long> g_alloc_calls{0};  // allocations made by the library
+
+cudaError_t dev_alloc_bytes(void** p, size_t bytes) {
+  g_alloc_calls.fetch_add(1, std::memory_order_relaxed);
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_alloc_pinned_bytes(void** p, size_t bytes) {
+  g_alloc_calls.fetch_add(1, std::memory_order_relaxed);
+  return cudaMallocHost(p, bytes);
+}
 
 int64_t basis_frames(const melt_basis* b, int64_t len) { return frames_of(b, len); }
 
@@ -549,7 +562,7 @@ melt_status melt_basis_set_correction(melt_basis* b, const melt_mlp* mlp) {
       cudaFree(b->tc.d_mlp_img);
       b->tc.d_mlp_img = nullptr;
       b->tc.mlp_hd = 0;
-      MELT_CUDA(cudaMalloc(&b->tc.d_mlp_img, 2 * half));
+      MELT_CUDA(melt::dev_alloc(&b->tc.d_mlp_img, 2 * half));
       b->tc.mlp_half = half;
     }
     b->tc.mlp_hd = mlp_hidden(mlp);
@@ -590,6 +603,8 @@ melt_status melt_diag_wait_timeout(melt_basis* b, void* stream) {
   MELT_CUDA(cudaGetLastError());
   return MELT_OK;
 }
+
+long long melt_diag_alloc_count(void) { return melt::g_alloc_calls.load(std::memory_order_relaxed); }
 
 melt_status melt_sync(melt_basis* b, void* stream) {
   if (!b) return MELT_ERR_ARG;

@@ -138,7 +138,7 @@ melt_status make_entry(melt_group* g, const float* wave, const int64_t* offsets,
   melt_status st = MELT_OK;
   if (cudaEventCreateWithFlags(&e->done, cudaEventDisableTiming) != cudaSuccess) st = MELT_ERR_CUDA;
   const size_t bytes = std::max<size_t>(g->host.size(), 1) * sizeof(TileDesc);
-  if (st == MELT_OK && cudaMalloc(&e->d_tiles, bytes) != cudaSuccess) st = MELT_ERR_OOM;
+  if (st == MELT_OK && melt::dev_alloc(&e->d_tiles, bytes) != cudaSuccess) st = MELT_ERR_OOM;
   // pageable source: the call returns once the bytes are staged, so g->host may be reused
   if (st == MELT_OK && !g->host.empty() &&
       cudaMemcpyAsync(e->d_tiles, g->host.data(), g->host.size() * sizeof(TileDesc),

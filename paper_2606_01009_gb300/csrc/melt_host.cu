@@ -147,7 +147,7 @@ melt_status plan_host(melt_basis* b, HostPipe* hp, const int64_t* offsets, const
       hp->d_wave[i] = nullptr;
     }
     hp->wave_cap = 0;
-    for (int i = 0; i < kHostSlots; ++i) HCUDA(cudaMalloc(&hp->d_wave[i], wave_max * sizeof(float)));
+    for (int i = 0; i < kHostSlots; ++i) HCUDA(melt::dev_alloc(&hp->d_wave[i], wave_max * sizeof(float)));
     hp->wave_cap = wave_max;
   }
   if (out_max > hp->out_cap) {
@@ -156,7 +156,7 @@ melt_status plan_host(melt_basis* b, HostPipe* hp, const int64_t* offsets, const
       hp->d_out[i] = nullptr;
     }
     hp->out_cap = 0;
-    for (int i = 0; i < kHostSlots; ++i) HCUDA(cudaMalloc(&hp->d_out[i], out_max * sizeof(float)));
+    for (int i = 0; i < kHostSlots; ++i) HCUDA(melt::dev_alloc(&hp->d_out[i], out_max * sizeof(float)));
     hp->out_cap = out_max;
   }
   const size_t nt = std::max<size_t>(hp->h_tiles.size(), 1);
@@ -164,7 +164,7 @@ melt_status plan_host(melt_basis* b, HostPipe* hp, const int64_t* offsets, const
     cudaFree(hp->d_tiles);
     hp->d_tiles = nullptr;
     hp->tiles_cap = 0;
-    HCUDA(cudaMalloc(&hp->d_tiles, nt * sizeof(TileDesc)));
+    HCUDA(melt::dev_alloc(&hp->d_tiles, nt * sizeof(TileDesc)));
     hp->tiles_cap = nt;
   }
   HCUDA(cudaMemcpy(hp->d_tiles, hp->h_tiles.data(), hp->h_tiles.size() * sizeof(TileDesc),

@@ -42,6 +42,20 @@ struct SimtParams {
   int mode;           // 0: log-Mel / MFCC, 1: raw R|I components
 };
 
+// Every device allocation and every page-locked host allocation the library
+// makes goes through these two calls, which count them (the count is read by
+// melt_diag_alloc_count, so a test can show that a call allocated nothing).
+cudaError_t dev_alloc_bytes(void** p, size_t bytes);
+cudaError_t host_alloc_pinned_bytes(void** p, size_t bytes);
+template <class T>
+inline cudaError_t dev_alloc(T** p, size_t bytes) {
+  return dev_alloc_bytes(reinterpret_cast<void**>(p), bytes);
+}
+template <class T>
+inline cudaError_t host_alloc_pinned(T** p, size_t bytes) {
+  return host_alloc_pinned_bytes(reinterpret_cast<void**>(p), bytes);
+}
+
 // Launch the FP32 SIMT kernel for `p` (grid picked by the caller).
 cudaError_t launch_simt(const SimtParams& p, int mj, int grid, cudaStream_t stream);
 int simt_smem_bytes(int mj, int n_mels, int n_mfcc);

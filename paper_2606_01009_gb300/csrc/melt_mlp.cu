@@ -365,8 +365,8 @@ melt_status ensure_ws(melt_mlp* p, int batch) {
   if (batch <= p->cap) return MELT_OK;
   free_ws(p);
   const size_t h = (size_t)batch * p->Hd * sizeof(float), o = (size_t)batch * p->M * sizeof(float);
-  if (cudaMalloc(&p->d_H, h) != cudaSuccess || cudaMalloc(&p->d_A, h) != cudaSuccess ||
-      cudaMalloc(&p->d_dY, o) != cudaSuccess || cudaMalloc(&p->d_dH, h) != cudaSuccess) {
+  if (melt::dev_alloc(&p->d_H, h) != cudaSuccess || melt::dev_alloc(&p->d_A, h) != cudaSuccess ||
+      melt::dev_alloc(&p->d_dY, o) != cudaSuccess || melt::dev_alloc(&p->d_dH, h) != cudaSuccess) {
     free_ws(p);
     return MELT_ERR_OOM;
   }
@@ -550,10 +550,10 @@ melt_status melt_mlp_create(int n_in, int n_hidden, const float* params, const f
   p->Hd = n_hidden;
   p->n_params = param_count(n_in, n_hidden);
   const size_t pb = (size_t)p->n_params * sizeof(float);
-  bool ok = cudaMalloc(&p->d_params, pb) == cudaSuccess && cudaMalloc(&p->d_grads, pb) == cudaSuccess &&
-            cudaMalloc(&p->d_m, pb) == cudaSuccess && cudaMalloc(&p->d_v, pb) == cudaSuccess &&
-            cudaMalloc(&p->d_mu, n_in * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&p->d_sd, n_in * sizeof(float)) == cudaSuccess;
+  bool ok = melt::dev_alloc(&p->d_params, pb) == cudaSuccess && melt::dev_alloc(&p->d_grads, pb) == cudaSuccess &&
+            melt::dev_alloc(&p->d_m, pb) == cudaSuccess && melt::dev_alloc(&p->d_v, pb) == cudaSuccess &&
+            melt::dev_alloc(&p->d_mu, n_in * sizeof(float)) == cudaSuccess &&
+            melt::dev_alloc(&p->d_sd, n_in * sizeof(float)) == cudaSuccess;
   if (ok) {
     std::vector<float> m0(n_in, 0.f), s0(n_in, 1.f);
     ok = cudaMemcpy(p->d_params, params, pb, cudaMemcpyHostToDevice) == cudaSuccess &&

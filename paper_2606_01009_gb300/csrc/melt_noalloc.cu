@@ -15,8 +15,11 @@
 // library holds until the process exits.  Its device address is looked up
 // once per device with cudaGetSymbolAddress; host code never passes the
 // symbol itself to a kernel.  The tiles are planned into a file-scope host
-// array and copied with cudaMemcpyAsync from that pageable buffer (the call
-// returns once the driver has staged the bytes).
+// array and copied with cudaMemcpyAsync from that pageable buffer: the driver
+// stages the bytes before the call returns, so the host array is free for the
+// next call at once, but the copy may first wait for the work already queued
+// on the stream.  A pageable copy cannot be replayed from a CUDA graph, so
+// the call refuses to run while its stream is being captured.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -47,6 +50,11 @@ extern "C" melt_status melt_forward_noalloc(melt_basis* basis, const float* wave
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MELT_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices || dev != basis_device(basis)) return MELT_ERR_ARG;
+  cudaStream_t stream = (cudaStream_t)stream_v;
+  // the plan is copied from pageable memory, which a captured graph cannot replay
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return MELT_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return MELT_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_dev_tiles[dev]) {
     // set-up, once per device, with that device current
@@ -60,7 +68,6 @@ extern "C" melt_status melt_forward_noalloc(melt_basis* basis, const float* wave
   if (n == 0) return MELT_OK;
   const TileDesc& last = g_host_tiles[n - 1];  // planned in output-row order
   const int64_t rows = last.out_row + last.n_frames;
-  cudaStream_t stream = (cudaStream_t)stream_v;
   // Every field of the n descriptors is written here; nothing in the array
   // has to start at zero.
   if (cudaMemcpyAsync(g_dev_tiles[dev], g_host_tiles, (size_t)n * sizeof(TileDesc),

@@ -357,7 +357,7 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
     std::memset(&probe, 0, sizeof(probe));
     if (!plan_smem(tb, probe, c.n_mfcc)) return MELT_ERR_UNSUPPORTED;  // operands do not fit shared memory
   }
-  if (cudaMalloc(&tb->d_b, img.size()) != cudaSuccess) return MELT_ERR_OOM;
+  if (melt::dev_alloc(&tb->d_b, img.size()) != cudaSuccess) return MELT_ERR_OOM;
   if (cudaMemcpy(tb->d_b, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return MELT_ERR_CUDA;
   if (P == MELT_BF16 || P == MELT_FP8E4M3) {
@@ -372,12 +372,12 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
             std::memcpy(img2.data() + ((size_t)h * KS + s) * half_step + (size_t)cc * MP * 16 + (size_t)r * 16,
                         img.data() + (size_t)s * kstep_bytes + (size_t)cc * NC * 16 + (size_t)(h * MP + r) * 16,
                         16);
-    if (cudaMalloc(&tb->d_b2, img2.size()) != cudaSuccess) return MELT_ERR_OOM;
+    if (melt::dev_alloc(&tb->d_b2, img2.size()) != cudaSuccess) return MELT_ERR_OOM;
     if (cudaMemcpy(tb->d_b2, img2.data(), img2.size(), cudaMemcpyHostToDevice) != cudaSuccess)
       return MELT_ERR_CUDA;
     // counters of the dynamic pair schedule (each launch leaves its pair at zero)
     const size_t sb = sizeof(unsigned long long) * 2 * kSchedWords;
-    if (cudaMalloc(&tb->d_sched, sb) != cudaSuccess) return MELT_ERR_OOM;
+    if (melt::dev_alloc(&tb->d_sched, sb) != cudaSuccess) return MELT_ERR_OOM;
     if (cudaMemset(tb->d_sched, 0, sb) != cudaSuccess) return MELT_ERR_CUDA;
   }
   return MELT_OK;

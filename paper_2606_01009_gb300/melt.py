@@ -56,6 +56,7 @@ SIGNATURES = {
     "melt_forward_host": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
     "melt_pad_reflect": (C.c_int, [_VP, _I64P, _I64P, C.c_int, C.c_int, _VP, _I64P, _VP]),
     "melt_diag_wait_timeout": (C.c_int, [_VP, _VP]),
+    "melt_diag_alloc_count": (C.c_longlong, []),
     "melt_plan_get": (C.c_int, [_VP, _VP]),
     "melt_plan_set": (C.c_int, [_VP, _VP]),
     "melt_autotune": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP, C.c_int, _VP]),
@@ -228,6 +229,11 @@ def melt_pad_reflect(wave, offsets, lengths, pad, out, out_offsets=None, stream=
 def melt_diag_wait_timeout(basis, stream=None):
     """Run the failure path of the bounded waits: the next melt_sync reports MELT_ERR_TIMEOUT."""
     _check(lib.melt_diag_wait_timeout(basis, _stream_ptr(stream)), "melt_diag_wait_timeout")
+
+
+def melt_diag_alloc_count() -> int:
+    """Device and page-locked host allocations libmelt has made in this process."""
+    return int(lib.melt_diag_alloc_count())
 
 
 def padded_layout(lengths, pad):

@@ -12,6 +12,32 @@ LOGF_ABS = 2.0 ** -21  # __logf: absolute error <= 2^-21.41 on [0.5, 2]
 LOGF_REL = 4 * 2.0 ** -23  # ... and <= 3 ulp of the result elsewhere
 
 
+# Stated dB tolerance of each operand form against the FP64 oracle, for bins
+# within 10 / 30 / 60 / 100 dB of their frame's largest bin and for all bins:
+# (max, RMS) of |form - FP64| in dB.  The reduced forms' figures are the
+# rounded-operand oracle's own error over the whole 1024 x 10 s precision
+# sweep (1,021,952 frames, levels -60..0 dBFS), rounded up by 10-30 %: their
+# kernels differ from that oracle only by FP32 accumulation, which the
+# element-wise parity tests bound separately.  FP32 is held to 1e-3 dB within
+# 60 dB; deeper bins carry the FP32 rounding of the basis itself (up to
+# 4.1e-3 dB at 100 dB over the sweep with exact sums).
+FORM_TOL_DB = {
+    "bf16": {"within_10dB": {"max": 0.5, "rms": 0.006}, "within_30dB": {"max": 6.0, "rms": 0.035},
+             "within_60dB": {"max": 30.0, "rms": 0.32}, "within_100dB": {"max": 50.0, "rms": 0.6},
+             "all": {"max": 50.0, "rms": 0.6}},
+    "bf16x3": {"within_10dB": {"max": 1e-3, "rms": 1.5e-5}, "within_30dB": {"max": 0.01, "rms": 1e-4},
+               "within_60dB": {"max": 0.08, "rms": 8e-4}, "within_100dB": {"max": 0.8, "rms": 2e-3},
+               "all": {"max": 2.5, "rms": 2e-3}},
+    "fp8": {"within_10dB": {"max": 9.0, "rms": 0.09}, "within_30dB": {"max": 55.0, "rms": 0.5},
+            "within_60dB": {"max": 70.0, "rms": 3.0}, "within_100dB": {"max": 70.0, "rms": 3.9},
+            "all": {"max": 80.0, "rms": 3.9}},
+    "fp32": {"within_10dB": {"max": 1e-4, "rms": 1e-6}, "within_30dB": {"max": 2e-4, "rms": 2e-6},
+             "within_60dB": {"max": 1e-3, "rms": 1e-5}, "within_100dB": {"max": 8e-3, "rms": 2e-5},
+             "all": {"max": 2.5e-2, "rms": 2e-5}},
+}
+TOL_DEPTHS = (10.0, 30.0, 60.0, 100.0)
+
+
 def gpu_features(fe, clips, offsets=None, stream=None):
     """Run a Frontend on host clips (packed at 4-float alignment) -> float64 [sum T, n_out]."""
     import torch
@@ -69,7 +95,23 @@ def fp32_sum_error(n_terms: int) -> float:
     return g / (1 - g)
 
 
-def db_report(got, ref, depths=(60.0, 100.0)):
+def mma_terms(precision: str, n_fft: int, hop: int) -> int:
+    """Products per accumulated sum of a tensor-core form: each polyphase slice
+    j (min(H, N - jH) samples) is padded to the MMA's K step (16 for BF16, 32
+    for FP8); BF16x3 issues three products per term."""
+    step = 32 if precision == "fp8" else 16
+    J = -(-n_fft // hop)
+    k = sum(-(-min(hop, n_fft - j * hop) // step) * step for j in range(J))
+    return 3 * k if precision == "bf16x3" else k
+
+
+def acc_rel(precision: str, n_fft: int = 400, hop: int = 160) -> float:
+    """Accumulation allowance per sum of a tensor-core form, relative to the
+    sum of |products|: four times the worst-case FP32 summation error."""
+    return 4 * fp32_sum_error(mma_terms(precision, n_fft, hop))
+
+
+def db_report(got, ref, depths=TOL_DEPTHS):
     out = {}
     mx, rms = O.err_db(got, ref)
     out["all"] = (mx, rms)
@@ -77,6 +119,16 @@ def db_report(got, ref, depths=(60.0, 100.0)):
         m = O.within_db_of_frame_max(ref, d)
         out[f"within_{int(d)}dB"] = O.err_db(got, ref, m)
     return out
+
+
+def check_form_tolerance(prec, rep):
+    """Every mask of a db_report within the form's stated tolerance; returns the violations."""
+    bad = []
+    for key, (mx, rms) in rep.items():
+        tol = FORM_TOL_DB[prec].get(key)
+        if tol and (mx > tol["max"] or rms > tol["rms"]):
+            bad.append((key, mx, rms, tol))
+    return bad
 
 
 def rounded_components(spec, clips, precision):
@@ -98,18 +150,10 @@ def rounded_components(spec, clips, precision):
             Y = xh @ wh.T + xh @ wl.T + xl @ wh.T
             E = np.abs(xh) @ np.abs(wh).T + np.abs(xh) @ np.abs(wl).T + np.abs(xl) @ np.abs(wh).T
         elif precision == "fp8":
-            Xs = X.astype(np.float32)
-            amax = np.max(np.abs(Xs), axis=1) if Xs.size else np.zeros(0, np.float32)
-            pos = amax > 0
-            inv = np.ones_like(amax)
-            inv[pos] = (np.float32(448.0) / amax[pos]).astype(np.float32)
-            st = np.ones_like(amax)
-            st[pos] = (amax[pos] / np.float32(448.0)).astype(np.float32)
-            Aq = O.round_e4m3((Xs * inv[:, None]).astype(np.float32))
-            Bq = O.round_e4m3(W * 448.0)
-            sc = (st.astype(np.float64) / 448.0)[:, None]
-            Y = (Aq @ Bq.T) * sc
-            E = (np.abs(Aq) @ np.abs(Bq).T) * sc
+            Xq = O.frame_signal(O.fp8_row_quantised(c, spec.hop), spec.n_fft, spec.hop)
+            Bq = O.fp8_basis_quantised(W)
+            Y = Xq @ Bq.T
+            E = np.abs(Xq) @ np.abs(Bq).T
         else:
             raise ValueError(precision)
         Rs.append(Y[:, :M]); Is.append(Y[:, M:])

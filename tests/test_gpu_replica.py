@@ -17,7 +17,7 @@ import pytest
 
 from oracle import melt_oracle as O
 from paper_2606_01009_gb300 import inputs as G
-from tests.helpers import (db_report, fp32_sum_error, gpu_features, log_error_bound, oracle_features,
+from tests.helpers import (acc_rel, db_report, fp32_sum_error, gpu_features, log_error_bound, oracle_features,
                            rounded_log_bound)
 
 pytestmark = pytest.mark.gpu
@@ -50,17 +50,10 @@ def _frontend(melt, prec, cfg, n_mfcc=0):
         pytest.skip(f"{prec} does not fit shared memory for {cfg} (MELT_ERR_UNSUPPORTED)")
 
 
-def _terms(prec, n_fft):
-    # products per accumulated sum: K padded to the MMA's K step (16; FP8 32),
-    # three products per sample for the split-BF16 form
-    step = 32 if prec == "fp8" else 16
-    return -(-n_fft // step) * step * (3 if prec == "bf16x3" else 1)
-
-
 def _log_mel_bound(spec, clips, prec):
     if prec == "fp32":
         return log_error_bound(spec, clips, fp32_sum_error(spec.n_fft)), oracle_features(spec, clips)
-    rel = 4 * fp32_sum_error(_terms(prec, spec.n_fft))
+    rel = acc_rel(prec, spec.n_fft, spec.hop)
     return rounded_log_bound(spec, clips, prec, rel), oracle_features(spec, clips, rounded=prec)
 
 
