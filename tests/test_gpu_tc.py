@@ -111,25 +111,31 @@ def test_silent_and_tiny_inputs(melt):
         _check(melt, prec, clips)
 
 
+@pytest.fixture(scope="module")
+def levels():
+    """The 1024 x 10 s sweep workload and the FP64 oracle on its checked clips."""
+    clips, sr = G.workload("levels_1024x10s")
+    idx = list(range(0, 1024, 32))
+    sub = [clips[b] for b in idx]
+    return clips, sr, idx, sub, oracle_features(_spec(), sub)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("prec", ["fp32"] + FORMS)
-def test_precision_sweep_1024x10s(melt, prec):
+def test_precision_sweep_1024x10s(melt, levels, prec):
     """The precision sweep: all 1024 clips of 10 s (levels -60..0 dBFS) in
     one launch per form.  Every 32nd clip (32 clips, 31,936 frames) is
     checked element by element (reduced forms: against the rounded-operand
     oracle within the accumulation bound; FP32: against FP64 within the FP32
     bound), and each form's error against FP64 must stay within its stated
     tolerance at every depth below the frame maximum."""
-    clips, sr = G.workload("levels_1024x10s")
+    clips, sr, idx, sub, exact = levels
     spec = _spec()
     fe = melt.Frontend(sr=sr, precision=prec)
     got = gpu_features(fe, clips)
     fe.close()
     assert got.shape == (1024 * 998, 80)
-    idx = list(range(0, 1024, 32))
-    sub = [clips[b] for b in idx]
     rows = np.concatenate([np.arange(998) + b * 998 for b in idx])
-    exact = oracle_features(spec, sub)
     if prec == "fp32":
         ref, bound = exact, log_error_bound(spec, sub, fp32_sum_error(spec.n_fft))
     else:
