@@ -74,15 +74,13 @@ bool plan_smem(const TcBasis* tb, TcParams& p, int n_mfcc) {
   p.nq = p.zrows * (p.H / 4);
   p.kstep_bytes = (uint32_t)tb->kstep_bytes;
   const int parts = P == MELT_BF16X3 ? 2 : 1;
-  if (P == MELT_FP8E4M3) {
-    p.lbo_a = kF * 16 + 16;                    // 128 rows x 16 B, +16 B spreads banks
-    p.a_bytes = p.lbo_a * (uint32_t)(p.KS * 2);
-  } else {
-    int zr = p.zrows;
-    while ((zr & 7) != 1) ++zr;                // rows % 8 == 1: converter stores spread banks
-    p.lbo_a = (uint32_t)zr * 16;
-    p.a_bytes = p.lbo_a * (uint32_t)(p.H / 8);
-  }
+  // A operand: the tile's Z rows in the K-major core-matrix layout, one core
+  // column per 16 bytes of a row (8 BF16 or 16 e4m3 samples; FP8 rows are
+  // padded to whole 32-sample K-steps)
+  int zr = p.zrows;
+  while ((zr & 7) != 1) ++zr;                  // rows % 8 == 1: converter stores spread banks
+  p.lbo_a = (uint32_t)zr * 16;
+  p.a_bytes = p.lbo_a * (uint32_t)(P == MELT_FP8E4M3 ? 2 * ((p.H + 31) / 32) : p.H / 8);
   p.abuf_bytes = p.a_bytes * parts;
   p.step_bytes = p.kstep_bytes * parts;
   melt_plan cands[kMaxCands];
@@ -106,7 +104,8 @@ namespace {
 
 bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) {
   const int P = tb->precision;
-  if (c.cta_pair != 0 || c.schedule != 0) return false;
+  if (c.cta_pair != 0 || c.schedule != 0 || P == MELT_FP8E4M3) return false;  // FP8 runs in CTA pairs
+  p.nacc = 2;
   p.Hd = 0;
   p.NS = p.CH = p.NCHUNK = 0;
   p.st_bytes = p.off_st = 0;
@@ -134,29 +133,25 @@ bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) 
   off += align_up(8 * p.KS, 128);
   p.off_misc = off;
   off += 128;
-  p.off_scale = off;
-  off += (P == MELT_FP8E4M3) ? kScaleRing * kF * 4 : 0;
-  p.off_rowmax = off;
-  off += (P == MELT_FP8E4M3) ? align_up((2 * p.zrows + kF) * 4, 128) : 0;
   p.off_dct = off;
   off += align_up(4 * n_mfcc * p.MP, 128);
   if (off + 128 > kSmemLimit) return false;
   p.smem_total = off + 128;
   p.tmem_cols = p.NC <= 32 ? 64 : p.NC <= 64 ? 128 : p.NC <= 128 ? 256 : 512;
   p.acc_stride = p.tmem_cols / 2;
-  p.idesc = idesc_f32acc(P == MELT_FP8E4M3 ? 0u : 1u, kF, p.NC);
+  p.idesc = idesc_f32acc(1u, kF, p.NC);
   p.desc_hi = (128u >> 4) | (1u << 14);  // SBO = 128 B; version bit (descriptor bit 46)
   return true;
 }
 
-// CTA-pair layout (BF16): A buffers, the waveform staging ring and this
+// CTA-pair layout (BF16, FP8): A buffers, the waveform staging ring and this
 // CTA's half of the basis (resident), then barriers and tables.  The ring
 // takes every slot that still fits (2..8).
 bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) {
   const bool fp8 = tb->precision == MELT_FP8E4M3;
   if (c.cta_pair != 1 || (tb->precision != MELT_BF16 && !fp8) || !tb->d_b2) return false;
-  // FP8: a frame's 16-sample groups must not straddle staged chunks
-  if (fp8 && (p.H % 16) != 0) return false;
+  // FP8: a converter lane holds at most two quads of a Z row
+  if (fp8 && p.H > 256) return false;
   if (c.basis_resident != 1 || c.a_buffers < 1 || c.a_buffers > 2) return false;
   if (c.prefetch_tiles < 0 || c.prefetch_tiles > kMaxPrefetch) return false;
   if (c.schedule != 0 && c.schedule != 1) return false;
@@ -172,6 +167,14 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
   // fused correction MLP: its weight half in shared memory, one projection
   // accumulator in TMEM and the MLP's operands beside it
   p.Hd = fp8 ? 0 : tb->mlp_hd;
+  // TMEM: two projection accumulators 256 columns apart when room is left
+  // beside the first for FP8's scale-factor columns (sfg groups of four per A
+  // buffer, then kSfBCols for the basis scale), else one
+  p.sfg = fp8 ? (p.J + 3) / 4 : 0;
+  const int sf_cols = fp8 ? 4 * p.sfg * p.ZB + kSfBCols : 0;
+  p.nacc = (p.Hd > 0 || p.NC + sf_cols > 256) ? 1 : 2;
+  p.sf_col = (uint32_t)(p.nacc == 2 ? p.NC : 256);
+  if (fp8 && (p.nacc == 2 ? p.NC + sf_cols > 256 : p.NC > 256 || 256 + sf_cols > 512)) return false;
   if (p.Hd > 0) {
     if (n_mfcc != 0 || p.NC > 160 || 160 + p.MP > 256 || 256 + p.Hd > 512) return false;
     p.mlp_half = (uint32_t)tb->mlp_half;
@@ -197,8 +200,8 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
   p.CH = ch;
   p.NCHUNK = (p.zrows + ch - 1) / ch;
   p.st_bytes = row_bytes * ch;
-  if (fp8 && ch < p.J - 1) return false;  // the streaming FP8 converter frees chunk ch-1 after chunk ch
-  for (int ns = 8; ns >= (fp8 ? 3 : 2); --ns) {
+  p.codes_stride = fp8 ? align_up((uint32_t)p.zrows + 3, 16) : 0u;
+  for (int ns = 8; ns >= 2; --ns) {
     const PairBars B(ns, p.ZB, p.KS);
     uint32_t off = 0;
     p.off_a = off;
@@ -215,18 +218,16 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
     off += align_up(8 * p.KS, 128);
     p.off_misc = off;
     off += 128;
-    p.off_scale = off;  // FP8: per-frame scale ring, then row maxima and frame multipliers
-    off += fp8 ? kScaleRing * kF * 4 : 0u;
-    p.off_rowmax = off;  // row maxima (2 zrows), then per-frame multiplier and sample locations (4 kF)
-    off += fp8 ? align_up((2 * p.zrows + 4 * kF) * 4, 128) : 0u;
+    p.off_codes = off;  // FP8: the scale code of every Z row of the tile, per A buffer
+    off += fp8 ? align_up(p.codes_stride * (uint32_t)p.ZB, 128) : 0u;
     p.off_dct = off;
     off += align_up(4 * n_mfcc * p.MP, 128);
     if (off + 128 > kSmemLimit) continue;
     p.NS = ns;
     p.smem_total = off + 128;
-    p.tmem_cols = p.NC <= 32 ? 64 : p.NC <= 64 ? 128 : p.NC <= 128 ? 256 : 512;
+    p.tmem_cols = fp8 ? 512 : p.NC <= 32 ? 64 : p.NC <= 64 ? 128 : p.NC <= 128 ? 256 : 512;
     p.acc_stride = p.tmem_cols / 2;
-    p.idesc = idesc_f32acc(fp8 ? 0u : 1u, 2 * kF, p.NC);  // M = 256 over the pair
+    p.idesc = fp8 ? idesc_mxf8(2 * kF, p.NC) : idesc_f32acc(1u, 2 * kF, p.NC);  // M = 256 over the pair
     p.desc_hi = (128u >> 4) | (1u << 14);
     return true;
   }
@@ -252,18 +253,17 @@ int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap
   const int sb = (int)std::max(1u, p.kstep_bytes * (tb->precision == MELT_BF16X3 ? 2u : 1u));
   melt_plan alts[2];
   int n_alt = 0;
-  if (tb->precision == MELT_BF16 && tb->d_b2) {
+  if ((tb->precision == MELT_BF16 || tb->precision == MELT_FP8E4M3) && tb->d_b2) {
     // CTA pairs first (measured on the 64 x 30 s batch at M = 80: 41 us
     // against 50 us single-CTA).  A staging ring of fewer than 4 slots keeps
     // too few bytes in flight; an L2 prefetch stream one tile ahead makes up
     // for it (M = 128, two A buffers, 2 slots: 58 us against 66 us without,
     // and 63 us with one A buffer and more slots), but costs time where the
     // ring is deep enough (M = 80, 5 slots: 42.5 against 42.1 us) and with
-    // the correction fused (167 against 164 us).  FP8 pairs are a plan a
-    // caller may set: their converters quantise every frame separately
-    // (per-frame scales), and the pair form runs 177 us against 161 us for
-    // the single-CTA FP8 kernel on the same batch.  The static schedule is
-    // the default: the dynamic one measured no gain (42.6 against 42.4 us).
+    // the correction fused (167 against 164 us).  FP8 runs in CTA pairs only
+    // (its converter is the polyphase one with a per-row scale).  The static
+    // schedule is the default: the dynamic one measured no gain (42.6 against
+    // 42.4 us).
     for (int zb = 2; zb >= 1; --zb) {
       melt_plan pc{1, zb, 0, p.KS, 1, 1, kDefaultSchedule};
       TcParams q = p;
@@ -277,6 +277,10 @@ int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap
         if (n_alt < 2) alts[n_alt++] = alt;
       }
     }
+  }
+  if (tb->precision == MELT_FP8E4M3) {  // no single-CTA FP8 layouts
+    for (int i = 0; i < n_alt && n < cap; ++i) out[n++] = alts[i];
+    return n;
   }
   add(1, 2, 2, p.KS, 1);
   const int kps_hi = std::max(1, std::min(p.KS, 65536 / sb));   // <= 64 KB per slot
@@ -298,17 +302,15 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
   if (M > 128) return MELT_ERR_UNSUPPORTED;
   const int MP = (M + 15) / 16 * 16, NC = 2 * MP;
   const int J = (N + H - 1) / H;
-  int KS = 0;
-  std::vector<std::pair<int, int>> steps;  // BF16 forms: (j, first column r0)
-  if (P == MELT_FP8E4M3) {
-    KS = (N + 31) / 32;
-  } else {
-    for (int j = 0; j < J; ++j) {
-      const int kj = std::min(H, N - j * H);
-      for (int kk = 0; kk < (kj + 15) / 16; ++kk) steps.push_back({j, 16 * kk});
-    }
-    KS = (int)steps.size();
+  // K-steps in (slice j, first sample r0 of the step) order; a step covers
+  // 16 samples of slice j (BF16 forms) or 32 (FP8)
+  const int kstep = P == MELT_FP8E4M3 ? 32 : 16;
+  std::vector<std::pair<int, int>> steps;
+  for (int j = 0; j < J; ++j) {
+    const int kj = std::min(H, N - j * H);
+    for (int kk = 0; kk < (kj + kstep - 1) / kstep; ++kk) steps.push_back({j, kstep * kk});
   }
+  const int KS = (int)steps.size();
   const size_t kstep_bytes = (size_t)NC * 32;  // 2 core columns x NC rows x 16 B
   const int parts = (P == MELT_BF16X3) ? 2 : 1;
   std::vector<uint8_t> img((size_t)KS * parts * kstep_bytes, 0);
@@ -320,15 +322,18 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
   };
   for (int s = 0; s < KS; ++s) {
     uint8_t* blk = img.data() + (size_t)s * parts * kstep_bytes;
+    const int j = steps[s].first, r0 = steps[s].second;
+    const int kj = std::min(H, N - j * H);  // samples of slice j; zero past them
     for (int cc = 0; cc < 2; ++cc)
       for (int row = 0; row < NC; ++row) {
         if (P == MELT_FP8E4M3) {
+          // 16 e4m3 values per core-column row: W 2^8 (the MMA scales by 2^-8)
           for (int e = 0; e < 16; ++e) {
-            const int n = 32 * s + 16 * cc + e;
-            blk[(size_t)cc * NC * 16 + row * 16 + e] = e4m3_bits(wval(row, n) * 448.0);
+            const int r = r0 + 16 * cc + e;
+            const double w = r < kj ? std::ldexp(wval(row, j * H + r), 8) : 0.0;
+            blk[(size_t)cc * NC * 16 + row * 16 + e] = e4m3_bits(w);
           }
         } else {
-          const int j = steps[s].first, r0 = steps[s].second;
           for (int e = 0; e < 8; ++e) {
             const int r = r0 + 8 * cc + e;
             const double w = (r < H) ? wval(row, j * H + r) : 0.0;
@@ -348,18 +353,15 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
   tb->n_mels = M;
   tb->J = J;
   tb->ksteps = KS;
-  tb->kstep_k = P == MELT_FP8E4M3 ? 32 : 16;
+  tb->kstep_k = kstep;
   tb->n_cols = NC;
   tb->kstep_bytes = kstep_bytes;
   tb->n_mfcc = c.n_mfcc;
-  {
-    TcParams probe;
-    std::memset(&probe, 0, sizeof(probe));
-    if (!plan_smem(tb, probe, c.n_mfcc)) return MELT_ERR_UNSUPPORTED;  // operands do not fit shared memory
+  if (P != MELT_FP8E4M3) {  // the single-CTA image (FP8 runs in CTA pairs only)
+    if (melt::dev_alloc(&tb->d_b, img.size()) != cudaSuccess) return MELT_ERR_OOM;
+    if (cudaMemcpy(tb->d_b, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return MELT_ERR_CUDA;
   }
-  if (melt::dev_alloc(&tb->d_b, img.size()) != cudaSuccess) return MELT_ERR_OOM;
-  if (cudaMemcpy(tb->d_b, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-    return MELT_ERR_CUDA;
   if (P == MELT_BF16 || P == MELT_FP8E4M3) {
     // CTA-pair image: the K-step blocks of basis rows [0, MP) (W_r), then those
     // of rows [MP, 2 MP) (W_i); each block is 2 core columns x MP rows x 16 B
@@ -379,6 +381,11 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
     const size_t sb = sizeof(unsigned long long) * 2 * kSchedWords;
     if (melt::dev_alloc(&tb->d_sched, sb) != cudaSuccess) return MELT_ERR_OOM;
     if (cudaMemset(tb->d_sched, 0, sb) != cudaSuccess) return MELT_ERR_CUDA;
+  }
+  {
+    TcParams probe;
+    std::memset(&probe, 0, sizeof(probe));
+    if (!plan_smem(tb, probe, c.n_mfcc)) return MELT_ERR_UNSUPPORTED;  // operands do not fit shared memory
   }
   return MELT_OK;
 }
@@ -508,7 +515,7 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
   attr[1].val.clusterDim.x = 2;
   attr[1].val.clusterDim.y = 1;
   attr[1].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(pair_threads(fused, tb->precision), 1, 1);
+  cfg.blockDim = dim3(pair_threads(fused), 1, 1);
   cfg.numAttrs = 2;
   TcBasis* mtb = const_cast<TcBasis*>(tb);
   if (mtb->pair_clusters < 0 || mtb->pair_smem != smem) {

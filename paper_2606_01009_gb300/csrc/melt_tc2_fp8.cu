@@ -1,5 +1,5 @@
 // Instantiations of the CTA-pair tensor-core MelT kernel with FP8 e4m3
-// operands and per-frame scales.
+// operands (per-row power-of-two scales applied by block-scaled MMAs).
 #include "melt_tc2_kernel.cuh"
 
 namespace melt {

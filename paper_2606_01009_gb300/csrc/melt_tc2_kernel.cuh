@@ -12,6 +12,14 @@
 // Each CTA's TMEM receives R and I of its own frames, so the epilogue is the
 // single-CTA one.
 //
+// FP8 e4m3 (template PREC): the converters quantise each polyphase Z row
+// (H samples) with its own power-of-two scale 2^e_u, e_u the least integer
+// with max|row| 2^-e_u <= 448, and write the rows' UE8M0 scale codes into
+// TMEM; the MMAs are block-scaled (kind::mxf8f6f4), so the tensor cores apply
+// 2^e_u to every product of row u (the scale of A row t in slice j is that of
+// Z row t + j, selected by the scale-factor byte j) and 2^-8 to the basis,
+// which is stored as e4m3(W 2^8).  The accumulator holds R and I directly.
+//
 // Warp roles per CTA (11 warps; 15 with the fused MLP):
 //   warps 0-3   epilogue: TMEM -> registers, R^2 + I^2, log, (DCT), store (with
 //               the fused MLP, warps 0-7: warps e and e+4 read the same 32 TMEM
@@ -19,7 +27,8 @@
 //   next warp   TMEM allocation for the pair; in the even CTA, the MMA issuer
 //   next warp   basis producer: this CTA's half of the basis, once
 //   next warp   waveform producer: bulk copies of the tile's FP32 span into a ring
-//   last four   converters: staged FP32 samples -> polyphase Z rows (BF16)
+//   last four   converters: staged FP32 samples -> polyphase Z rows (BF16, or
+//               e4m3 with per-row scales written to TMEM)
 //
 // Fused correction MLP (template flag MLP).  After the log-Mel of a tile the
 // epilogue writes x-hat = (x - mu)/sd as BF16 into TMEM and the even CTA
@@ -49,20 +58,15 @@ namespace tc {
 constexpr int kPCvtWarps = 4;
 constexpr int kPCvtThreads = 32 * kPCvtWarps;  // 128
 __host__ __device__ constexpr int pair_epi_warps(bool mlp) { return mlp ? 8 : 4; }
-// Converter warps: 4 (BF16, polyphase: each sample converted once), 8 for
-// FP8, whose frames are quantised one by one (2.5x the samples, more work
-// per sample): two warps per SM sub-partition hide each other's latency.
-__host__ __device__ constexpr int pair_cvt_warps(int prec) { return prec == MELT_FP8E4M3 ? 8 : 4; }
-__host__ __device__ constexpr int pair_threads(bool mlp, int prec = MELT_BF16) {
-  return 32 * (pair_epi_warps(mlp) + 3 + pair_cvt_warps(prec));
-}
-constexpr int kPCvtWarpsF8 = pair_cvt_warps(MELT_FP8E4M3);
-constexpr int kPCvtThreadsF8 = 32 * kPCvtWarpsF8;
+__host__ __device__ constexpr int pair_threads(bool mlp) { return 32 * (pair_epi_warps(mlp) + 3 + kPCvtWarps); }
 constexpr int kPQuads = 8;  // float4s per converter thread per staged chunk (<= 16 KB)
+constexpr uint32_t kSfOne = 0x7F7F7F7Fu;    // four UE8M0 codes of 2^0
+constexpr uint32_t kSfBasis = 0x77777777u;  // four UE8M0 codes of 2^-8 (the e4m3 basis holds W 2^8)
+constexpr int kSfBCols = 16;                // TMEM columns holding the basis scale (any layout reads 2^-8)
 
 struct PairBars {
   int s_full, s_empty, z_full, z_empty, b_full, peer_b, t_full, t_empty, h_full, a2_full, y_full,
-      sc_full, drain, sched_full, sched_empty, total;
+      drain, sched_full, sched_empty, total;
   __host__ __device__ PairBars(int NS, int ZB, int KS) {
     s_full = 0;
     s_empty = s_full + NS;
@@ -75,8 +79,7 @@ struct PairBars {
     h_full = t_empty + 2;  // fused MLP: hidden layer in TMEM
     a2_full = h_full + 1;  //            GELU(H) written back (both CTAs' epilogues)
     y_full = a2_full + 1;  //            MLP output in TMEM
-    sc_full = y_full + 1;  // FP8: per-frame scales of a tile ready (kScaleRing deep)
-    drain = sc_full + kScaleRing;
+    drain = y_full + 1;
     sched_full = drain + 1;              // dynamic schedule: ring entry published (per CTA)
     sched_empty = sched_full + kSchedRing;  //               ring entry read by both epilogues
     total = sched_empty + kSchedRing;
@@ -331,7 +334,8 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
   const uint64_t hi = (uint64_t)p.desc_hi << 32;
   const uint32_t a_lo0 = ((c.sbase + p.off_a) >> 4) | ((p.lbo_a >> 4) << 16);
   const uint32_t abuf16 = p.abuf_bytes >> 4;
-  constexpr int nacc = MLP ? 1 : 2;  // the fused MLP's TMEM leaves room for one accumulator
+  const int nacc = MLP ? 1 : p.nacc;  // the fused MLP's TMEM leaves room for one accumulator
+  const uint32_t sfb = tmem_base + p.sf_col + (uint32_t)(4 * p.sfg * p.ZB);  // FP8: basis scale 2^-8
   int k = 0;
   bool ok = true;
   for (;; ++k) {
@@ -368,10 +372,16 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
 #pragma unroll
       for (int u = 0; u < 8; ++u)
         if (s0 + u < p.KS) {
-          if constexpr (PREC == MELT_FP8E4M3)
-            mma_f8_pair(d, hi | (alo + tx[u]), hi | ty[u], p.idesc, s0 + u > 0);
-          else
+          if constexpr (PREC == MELT_FP8E4M3) {
+            // K-step of slice j = tx >> 24: A row t is Z row t + j, whose scale is
+            // byte j % 4 of scale group j / 4 of this A buffer
+            const uint32_t j = tx[u] >> 24;
+            const uint32_t sfa = tmem_base + p.sf_col + (uint32_t)(4 * (p.sfg * zb)) + 4u * (j >> 2);
+            mma_f8_pair_bs(d, hi | (alo + (tx[u] & 0xFFFFFFu)), hi | ty[u], p.idesc | ((j & 3u) << 29), sfa, sfb,
+                           s0 + u > 0);
+          } else {
             mma_f16_pair(d, hi | (alo + tx[u]), hi | ty[u], p.idesc, s0 + u > 0);
+          }
         }
     }
     mma_commit_pair_mc(pbar(p, c, B.z_empty + zb), 3);
@@ -470,209 +480,131 @@ static __device__ void pair_convert(const TcParams& p, const PairCtx& c, const P
   }
 }
 
-// Shared-memory float4 load under a predicate (zeros otherwise), without a branch.
-static __device__ __forceinline__ float4 lds128_if(uint32_t addr, bool pred) {
-  float4 v;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.u32 p, %5, 0;\n\t"
-      "mov.b32 %0, 0;\n\tmov.b32 %1, 0;\n\tmov.b32 %2, 0;\n\tmov.b32 %3, 0;\n\t"
-      "@p ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n\t}"
-      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-      : "r"(addr), "r"((uint32_t)pred));
-  return v;
+// UE8M0 exponent of the scale of a Z row whose max |x| has float bits `bits`:
+// the least e with amax 2^-e <= 448 (amax = m 2^E, m in [1, 2): e = E - 8,
+// one more when m > 1.75), at least -127; -127 for an all-zero or subnormal
+// row.  Returns the code e + 127 (0..247).
+static __device__ __forceinline__ uint32_t fp8_row_code(uint32_t bits) {
+  const int ef = (int)(bits >> 23);
+  if (ef == 0) return 0u;
+  const int e = max(-127, ef - 127 - 8 + ((bits & 0x7FFFFFu) > 0x600000u ? 1 : 0));
+  return (uint32_t)(e + 127);
 }
 
-// Shared-memory 4-byte store under a predicate, without a branch.
-static __device__ __forceinline__ void sts32_if(uint32_t addr, uint32_t v, bool pred) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.u32 p, %2, 0;\n\t"
-      "@p st.shared.b32 [%0], %1;\n\t}" ::"r"(addr),
-      "r"(v), "r"((uint32_t)pred)
-      : "memory");
-}
-
-// The samples of a quad at or past the clip end set to zero, by selects (s =
-// span index of x.x).
-static __device__ __forceinline__ float4 clip_quad_sel(float4 x, int s, int nsamp) {
-  x.x = s < nsamp ? x.x : 0.f;
-  x.y = s + 1 < nsamp ? x.y : 0.f;
-  x.z = s + 2 < nsamp ? x.z : 0.f;
-  x.w = s + 3 < nsamp ? x.w : 0.f;
-  return x;
-}
-
-constexpr int kFRows = 4;    // FP8 pair converter: Z rows per warp per row-maximum batch
-constexpr int kFFrames = 4;  // FP8 pair converter: frames per warp per quantisation batch
-
-// FP8 converter: staged FP32 chunks -> quantised frame rows (im2col inside
-// shared memory only), with the frame's scale 448 / amax(frame).
+// FP8 e4m3 converter: staged FP32 chunks -> polyphase Z rows of e4m3 with a
+// power-of-two scale per row, and the rows' scale codes in TMEM.
 //
-// Frame f uses Z rows f .. f+J-1 (the last only up to KL = N - (J-1) H).  As
-// chunk ch of the span (Z rows [ch CH, (ch+1) CH)) arrives, the warps reduce
-// max |x| of its rows, then scale and quantise every frame whose rows are all
-// present (f < (ch+1) CH - J + 1, or all at the last chunk), and release chunk
-// ch-1, which no remaining frame needs (CH >= J - 1).  A warp takes one frame
-// at a time: lane l converts float4 number l + 32 i of the frame's samples
-// (consecutive lanes, consecutive 16 bytes) and stores its 4 e4m3 bytes at
-// core column (l + 32 i) / 4 of the frame's row, byte 4 ((l + 32 i) % 4); the
-// core-column pitch lbo_a = 2064 bytes puts the 32 lanes on 32 banks.  A
-// frame lies in at most two chunks, whose ring slots it looks up once.
-// Named barriers take the AND of the warps' wait results, so all four warps
-// leave together when a wait gives up.
+// A warp takes whole rows of a chunk (rows cw, cw + 4, ... of the chunk, two
+// at a time): lane l holds quads l and l + 32 of the row (H <= 256), the warp
+// reduces max |x| over them (float bits of non-negative values order like
+// unsigned ints), derives the row's exponent e, multiplies by 2^-e (exact)
+// and converts with saturating round-to-nearest-even.  Z element (u, r) sits
+// at (r / 16) lbo_a + 16 u + r % 16, so a quad of row u is 4 bytes at core
+// column q / 4, byte 4 (q % 4): lanes of a warp hit 32 different banks
+// (lbo_a = 16 mod 128).  The code of row u goes to shared memory; after the
+// tile's last chunk each warp writes, for the 32 TMEM lanes of its quarter
+// (frame t), one 32-bit word per group of four slices: byte j is the code of
+// Z row t + 4g + j, the scale of A row t in slice 4g + j.  The word is
+// repeated over the group's four columns (the MMA reads row t's scale in
+// lane t, column t / 32 of the group).
 static __device__ void pair_convert_fp8(const TcParams& p, uint8_t* gbase, const PairCtx& c,
-                                        const PairBars& B, int cvt0) {
-  const int ct = threadIdx.x - 32 * cvt0;
-  const int cw = ct >> 5, lane = threadIdx.x & 31;
-  const int KL = p.N - (p.J - 1) * p.H;
-  const int nq = p.KS * 8;                    // float4s per frame row, zero past N
-  const int h4 = p.H >> 2;
-  const int chunk_samples = p.CH * p.H;
-  unsigned* rowmax = reinterpret_cast<unsigned*>(gbase + p.off_rowmax);  // [zrows] float bits
-  unsigned* rowpre = rowmax + p.zrows;                                   // [zrows]
-  float* finv = reinterpret_cast<float*>(rowpre + p.zrows);              // [kF] 448 / amax
-  int* fsplit = reinterpret_cast<int*>(finv + kF);                        // [kF]
-  uint32_t* fbase0 = reinterpret_cast<uint32_t*>(fsplit + kF);            // [kF]
-  uint32_t* fbase1 = fbase0 + kF;                                         // [kF]
-  float* scales = reinterpret_cast<float*>(gbase + p.off_scale);
+                                        const PairBars& B, int cvt0, uint32_t tmem_base) {
+  const int cw = (int)(threadIdx.x >> 5) - cvt0, lane = threadIdx.x & 31;
+  const int quarter = (threadIdx.x >> 5) & 3;  // the TMEM lanes this warp may access
+  const int h4 = p.H >> 2;                     // quads per Z row (<= 64)
   const uint32_t st0 = c.sbase + p.off_st;
-  // float4 j of a frame row goes to core column j / 4, byte 4 (j % 4) of it:
-  // for j = lane + 32 m that is column lane / 4 + 8 m
-  const uint32_t lane_col = (uint32_t)(lane >> 2) * p.lbo_a + 4u * (uint32_t)(lane & 3);
-  int g = 0;  // chunks consumed so far (ring position)
+  uint8_t* codes_all = gbase + p.off_codes;
+  // zero both A buffers once: bytes past H in a row's last core columns stay zero
+  for (uint32_t o = 16u * (uint32_t)(threadIdx.x - 32 * cvt0); o < p.abuf_bytes * p.ZB; o += 16u * kPCvtThreads)
+    sts128(c.sbase + p.off_a + o, make_uint4(0u, 0u, 0u, 0u));
+  fence_proxy_async();
+  int slot = 0;
+  uint32_t sphase = 0;
   for (int k = 0;; ++k) {
     bool okq = true;
     const int qp = k == 0 ? c.cluster : pair_next_warp(p, c, B, k, okq);
     // every converter warp reads the same entry; a timeout in any of them stops all
-    if (!named_barrier_and(1, kPCvtThreadsF8, okq) || qp >= p.n_pairs) break;
+    if (!named_barrier_and(1, kPCvtThreads, okq) || qp >= p.n_pairs) break;
     const int zb = p.ZB == 2 ? (k & 1) : 0;
     bool ok = warp_wait_cl(pbar(p, c, B.z_empty + zb), ((p.ZB == 2 ? (k >> 1) : k) & 1) ^ 1, c.abort, p.err);
-    if (!named_barrier_and(1, kPCvtThreadsF8, ok)) break;
+    if (!named_barrier_and(1, kPCvtThreads, ok)) break;
     const TileDesc td = pair_tile(p, c, qp);
     const int nsamp = td.n_samples;
-    const bool tail = nsamp < p.zrows * p.H;  // the clip ends inside the span: clip samples past it
-    const uint32_t abase = c.sbase + p.off_a + zb * p.abuf_bytes;
+    const uint32_t zaddr = c.sbase + p.off_a + zb * p.abuf_bytes;
+    uint8_t* codes = codes_all + zb * p.codes_stride;
     if (td.n_frames > 0) {
-      int f_done = 0;
       for (int ch = 0; ch < p.NCHUNK; ++ch) {
-        const int slot = (g + ch) % p.NS;
-        ok = warp_wait(pbar(p, c, B.s_full + slot), ((g + ch) / p.NS) & 1, c.abort, p.err);
-        ok = named_barrier_and(1, kPCvtThreadsF8, ok);  // every warp takes the same decision
-        if (!ok) break;
-        // 1. max |x| over each row of the chunk and over its first KL samples.
-        //    A warp takes rows cw, cw + 4, ... in batches of kFRows rows and
-        //    issues all of a batch's loads before its reductions.
-        const uint32_t sp = st0 + (uint32_t)slot * p.st_bytes;
-        const int r0 = ch * p.CH, rows = min(p.CH, p.zrows - r0);
-        for (int rb = cw; rb < rows; rb += kPCvtWarpsF8 * kFRows) {
-          unsigned mf[kFRows], mp[kFRows];
+        ok = warp_wait(pbar(p, c, B.s_full + slot), sphase, c.abort, p.err);
+        if (!named_barrier_and(1, kPCvtThreads, ok)) break;
+        const int rows = min(p.CH, p.zrows - ch * p.CH);
+        const uint32_t st = st0 + slot * p.st_bytes;
+        const int s_base = ch * p.CH * p.H;
+        const bool tail = s_base + rows * p.H > nsamp;
+        for (int rl0 = cw; rl0 < rows; rl0 += 2 * kPCvtWarps) {
+          float4 x[2][2];
 #pragma unroll
-          for (int r = 0; r < kFRows; ++r) mf[r] = mp[r] = 0u;
-          for (int j = lane; j < h4; j += 32) {
-            float4 v[kFRows];
+          for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int r = 0; r < kFRows; ++r) {
-              const int rl = rb + kPCvtWarpsF8 * r;
-              v[r] = lds128_if(sp + 16u * (uint32_t)(rl * h4 + j), rl < rows);
+            for (int h = 0; h < 2; ++h) {
+              const int rl = rl0 + kPCvtWarps * r, j = lane + 32 * h;
+              const bool live = rl < rows && j < h4;
+              x[r][h] = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (live) {
+                asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                             : "=f"(x[r][h].x), "=f"(x[r][h].y), "=f"(x[r][h].z), "=f"(x[r][h].w)
+                             : "r"(st + 16u * (uint32_t)(rl * h4 + j)));
+                if (tail) clip_quad(x[r][h], s_base + rl * p.H + 4 * j, nsamp);
+              }
             }
 #pragma unroll
-            for (int r = 0; r < kFRows; ++r) {
-              const float4 x = tail ? clip_quad_sel(v[r], (r0 + rb + kPCvtWarpsF8 * r) * p.H + 4 * j, nsamp) : v[r];
-              const unsigned m = __float_as_uint(fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
-              mf[r] = max(mf[r], m);
-              mp[r] = 4 * j < KL ? max(mp[r], m) : mp[r];
-            }
-          }
-#pragma unroll
-          for (int r = 0; r < kFRows; ++r) {
-            const int rl = rb + kPCvtWarpsF8 * r;
-            const unsigned a = __reduce_max_sync(0xffffffffu, mf[r]);
-            const unsigned b = __reduce_max_sync(0xffffffffu, mp[r]);
-            if (lane == 0 && rl < rows) {
-              rowmax[r0 + rl] = a;
-              rowpre[r0 + rl] = b;
-            }
-          }
-        }
-        named_barrier(1, kPCvtThreadsF8);
-        // 2. the frames whose rows are all present now.  Each converter thread
-        //    sets up one frame: its multiplier 448 / amax and where its samples
-        //    are.  Such a frame starts in this chunk or in the previous one
-        //    (CH >= J - 1) and, if in the previous one, ends in this one.
-        const int f_hi = ch == p.NCHUNK - 1 ? kF : min(kF, (ch + 1) * p.CH - p.J + 1);
-        {
-          const int f = f_done + ct;  // at most kF frames per chunk
-          if (f < f_hi) {
-            unsigned am = rowpre[f + p.J - 1];
-            for (int j = 0; j < p.J - 1; ++j) am = max(am, rowmax[f + j]);
-            const float amax = __uint_as_float(am);
-            const bool pos = amax > 0.f;
-            finv[f] = pos ? 448.f / amax : 1.f;
-            scales[(k % kScaleRing) * kF + f] = (pos ? amax / 448.f : 1.f) / 448.f;
-            const bool here = f >= ch * p.CH;
-            const int c0 = here ? ch : ch - 1;
-            const int s0 = f * p.H;
-            const int prev = (g + ch + p.NS - 1) % p.NS;
-            fsplit[f] = (c0 + 1) * chunk_samples - s0;  // samples before chunk c0 + 1
-            fbase0[f] = st0 + (uint32_t)(here ? slot : prev) * p.st_bytes + 4u * (uint32_t)(s0 - c0 * chunk_samples);
-            fbase1[f] = sp;  // chunk ch: only a frame that started in chunk ch - 1 reaches it
-          }
-        }
-        named_barrier(1, kPCvtThreadsF8);
-        // 3. quantised frame rows.  A warp takes kFFrames frames at a time
-        //    (frames f0, f0 + 4, ...) and issues two float4 loads per frame
-        //    before converting; loads, clipping and stores are predicated.
-        for (int f0 = f_done + cw; f0 < f_hi; f0 += kPCvtWarpsF8 * kFFrames) {
-          float inv[kFFrames];
-          uint32_t base0[kFFrames], base1[kFFrames], arow[kFFrames];
-          int split[kFFrames], s0v[kFFrames];
-          bool live[kFFrames];
-#pragma unroll
-          for (int u = 0; u < kFFrames; ++u) {
-            const int f = f0 + kPCvtWarpsF8 * u;
-            live[u] = f < f_hi;
-            const int fc = live[u] ? f : f0;
-            inv[u] = finv[fc];
-            split[u] = fsplit[fc];
-            base0[u] = fbase0[fc];
-            base1[u] = fbase1[fc];
-            s0v[u] = fc * p.H;
-            arow[u] = abase + (uint32_t)fc * 16u;
-          }
-          for (int jb = lane, i = 0; jb < nq; jb += 64, ++i) {
-            const uint32_t col = lane_col + (uint32_t)(16 * i) * p.lbo_a;  // core column of j = jb, byte in it
-            float4 v[2][kFFrames];
+          for (int r = 0; r < 2; ++r) {
+            const int rl = rl0 + kPCvtWarps * r;
+            float m = 0.f;
 #pragma unroll
             for (int h = 0; h < 2; ++h)
+              m = fmaxf(m, fmaxf(fmaxf(fabsf(x[r][h].x), fabsf(x[r][h].y)), fmaxf(fabsf(x[r][h].z), fabsf(x[r][h].w))));
+            const uint32_t code = fp8_row_code(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
+            const float inv = __uint_as_float((254u - code) << 23);  // 2^-e, e = code - 127
+            if (rl < rows) {
+              const int u = ch * p.CH + rl;
+              if (lane == 0) codes[u] = (uint8_t)code;
 #pragma unroll
-              for (int u = 0; u < kFFrames; ++u) {
-                const int n = 4 * (jb + 32 * h);
-                const uint32_t a = n < split[u] ? base0[u] + 4u * (uint32_t)n : base1[u] + 4u * (uint32_t)(n - split[u]);
-                v[h][u] = lds128_if(a, live[u] && n < p.N);
+              for (int h = 0; h < 2; ++h) {
+                const int j = lane + 32 * h;
+                if (j < h4) {
+                  const uint32_t w = pack_e4m3x4(x[r][h].x * inv, x[r][h].y * inv, x[r][h].z * inv, x[r][h].w * inv);
+                  asm volatile("st.shared.b32 [%0], %1;" ::"r"(zaddr + (uint32_t)(j >> 2) * p.lbo_a + 16u * (uint32_t)u +
+                                                               4u * (uint32_t)(j & 3)),
+                               "r"(w));
+                }
               }
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-              for (int u = 0; u < kFFrames; ++u) {
-                const int j = jb + 32 * h;
-                const float4 x = tail ? clip_quad_sel(v[h][u], s0v[u] + 4 * j, nsamp) : v[h][u];
-                const uint32_t w = pack_e4m3x4(x.x * inv[u], x.y * inv[u], x.z * inv[u], x.w * inv[u]);
-                sts32_if(arow[u] + col + (uint32_t)(8 * h) * p.lbo_a, w, live[u] && j < nq);
-              }
+            }
           }
         }
-        named_barrier(1, kPCvtThreadsF8);
-        if (ch > 0) warp_arrive(pbar(p, c, B.s_empty + (g + ch - 1) % p.NS));
-        f_done = f_hi;
+        warp_arrive(pbar(p, c, B.s_empty + slot));
+        if (++slot == p.NS) {
+          slot = 0;
+          sphase ^= 1;
+        }
       }
       if (!ok) break;
-      warp_arrive(pbar(p, c, B.s_empty + (g + p.NCHUNK - 1) % p.NS));
-      g += p.NCHUNK;
+      // every row's code is in shared memory: the scale words of this warp's TMEM lanes
+      named_barrier(1, kPCvtThreads);
+      const int t = 32 * quarter + lane;
+      for (int g = 0; g < p.sfg; ++g) {
+        uint32_t w = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int jj = 4 * g + j;
+          w |= (jj < p.J ? (uint32_t)codes[t + jj] : 0x7Fu) << (8 * j);
+        }
+        tmem_st4(tmem_base + ((uint32_t)(32 * quarter) << 16) + p.sf_col + (uint32_t)(4 * (p.sfg * zb + g)), w);
+      }
+      tmem_st_wait();
     }
+    tc_fence_before();
     fence_proxy_async();
     warp_arrive_leader(pbar(p, c, B.z_full + zb));
-    warp_arrive(pbar(p, c, B.sc_full + (k % kScaleRing)));
   }
 }
 
@@ -688,7 +620,6 @@ static __device__ __forceinline__ void half_chunks(int n, int halves, int h, int
 template <int NCH, bool MFCC, int EPW, int PREC>
 __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& c, const PairBars& B,
                               uint32_t tmem_base) {
-  const float* scales = reinterpret_cast<const float*>(gbase + p.off_scale);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3, half = warp >> 2;
   const int row = 32 * quarter + lane;
@@ -697,20 +628,16 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
   const int nch = p.MP >> 4;
   int c_lo, c_hi;
   half_chunks(nch, EPW / 4, half, c_lo, c_hi);
+  constexpr float sc = 1.f;  // every form's accumulator holds R and I (FP8: scaled by the MMA)
   for (int k = 0;; ++k) {
     bool okq = true;
     const int q = k == 0 ? c.cluster : pair_next_warp(p, c, B, k, okq);
     if (!okq || q >= p.n_pairs) break;
-    const int acc = k & 1;
+    const int acc = p.nacc == 2 ? (k & 1) : 0;
+    const uint32_t tphase = p.nacc == 2 ? ((k >> 1) & 1) : (k & 1);
     const TileDesc td = pair_tile(p, c, q);
-    if (!warp_wait_cl(pbar(p, c, B.t_full + acc), (k >> 1) & 1, c.abort, p.err)) break;
+    if (!warp_wait_cl(pbar(p, c, B.t_full + acc), tphase, c.abort, p.err)) break;
     sched_release(p, c, B, k);
-    float sc = 1.f;  // FP8: s_t / 448 of the frame (sample and basis scales)
-    if constexpr (PREC == MELT_FP8E4M3) {
-      if (!warp_wait(pbar(p, c, B.sc_full + (k % kScaleRing)), (k / kScaleRing) & 1, c.abort, p.err))
-        break;
-      sc = scales[(k % kScaleRing) * kF + row];
-    }
     tc_fence_after();
     const bool valid = row < td.n_frames;
     const uint32_t t0 = tmem_base + ((uint32_t)(32 * quarter) << 16) + acc * p.acc_stride;
@@ -925,7 +852,7 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
 }
 
 template <int NCH, bool MFCC, bool MLP, int PREC = MELT_BF16>
-__global__ void __launch_bounds__(pair_threads(MLP, PREC), 1) melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
   constexpr int EPW = pair_epi_warps(MLP);
   constexpr int kPMmaWarp = EPW, kPBWarp = EPW + 1, kPProdWarp = EPW + 2, kPCvtWarp0 = EPW + 3;
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -946,10 +873,10 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC), 1) melt_tc_pair_kerne
     auto bar = [&](int i) { return sbase + p.off_bar + 8 * i; };
     for (int i = 0; i < p.NS; ++i) {
       mbar_init(bar(B.s_full + i), 1);
-      mbar_init(bar(B.s_empty + i), pair_cvt_warps(PREC));
+      mbar_init(bar(B.s_empty + i), kPCvtWarps);
     }
     for (int i = 0; i < p.ZB; ++i) {
-      mbar_init(bar(B.z_full + i), 2 * pair_cvt_warps(PREC));  // converters of both CTAs (even CTA's copy is used)
+      mbar_init(bar(B.z_full + i), 2 * kPCvtWarps);  // converters of both CTAs (even CTA's copy is used)
       mbar_init(bar(B.z_empty + i), 1);
     }
     mbar_init(bar(B.b_full), 1);
@@ -961,7 +888,6 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC), 1) melt_tc_pair_kerne
     mbar_init(bar(B.h_full), 1);
     mbar_init(bar(B.a2_full), 2 * EPW);
     mbar_init(bar(B.y_full), 1);
-    for (int i = 0; i < kScaleRing; ++i) mbar_init(bar(B.sc_full + i), pair_cvt_warps(PREC));
     mbar_init(bar(B.drain), 1);
     for (int i = 0; i < kSchedRing; ++i) {
       mbar_init(bar(B.sched_full + i), 1);           // the even CTA's producer (here or remote)
@@ -975,16 +901,16 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC), 1) melt_tc_pair_kerne
     uint2* tab = reinterpret_cast<uint2*>(gbase + p.off_tab);
     const uint32_t b_lo0 = ((sbase + p.off_b) >> 4) | ((p.b_lbo >> 4) << 16);
     const uint32_t step16 = p.step_bytes >> 4;
-    if constexpr (PREC == MELT_FP8E4M3) {
-      // frame rows (im2col in shared memory): K-step s starts 2 s core columns in
-      for (int s = lane; s < p.KS; s += 32) tab[s] = make_uint2((2u * s * p.lbo_a) >> 4, b_lo0 + s * step16);
-    } else {
-      for (int j = 0, s0 = 0; j < p.J; ++j) {
-        const int steps = (min(p.H, p.N - j * p.H) + 15) / 16;
-        for (int kk = lane; kk < steps; kk += 32)
-          tab[s0 + kk] = make_uint2((2u * kk * p.lbo_a + 16u * j) >> 4, b_lo0 + (s0 + kk) * step16);
-        s0 += steps;
-      }
+    // steps in (slice j, K-group kk) order, the order of the basis image; a
+    // K-step is 16 samples (BF16) or 32 (FP8, which also keeps j in bits 24..31
+    // of the A entry for the scale-factor selection)
+    constexpr int kstep = PREC == MELT_FP8E4M3 ? 32 : 16;
+    for (int j = 0, s0 = 0; j < p.J; ++j) {
+      const int steps = (min(p.H, p.N - j * p.H) + kstep - 1) / kstep;
+      const uint32_t jtag = PREC == MELT_FP8E4M3 ? (uint32_t)j << 24 : 0u;
+      for (int kk = lane; kk < steps; kk += 32)
+        tab[s0 + kk] = make_uint2(((2u * kk * p.lbo_a + 16u * j) >> 4) | jtag, b_lo0 + (s0 + kk) * step16);
+      s0 += steps;
     }
   }
   if (warp == kPMmaWarp) {
@@ -1005,6 +931,22 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC), 1) melt_tc_pair_kerne
   cluster_sync_all();  // both CTAs' barriers exist before either arrives on the other's
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  if constexpr (PREC == MELT_FP8E4M3) {
+    // scale-factor columns: every row scale 2^0 until the converters write a
+    // tile's codes; the basis scale 2^-8 for good (the epilogue warps cover
+    // the four lane quarters); both CTAs' columns are set before any MMA
+    if (warp < 4) {
+      const uint32_t tl = tmem_base + ((uint32_t)(32 * warp) << 16) + p.sf_col;
+      const int na = 4 * p.sfg * p.ZB;
+      for (int col = 0; col < na; col += 4) tmem_st4(tl + col, kSfOne);
+      for (int col = 0; col < kSfBCols; col += 4) tmem_st4(tl + na + col, kSfBasis);
+      tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();
+    tc_fence_after();
+  }
   if (threadIdx.x == 0) pdl_launch_dependents();
 
   // MMA issuer and basis producer start at once (own data only; the basis
@@ -1027,7 +969,7 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC), 1) melt_tc_pair_kerne
   } else if (warp >= kPCvtWarp0) {
     pdl_wait();
     if constexpr (PREC == MELT_FP8E4M3)
-      pair_convert_fp8(p, gbase, c, B, kPCvtWarp0);
+      pair_convert_fp8(p, gbase, c, B, kPCvtWarp0, tmem_base);
     else
       pair_convert(p, c, B, kPCvtWarp0);
     __syncwarp();

@@ -1,9 +1,10 @@
 // Device side of the tensor-core MelT kernels (included by the two
 // instantiation units melt_tc_plain.cu and melt_tc_mfcc.cu).
 #pragma once
-// Tensor-core MelT kernels for sm_103a: BF16, split-BF16 (three products)
-// and FP8 e4m3 forms of the projection of Sec. III-A (Eq. 6), with power
-// (Eq. 7), log (Eq. 8) and the optional DCT-II (Eq. 9) fused in the epilogue.
+// Tensor-core MelT kernels for sm_103a: BF16 and split-BF16 (three products)
+// forms of the projection of Sec. III-A (Eq. 6), with power (Eq. 7), log
+// (Eq. 8) and the optional DCT-II (Eq. 9) fused in the epilogue.  (The FP8
+// e4m3 form runs in the CTA-pair kernel of melt_tc2_kernel.cuh.)
 //
 // One persistent CTA per SM walks a static round-robin list of tiles
 // (128 consecutive frames of one clip).  Warp roles (18 warps):
@@ -12,11 +13,11 @@
 //   warp  5     basis producer: bulk async copies (TMA engine) of the basis
 //               K-step blocks, once per CTA when the basis fits in shared
 //               memory next to two A buffers, else streamed through a ring
-//   warps 6-17  converters: waveform samples -> MMA A operand in shared memory
+//   warps 6-17  converters: waveform samples -> MMA A operand (BF16 Z rows) in shared memory
 //
 // Waveform path.  The converters read the tile's FP32 samples straight from
-// global memory into registers (coalesced 16-byte loads) and write the BF16 /
-// e4m3 A operand; one converter thread keeps the spans of the CTA's next
+// global memory into registers (coalesced 16-byte loads) and write the BF16
+// A operand (split-BF16: its hi and lo parts); one converter thread keeps the spans of the CTA's next
 // tiles streaming into L2 with bulk prefetches, so those loads are L2 hits.
 // No shared memory is spent on staging FP32 samples, which leaves room for a
 // resident basis next to two A buffers (conversion of tile k+1 overlaps the
@@ -32,11 +33,6 @@
 // K-major canonical layout with rows 16 B apart) and the j-shift is a
 // 16-byte offset of the A descriptor's start address.  The J slices
 // accumulate into the same TMEM tile.
-// FP8 needs a per-frame scale, which differs between the frames that share
-// a Z row, so the FP8 form first reduces max |x| per Z row, derives each
-// frame's scale, and then writes each frame row (im2col inside shared memory
-// only), scaled by 448/amax(frame).
-//
 // Accumulators: two TMEM tiles of 128 lanes x NC columns (NC = 2*MP, MP =
 // M rounded up to 16): columns [0, MP) hold R, [MP, 2MP) hold I.
 #include <cuda_bf16.h>
@@ -64,11 +60,9 @@ constexpr int kThreads = 32 * (kCvtWarp0 + kCvtWarps);  // 576
 constexpr int kCvtThreads = 32 * kCvtWarps;             // 384
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kF = kTileFrames;  // 128 = UMMA M
-constexpr int kScaleRing = 4;    // FP8 per-frame scale buffers in flight
 constexpr int kSchedRing = 16;   // dynamic pair schedule: published pair indices in flight
 constexpr int kSchedWords = 16;  // dynamic pair schedule: counters, one per launch in flight
 constexpr int kQuadBatch = 8;    // float4 loads per converter thread per batch (two batches in flight)
-constexpr int kItemBatch = 3;    // FP8 frame-row items (16 samples each) per batch
 constexpr int kEpiGroup = 2;     // 16-column chunks per TMEM wait in the epilogue
 constexpr int kMaxMfccTc = 128;  // DCT outputs of the tensor-core epilogue (matrix in shared memory)
 constexpr int kMaxPrefetch = 4;  // tiles whose spans may be prefetched into L2 ahead of use
@@ -91,7 +85,7 @@ struct TcParams {
   uint32_t step_bytes;   // one K-step of the basis (BF16X3: hi + lo parts)
   uint32_t bslot_bytes;  // one basis slot: kps K-steps (resident: one K-step)
   int kps;               // K-steps per streamed basis slot
-  uint32_t lbo_a;        // A operand: bytes between K-adjacent core matrices
+  uint32_t lbo_a;        // A operand: bytes between K-adjacent core matrices (8 rows x 16 B each)
   uint32_t a_bytes;      // one A part
   uint32_t abuf_bytes;   // one A buffer (BF16X3: hi + lo parts)
   int ZB;                // A buffers
@@ -99,7 +93,7 @@ struct TcParams {
   int b_resident;        // 1: the whole basis stays in shared memory for the CTA's life
   uint32_t tmem_cols, acc_stride, idesc;
   uint32_t desc_hi;      // high word of every operand descriptor (SBO = 128 B, version)
-  uint32_t off_a, off_b, off_bar, off_misc, off_scale, off_rowmax, off_tab, off_dct;
+  uint32_t off_a, off_b, off_bar, off_misc, off_tab, off_dct;
   uint32_t smem_total;   // dynamic shared memory bytes (incl. alignment slack)
   // CTA-pair kernel only: FP32 span staging ring and the half-basis layout
   int NS, CH, NCHUNK;    // staging slots, Z rows per chunk, chunks per tile
@@ -107,6 +101,13 @@ struct TcParams {
   uint32_t off_st;
   uint32_t b_lbo;        // B operand: bytes between the two K core columns of a K-step block
   int n_pairs;           // tile pairs (tile 2q + rank of pair q goes to CTA `rank`)
+  int nacc;              // projection accumulators in TMEM (2: the epilogue of tile k overlaps tile k+1's MMAs)
+  // CTA-pair kernel, FP8: per-Z-row scale codes (shared memory, one byte per
+  // row and A buffer) and the TMEM scale-factor columns: sfg groups of four
+  // columns per A buffer from sf_col, then the basis scale
+  uint32_t off_codes, codes_stride;
+  uint32_t sf_col;
+  int sfg;
   // CTA-pair kernel, dynamic schedule (dyn = 1): after its first pair, each
   // cluster claims the next ones from sched[0] (a launch-wide counter that
   // the last CTA to finish, counted in sched[1], resets to zero)
@@ -125,7 +126,7 @@ struct TcParams {
 
 // barrier indices
 struct Bars {
-  int z_full, z_empty, b_full, b_empty, t_full, t_empty, sc_full, drain, total;
+  int z_full, z_empty, b_full, b_empty, t_full, t_empty, drain, total;
   __host__ __device__ Bars(int ZB, int NB) {
     z_full = 0;
     z_empty = z_full + ZB;
@@ -133,8 +134,7 @@ struct Bars {
     b_empty = b_full + NB;
     t_full = b_empty + NB;
     t_empty = t_full + 2;
-    sc_full = t_empty + 2;
-    drain = sc_full + kScaleRing;
+    drain = t_empty + 2;
     total = drain + 1;
   }
 };
@@ -188,15 +188,6 @@ static __device__ __forceinline__ void sts128(uint32_t addr, uint4 v) {
 static __device__ __forceinline__ float4 ldg_stream(const float* p) {
   float4 v;
   asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "l"(p));
-  return v;
-}
-
-// Read of 4 samples that neighbouring threads read again (FP8 frame rows): L1-cached.
-static __device__ __forceinline__ float4 ldg_cached(const float* p) {
-  float4 v;
-  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                : "l"(p));
   return v;
@@ -342,14 +333,10 @@ __device__ void role_mma(const TcParams& p, uint8_t* gbase, uint32_t sbase, cons
           if (s < p.KS) {
             const uint64_t ad = hi | (alo + tx[u]);
             const uint64_t bd = hi | ty[u];
-            if constexpr (PREC == MELT_FP8E4M3) {
-              mma_f8(d, ad, bd, p.idesc, s > 0);
-            } else {
-              mma_f16(d, ad, bd, p.idesc, s > 0);
-              if constexpr (PREC == MELT_BF16X3) {
-                mma_f16(d, ad, hi | (ty[u] + bpart16), p.idesc, 1);
-                mma_f16(d, hi | (alo + tx[u] + apart16), bd, p.idesc, 1);
-              }
+            mma_f16(d, ad, bd, p.idesc, s > 0);
+            if constexpr (PREC == MELT_BF16X3) {
+              mma_f16(d, ad, hi | (ty[u] + bpart16), p.idesc, 1);
+              mma_f16(d, hi | (alo + tx[u] + apart16), bd, p.idesc, 1);
             }
           }
         }
@@ -371,14 +358,10 @@ __device__ void role_mma(const TcParams& p, uint8_t* gbase, uint32_t sbase, cons
           const uint32_t blo = blo0 + u * step16;
           const uint64_t ad = hi | (alo + t.x);
           const uint64_t bd = hi | blo;
-          if constexpr (PREC == MELT_FP8E4M3) {
-            mma_f8(d, ad, bd, p.idesc, s > 0);
-          } else {
-            mma_f16(d, ad, bd, p.idesc, s > 0);
-            if constexpr (PREC == MELT_BF16X3) {
-              mma_f16(d, ad, hi | (blo + bpart16), p.idesc, 1);
-              mma_f16(d, hi | (alo + t.x + apart16), bd, p.idesc, 1);
-            }
+          mma_f16(d, ad, bd, p.idesc, s > 0);
+          if constexpr (PREC == MELT_BF16X3) {
+            mma_f16(d, ad, hi | (blo + bpart16), p.idesc, 1);
+            mma_f16(d, hi | (alo + t.x + apart16), bd, p.idesc, 1);
           }
         }
         mma_commit(sbase + p.off_bar + 8 * (B.b_empty + bslot));
@@ -519,140 +502,11 @@ static __device__ void role_convert_bf16(const TcParams& p, uint32_t sbase, cons
   }
 }
 
-// Max over the lanes of a warp that hold the same Z row u, merged into
-// row_max[u] (float bits of non-negative values order like unsigned ints).
-// Every lane of the warp calls this together; rows >= zrows are ignored.
-static __device__ __forceinline__ void warp_row_max(unsigned* row_max, int u, unsigned bits,
-                                                    int zrows) {
-  const int lane = threadIdx.x & 31;
-  unsigned rem = 0xffffffffu;
-  while (rem) {
-    const int leader = __ffs(rem) - 1;
-    const int ul = __shfl_sync(0xffffffffu, u, leader);
-    const unsigned in = __ballot_sync(0xffffffffu, u == ul);
-    const unsigned m = __reduce_max_sync(0xffffffffu, u == ul ? bits : 0u);
-    if (lane == leader && ul < zrows && m) atomicMax(row_max + ul, m);
-    rem &= ~in;
-  }
-}
-
-// FP8 converter: per-Z-row max |x|, per-frame scale, quantised frame rows.
-static __device__ void role_convert_fp8(const TcParams& p, uint8_t* gbase, uint32_t sbase,
-                                 const Bars& B, volatile int* abort) {
-  const int ct = threadIdx.x - 32 * kCvtWarp0;
-  const int h4 = p.H >> 2;
-  const int du = kCvtThreads / h4, dc = kCvtThreads % h4;
-  const int KL = p.N - (p.J - 1) * p.H;  // samples of the last slice of a frame
-  const int G = 2 * p.KS;                // 16-sample groups per frame row
-  unsigned* rowmax = reinterpret_cast<unsigned*>(gbase + p.off_rowmax);  // [zrows]
-  unsigned* rowpre = rowmax + p.zrows;                                   // [zrows], r < KL
-  float* inv_s = reinterpret_cast<float*>(rowpre + p.zrows);             // [kF]
-  float* scales = reinterpret_cast<float*>(gbase + p.off_scale);
-  Prefetcher pf;
-  if (ct == 0) pf.start(p);
-  int k = 0;
-  TileDesc td_next;
-  if ((int)blockIdx.x < p.n_tiles) td_next = p.tiles[blockIdx.x];
-  for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++k) {
-    if (ct == 0) pf.step(p);
-    const int zb = p.ZB == 2 ? (k & 1) : 0;
-    const TileDesc td = td_next;
-    if (tile + (int)gridDim.x < p.n_tiles) td_next = p.tiles[tile + gridDim.x];
-    const float* src = p.wave + td.in_off;
-    const int nsamp = td.n_samples;
-    // 0. reset the row maxima (the previous tile's readers passed two barriers since)
-    for (int i = ct; i < 2 * p.zrows; i += kCvtThreads) rowmax[i] = 0u;
-    named_barrier(1, kCvtThreads);
-    // 1. max |x| per Z row, over the whole row and over its first KL samples
-    {
-      int u = ct / h4, c = ct - (ct / h4) * h4;
-      for (int q0 = 0; q0 < p.nq; q0 += kQuadBatch * kCvtThreads) {
-        float4 x[kQuadBatch];
-#pragma unroll
-        for (int i = 0; i < kQuadBatch; ++i) {
-          const int q = q0 + ct + i * kCvtThreads;
-          x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (q < p.nq && 4 * q < nsamp) x[i] = ldg_cached(src + 4 * q);
-        }
-#pragma unroll
-        for (int i = 0; i < kQuadBatch; ++i) {
-          const int q = q0 + ct + i * kCvtThreads;
-          clip_quad(x[i], 4 * q, nsamp);
-          const float m = fmaxf(fmaxf(fabsf(x[i].x), fabsf(x[i].y)), fmaxf(fabsf(x[i].z), fabsf(x[i].w)));
-          const unsigned bits = q < p.nq ? __float_as_uint(m) : 0u;
-          warp_row_max(rowmax, u, bits, p.zrows);
-          warp_row_max(rowpre, u, 4 * c < KL ? bits : 0u, p.zrows);
-          c += dc;
-          u += du;
-          if (c >= h4) {
-            c -= h4;
-            ++u;
-          }
-        }
-      }
-    }
-    named_barrier(1, kCvtThreads);
-    // 2. frame scale: s_t = amax/448, quantiser multiplier 448/amax (1 for silent frames)
-    if (ct < kF) {
-      const int f = ct;
-      float amax = __uint_as_float(rowpre[f + p.J - 1]);
-      for (int j = 0; j < p.J - 1; ++j) amax = fmaxf(amax, __uint_as_float(rowmax[f + j]));
-      const bool pos = amax > 0.f;
-      inv_s[f] = pos ? 448.f / amax : 1.f;
-      const float st = pos ? amax / 448.f : 1.f;
-      scales[(k % kScaleRing) * kF + f] = st / 448.f;
-    }
-    bool ok = warp_wait(sbase + p.off_bar + 8 * (B.z_empty + zb),
-                        ((p.ZB == 2 ? (k >> 1) : k) & 1) ^ 1, abort, p.err);
-    // all converter warps take the same decision at this barrier
-    if (!named_barrier_and(1, kCvtThreads, ok)) break;
-    // 3. quantised frame rows, K-major canonical layout (16-byte core rows)
-    const uint32_t abase = sbase + p.off_a + zb * p.abuf_bytes;
-    const int items = kF * G;
-    for (int i0 = 0; i0 < items; i0 += kItemBatch * kCvtThreads) {
-      float4 x[kItemBatch][4];
-#pragma unroll
-      for (int b = 0; b < kItemBatch; ++b) {
-        const int it = i0 + ct + b * kCvtThreads;
-        const int f = it / G, g = it - (it / G) * G;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int n = 16 * g + 4 * e;
-          const int s = f * p.H + n;
-          x[b][e] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (it < items && n < p.N && s < nsamp) x[b][e] = ldg_cached(src + s);
-        }
-      }
-#pragma unroll
-      for (int b = 0; b < kItemBatch; ++b) {
-        const int it = i0 + ct + b * kCvtThreads;
-        if (it < items) {
-          const int f = it / G, g = it - (it / G) * G;
-          const float inv = inv_s[f];
-          uint32_t w[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int n = 16 * g + 4 * e;
-            float4 v = x[b][e];
-            clip_quad(v, f * p.H + n, nsamp);
-            w[e] = pack_e4m3x4(v.x * inv, v.y * inv, v.z * inv, v.w * inv);
-          }
-          sts128(abase + (uint32_t)g * p.lbo_a + (uint32_t)f * 16u, make_uint4(w[0], w[1], w[2], w[3]));
-        }
-      }
-    }
-    fence_proxy_async();
-    warp_arrive(sbase + p.off_bar + 8 * (B.z_full + zb));
-    warp_arrive(sbase + p.off_bar + 8 * (B.sc_full + (k % kScaleRing)));
-  }
-}
-
 template <int PREC, int NCH, bool MFCC>
 __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase, const Bars& B,
                               uint32_t tmem_base, volatile int* abort) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = 32 * warp + lane;
-  const float* scales = reinterpret_cast<const float*>(gbase + p.off_scale);
   const float* dct = reinterpret_cast<const float*>(gbase + p.off_dct);  // [n_mfcc][dct_ld]
   const bool vec8 = ((p.n_out & 7) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 31) == 0);
   const int nch = p.MP >> 4;
@@ -664,13 +518,6 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
     const TileDesc td = td_next;  // loaded one tile early
     if (tile + (int)gridDim.x < p.n_tiles) td_next = p.tiles[tile + gridDim.x];
     if (!warp_wait(sbase + p.off_bar + 8 * (B.t_full + acc), (k >> 1) & 1, abort, p.err)) break;
-    float sc = 1.f;
-    if constexpr (PREC == MELT_FP8E4M3) {
-      if (!warp_wait(sbase + p.off_bar + 8 * (B.sc_full + (k % kScaleRing)), (k / kScaleRing) & 1,
-                     abort, p.err))
-        break;
-      sc = scales[(k % kScaleRing) * kF + row];
-    }
     tc_fence_after();
     const bool valid = row < td.n_frames;
     const uint32_t t0 = tmem_base + ((uint32_t)(32 * warp) << 16) + acc * p.acc_stride;
@@ -704,7 +551,7 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
           if (cc < nch) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-              const float r = re[g][e] * sc, i = im[g][e] * sc;
+              const float r = re[g][e], i = im[g][e];
               re[g][e] = __logf(fmaf(r, r, fmaf(i, i, p.eps)));
             }
             if (valid) {
@@ -732,7 +579,7 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
         tmem_ld_wait(re, im);
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          const float r = re[e] * sc, i = im[e] * sc;
+          const float r = re[e], i = im[e];
           lm[16 * c + e] = (16 * c + e < p.M) ? __logf(fmaf(r, r, i * i) + p.eps) : 0.f;
         }
       }
@@ -781,7 +628,6 @@ __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_const
       mbar_init(bar(B.t_full + i), 1);
       mbar_init(bar(B.t_empty + i), kEpiWarps);
     }
-    for (int i = 0; i < kScaleRing; ++i) mbar_init(bar(B.sc_full + i), kCvtWarps);
     mbar_init(bar(B.drain), 1);
     *abort = 0;
     fence_mbar_init();
@@ -791,17 +637,12 @@ __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_const
     uint2* tab = reinterpret_cast<uint2*>(gbase + p.off_tab);
     const uint32_t b_lo0 = ((sbase + p.off_b) >> 4) | (((uint32_t)p.NC * 16 >> 4) << 16);
     const uint32_t bslot16 = p.step_bytes >> 4;
-    if constexpr (PREC == MELT_FP8E4M3) {
-      for (int s = lane; s < p.KS; s += 32)
-        tab[s] = make_uint2((2u * s * p.lbo_a) >> 4, b_lo0 + s * bslot16);
-    } else {
-      // steps in (slice j, 16-column group kk) order, the order of the basis image
-      for (int j = 0, s0 = 0; j < p.J; ++j) {
-        const int steps = (min(p.H, p.N - j * p.H) + 15) / 16;
-        for (int kk = lane; kk < steps; kk += 32)
-          tab[s0 + kk] = make_uint2((2u * kk * p.lbo_a + 16u * j) >> 4, b_lo0 + (s0 + kk) * bslot16);
-        s0 += steps;
-      }
+    // steps in (slice j, 16-column group kk) order, the order of the basis image
+    for (int j = 0, s0 = 0; j < p.J; ++j) {
+      const int steps = (min(p.H, p.N - j * p.H) + 15) / 16;
+      for (int kk = lane; kk < steps; kk += 32)
+        tab[s0 + kk] = make_uint2((2u * kk * p.lbo_a + 16u * j) >> 4, b_lo0 + (s0 + kk) * bslot16);
+      s0 += steps;
     }
   }
   if (warp == kMmaWarp) {
@@ -836,10 +677,7 @@ __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_const
     __syncwarp();
   } else if (warp >= kCvtWarp0) {
     pdl_wait();
-    if constexpr (PREC == MELT_FP8E4M3)
-      role_convert_fp8(p, gbase, sbase, B, abort);
-    else
-      role_convert_bf16<PREC>(p, sbase, B, abort);
+    role_convert_bf16<PREC>(p, sbase, B, abort);
     __syncwarp();
   } else {
     pdl_wait();

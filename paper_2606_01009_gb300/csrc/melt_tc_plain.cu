@@ -8,7 +8,6 @@ KernelFn kernel_for_plain(int prec, int nch) {
   switch (prec) {
     case MELT_BF16: return pick_kernel<MELT_BF16, false>(nch);
     case MELT_BF16X3: return pick_kernel<MELT_BF16X3, false>(nch);
-    case MELT_FP8E4M3: return pick_kernel<MELT_FP8E4M3, false>(nch);
     default: return nullptr;
   }
 }

@@ -193,7 +193,7 @@ static __device__ __forceinline__ uint64_t sdesc_noswz(uint32_t addr, uint32_t l
 }
 
 // Instruction descriptor: dense, FP32 accumulator, K-major A and B, M x N tile.
-// `ab_format`: kind::f16 -> 1 = BF16; kind::f8f6f4 -> 0 = E4M3.
+// `ab_format`: kind::f16 -> 1 = BF16.
 static __host__ __device__ constexpr uint32_t idesc_f32acc(uint32_t ab_format, uint32_t m, uint32_t n) {
   return (1u << 4)                 // D format: F32
          | (ab_format << 7)        // A format
@@ -208,15 +208,6 @@ static __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, 
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-
-static __device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                       uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
@@ -244,6 +235,11 @@ static __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (
       "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
       "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
       : "memory");
+}
+
+// 32 lanes x 32 bit, 4 consecutive columns, all set to `v`: thread i writes lane (base lane + i).
+static __device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%1,%1,%1};" ::"r"(taddr), "r"(v) : "memory");
 }
 
 static __device__ __forceinline__ void tmem_st_wait() {
@@ -400,15 +396,28 @@ static __device__ __forceinline__ void mma_f16_pair(uint32_t d_tmem, uint64_t ad
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
-// 2-SM MMA with e4m3 operands (kind::f8f6f4, K = 32 per instruction); operand
-// split as for mma_f16_pair.
-static __device__ __forceinline__ void mma_f8_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                                   uint32_t idesc, uint32_t accumulate) {
+// 2-SM block-scaled MMA with e4m3 operands (kind::mxf8f6f4, K = 32 per
+// instruction, one UE8M0 scale per row of A and of B for the instruction's
+// K block): D += (A 2^sa) (B 2^sb)^T.  `sfa` / `sfb` are the TMEM addresses of
+// the scale columns (row r's scale in lane r, column r / 32, byte selected
+// by the instruction descriptor's scale-factor ids); operands split between
+// the CTAs as for mma_f16_pair.
+static __device__ __forceinline__ void mma_f8_pair_bs(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                                      uint32_t idesc, uint32_t sfa, uint32_t sfb,
+                                                      uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+      "setp.ne.b32 p, %6, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%4], [%5], p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate));
+}
+
+// Instruction descriptor of the block-scaled e4m3 MMA: E4M3 A and B,
+// K-major, UE8M0 scales, M x N tile; scale-factor ids 0 (OR in a_sf_id << 29).
+static __host__ __device__ constexpr uint32_t idesc_mxf8(uint32_t m, uint32_t n) {
+  return ((n >> 3) << 17)        // N / 8
+         | (1u << 23)            // scale type UE8M0
+         | ((m >> 4) << 24);     // M / 16
 }
 
 // Same 2-SM MMA with the A operand in TMEM (each CTA's 128 rows in its own
