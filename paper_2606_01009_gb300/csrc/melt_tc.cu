@@ -195,7 +195,9 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
   const uint32_t span_bytes = row_bytes * p.zrows;
   int nchunk = (int)((span_bytes + 16383) / 16384);
   int ch = (p.zrows + nchunk - 1) / nchunk;
-  const int max_rows = kPQuads * kPCvtThreads * 4 / p.H;
+  // (BF16: one converter pass covers <= kPQuads quads per thread; FP8: at
+  // most two sets of four rows per warp)
+  const int max_rows = fp8 ? kF8MaxRows : kPQuads * kPCvtThreads * 4 / p.H;
   if (ch > max_rows) ch = std::max(1, max_rows);
   p.CH = ch;
   p.NCHUNK = (p.zrows + ch - 1) / ch;

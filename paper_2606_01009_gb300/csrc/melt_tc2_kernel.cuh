@@ -486,32 +486,145 @@ static __device__ void pair_convert(const TcParams& p, const PairCtx& c, const P
 // row.  Returns the code e + 127 (0..247).
 static __device__ __forceinline__ uint32_t fp8_row_code(uint32_t bits) {
   const int ef = (int)(bits >> 23);
-  if (ef == 0) return 0u;
   const int e = max(-127, ef - 127 - 8 + ((bits & 0x7FFFFFu) > 0x600000u ? 1 : 0));
-  return (uint32_t)(e + 127);
+  return ef == 0 ? 0u : (uint32_t)(e + 127);
+}
+
+// Shared-memory stores under a predicate, without a branch.
+static __device__ __forceinline__ void sts32_if(uint32_t addr, uint32_t v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %2, 0;\n\t"
+      "@p st.shared.b32 [%0], %1;\n\t}" ::"r"(addr),
+      "r"(v), "r"((uint32_t)pred)
+      : "memory");
+}
+
+static __device__ __forceinline__ void sts8_if(uint32_t addr, uint32_t v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %2, 0;\n\t"
+      "@p st.shared.u8 [%0], %1;\n\t}" ::"r"(addr),
+      "r"(v), "r"((uint32_t)pred)
+      : "memory");
+}
+
+// The samples of a quad at or past the clip end set to zero, by selects (s =
+// clip sample index of x.x).
+static __device__ __forceinline__ float4 clip_quad_sel(float4 x, int s, int nsamp) {
+  x.x = s < nsamp ? x.x : 0.f;
+  x.y = s + 1 < nsamp ? x.y : 0.f;
+  x.z = s + 2 < nsamp ? x.z : 0.f;
+  x.w = s + 3 < nsamp ? x.w : 0.f;
+  return x;
 }
 
 // FP8 e4m3 converter: staged FP32 chunks -> polyphase Z rows of e4m3 with a
 // power-of-two scale per row, and the rows' scale codes in TMEM.
 //
-// A warp takes whole rows of a chunk (rows cw, cw + 4, ... of the chunk, two
-// at a time): lane l holds quads l and l + 32 of the row (H <= 256), the warp
-// reduces max |x| over them (float bits of non-negative values order like
-// unsigned ints), derives the row's exponent e, multiplies by 2^-e (exact)
-// and converts with saturating round-to-nearest-even.  Z element (u, r) sits
-// at (r / 16) lbo_a + 16 u + r % 16, so a quad of row u is 4 bytes at core
-// column q / 4, byte 4 (q % 4): lanes of a warp hit 32 different banks
-// (lbo_a = 16 mod 128).  The code of row u goes to shared memory; after the
-// tile's last chunk each warp writes, for the 32 TMEM lanes of its quarter
-// (frame t), one 32-bit word per group of four slices: byte j is the code of
-// Z row t + 4g + j, the scale of A row t in slice 4g + j.  The word is
-// repeated over the group's four columns (the MMA reads row t's scale in
-// lane t, column t / 32 of the group).
+// Eight lanes share a Z row: lane l8 of a group holds quads l8, l8 + 8, ...
+// of the row (H <= 256: at most 8 each), so the row's max |x| is a local max
+// and three butterfly shuffles inside the group.  A warp takes four rows at a
+// time and both of its row sets of a chunk (rows 4 w + g and 4 w + g + 16,
+// chunks of at most 32 rows) at once: all of a chunk's loads are in flight
+// together and the two reductions overlap.  The row's exponent is the least
+// e with amax 2^-e <= 448; its samples are multiplied by 2^-e (exact) and
+// converted with saturating round-to-nearest-even.  Z element (u, r) sits at
+// (r / 16) lbo_a + 16 u + r % 16, so quad q of row u is 4 bytes at core
+// column q / 4, byte 4 (q % 4).  The row's scale code goes to shared memory;
+// after the tile's last chunk each warp writes, for the 32 TMEM lanes of its
+// quarter (frame t), one 32-bit word per group of four slices: byte j is the
+// code of Z row t + 4g + j, the scale of A row t in slice 4g + j, repeated
+// over the group's four columns (the MMA reads row t's scale in lane t,
+// column t / 32 of the group).
+constexpr int kF8LanesPerRow = 8;
+constexpr int kF8MaxQuads = 8;   // quads per lane per row: H <= 4 * 8 * 8 = 256
+constexpr int kF8MaxRows = 32;   // rows per staged chunk: two sets of 4 rows per warp
+
+// One staged chunk of the FP8 converter (rows [r0, r0 + rows) of the tile's
+// Z rows): NQ = quads per lane per row (ceil(H / 32)), a compile-time count
+// so that every load is issued unconditionally and all are in flight at once.
+template <int NQ>
+static __device__ __forceinline__ void fp8_convert_chunk(const TcParams& p, uint32_t st, uint32_t zaddr,
+                                                         uint32_t codes_s, int r0, int rows, int nsamp, int cw,
+                                                         int g, int l8) {
+  const int h4 = p.H >> 2;
+  const int s_base = r0 * p.H;
+  const bool tail = s_base + rows * p.H > nsamp;
+  // loads at clamped (always valid) addresses; quads outside the chunk's rows
+  // or past H are zeroed by selects after
+  float4 x[2][NQ];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int u = min(4 * cw + g + 16 * h, rows - 1);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                   : "=f"(x[h][q].x), "=f"(x[h][q].y), "=f"(x[h][q].z), "=f"(x[h][q].w)
+                   : "r"(st + 16u * (uint32_t)(u * h4 + min(kF8LanesPerRow * q + l8, h4 - 1))));
+  }
+  float m[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int u = 4 * cw + g + 16 * h;
+    m[h] = 0.f;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int j = kF8LanesPerRow * q + l8;
+      const bool live = u < rows && j < h4;
+      float4 v = x[h][q];
+      if (tail) v = clip_quad_sel(v, s_base + u * p.H + 4 * j, nsamp);
+      v.x = live ? v.x : 0.f;
+      v.y = live ? v.y : 0.f;
+      v.z = live ? v.z : 0.f;
+      v.w = live ? v.w : 0.f;
+      x[h][q] = v;
+      m[h] = fmaxf(m[h], fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < kF8LanesPerRow; o <<= 1)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) m[h] = fmaxf(m[h], __shfl_xor_sync(0xffffffffu, m[h], o));
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int u = 4 * cw + g + 16 * h;
+    const bool row_live = u < rows;
+    const uint32_t code = fp8_row_code(__float_as_uint(m[h]));
+    const float inv = __uint_as_float((254u - code) << 23);  // 2^-e, e = code - 127
+    sts8_if(codes_s + (uint32_t)(r0 + u), code, row_live && l8 == 0);
+    const uint32_t zrow = zaddr + 16u * (uint32_t)(r0 + u);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int j = kF8LanesPerRow * q + l8;
+      const uint32_t w = pack_e4m3x4(x[h][q].x * inv, x[h][q].y * inv, x[h][q].z * inv, x[h][q].w * inv);
+      sts32_if(zrow + (uint32_t)(j >> 2) * p.lbo_a + 4u * (uint32_t)(j & 3), w, row_live && j < h4);
+    }
+  }
+}
+
+static __device__ __forceinline__ void fp8_convert_chunk_any(const TcParams& p, int nqr, uint32_t st, uint32_t zaddr,
+                                                             uint32_t codes_s, int r0, int rows, int nsamp, int cw,
+                                                             int g, int l8) {
+  switch (nqr) {
+    case 1: fp8_convert_chunk<1>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    case 2: fp8_convert_chunk<2>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    case 3: fp8_convert_chunk<3>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    case 4: fp8_convert_chunk<4>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    case 5: fp8_convert_chunk<5>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    case 6: fp8_convert_chunk<6>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    case 7: fp8_convert_chunk<7>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    default: fp8_convert_chunk<8>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+  }
+}
+
 static __device__ void pair_convert_fp8(const TcParams& p, uint8_t* gbase, const PairCtx& c,
                                         const PairBars& B, int cvt0, uint32_t tmem_base) {
   const int cw = (int)(threadIdx.x >> 5) - cvt0, lane = threadIdx.x & 31;
   const int quarter = (threadIdx.x >> 5) & 3;  // the TMEM lanes this warp may access
-  const int h4 = p.H >> 2;                     // quads per Z row (<= 64)
+  const int g = lane >> 3, l8 = lane & 7;
+  const int h4 = p.H >> 2;                     // quads per Z row
+  const int nqr = (h4 + kF8LanesPerRow - 1) / kF8LanesPerRow;  // quads per lane per row
   const uint32_t st0 = c.sbase + p.off_st;
   uint8_t* codes_all = gbase + p.off_codes;
   // zero both A buffers once: bytes past H in a row's last core columns stay zero
@@ -523,82 +636,43 @@ static __device__ void pair_convert_fp8(const TcParams& p, uint8_t* gbase, const
   for (int k = 0;; ++k) {
     bool okq = true;
     const int qp = k == 0 ? c.cluster : pair_next_warp(p, c, B, k, okq);
-    // every converter warp reads the same entry; a timeout in any of them stops all
+    // every converter warp reads the same entry and takes every named barrier
+    // below, or none: a timeout in any of them stops all of them here
     if (!named_barrier_and(1, kPCvtThreads, okq) || qp >= p.n_pairs) break;
     const int zb = p.ZB == 2 ? (k & 1) : 0;
     bool ok = warp_wait_cl(pbar(p, c, B.z_empty + zb), ((p.ZB == 2 ? (k >> 1) : k) & 1) ^ 1, c.abort, p.err);
-    if (!named_barrier_and(1, kPCvtThreads, ok)) break;
     const TileDesc td = pair_tile(p, c, qp);
     const int nsamp = td.n_samples;
     const uint32_t zaddr = c.sbase + p.off_a + zb * p.abuf_bytes;
     uint8_t* codes = codes_all + zb * p.codes_stride;
-    if (td.n_frames > 0) {
-      for (int ch = 0; ch < p.NCHUNK; ++ch) {
-        ok = warp_wait(pbar(p, c, B.s_full + slot), sphase, c.abort, p.err);
-        if (!named_barrier_and(1, kPCvtThreads, ok)) break;
-        const int rows = min(p.CH, p.zrows - ch * p.CH);
-        const uint32_t st = st0 + slot * p.st_bytes;
-        const int s_base = ch * p.CH * p.H;
-        const bool tail = s_base + rows * p.H > nsamp;
-        for (int rl0 = cw; rl0 < rows; rl0 += 2 * kPCvtWarps) {
-          float4 x[2][2];
-#pragma unroll
-          for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int rl = rl0 + kPCvtWarps * r, j = lane + 32 * h;
-              const bool live = rl < rows && j < h4;
-              x[r][h] = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (live) {
-                asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                             : "=f"(x[r][h].x), "=f"(x[r][h].y), "=f"(x[r][h].z), "=f"(x[r][h].w)
-                             : "r"(st + 16u * (uint32_t)(rl * h4 + j)));
-                if (tail) clip_quad(x[r][h], s_base + rl * p.H + 4 * j, nsamp);
-              }
-            }
-#pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            const int rl = rl0 + kPCvtWarps * r;
-            float m = 0.f;
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-              m = fmaxf(m, fmaxf(fmaxf(fabsf(x[r][h].x), fabsf(x[r][h].y)), fmaxf(fabsf(x[r][h].z), fabsf(x[r][h].w))));
-            const uint32_t code = fp8_row_code(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
-            const float inv = __uint_as_float((254u - code) << 23);  // 2^-e, e = code - 127
-            if (rl < rows) {
-              const int u = ch * p.CH + rl;
-              if (lane == 0) codes[u] = (uint8_t)code;
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int j = lane + 32 * h;
-                if (j < h4) {
-                  const uint32_t w = pack_e4m3x4(x[r][h].x * inv, x[r][h].y * inv, x[r][h].z * inv, x[r][h].w * inv);
-                  asm volatile("st.shared.b32 [%0], %1;" ::"r"(zaddr + (uint32_t)(j >> 2) * p.lbo_a + 16u * (uint32_t)u +
-                                                               4u * (uint32_t)(j & 3)),
-                               "r"(w));
-                }
-              }
-            }
-          }
-        }
-        warp_arrive(pbar(p, c, B.s_empty + slot));
-        if (++slot == p.NS) {
-          slot = 0;
-          sphase ^= 1;
-        }
+    const uint32_t codes_s = smem_u32(codes);
+    for (int ch = 0; ok && td.n_frames > 0 && ch < p.NCHUNK; ++ch) {
+      if (!warp_wait(pbar(p, c, B.s_full + slot), sphase, c.abort, p.err)) {
+        ok = false;
+        break;
       }
-      if (!ok) break;
-      // every row's code is in shared memory: the scale words of this warp's TMEM lanes
-      named_barrier(1, kPCvtThreads);
+      const int r0 = ch * p.CH;
+      fp8_convert_chunk_any(p, nqr, st0 + slot * p.st_bytes, zaddr, codes_s, r0, min(p.CH, p.zrows - r0), nsamp,
+                            cw, g, l8);
+      warp_arrive(pbar(p, c, B.s_empty + slot));
+      if (++slot == p.NS) {
+        slot = 0;
+        sphase ^= 1;
+      }
+    }
+    // all leave together when a wait gave up; otherwise every row's code is in
+    // shared memory: the scale words of this warp's TMEM lanes
+    if (!named_barrier_and(1, kPCvtThreads, ok)) break;
+    if (td.n_frames > 0) {
       const int t = 32 * quarter + lane;
-      for (int g = 0; g < p.sfg; ++g) {
+      for (int gg = 0; gg < p.sfg; ++gg) {
         uint32_t w = 0u;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int jj = 4 * g + j;
+          const int jj = 4 * gg + j;
           w |= (jj < p.J ? (uint32_t)codes[t + jj] : 0x7Fu) << (8 * j);
         }
-        tmem_st4(tmem_base + ((uint32_t)(32 * quarter) << 16) + p.sf_col + (uint32_t)(4 * (p.sfg * zb + g)), w);
+        tmem_st4(tmem_base + ((uint32_t)(32 * quarter) << 16) + p.sf_col + (uint32_t)(4 * (p.sfg * zb + gg)), w);
       }
       tmem_st_wait();
     }
