@@ -190,48 +190,58 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
     p.idesc1 = idesc_f32acc(1u, 2 * kF, (uint32_t)p.Hd);
     p.idesc2 = idesc_f32acc(1u, 2 * kF, (uint32_t)p.MP);
   }
-  // staging chunks: whole Z rows, <= 16 KB, <= what one converter pass covers
+  // staging chunks: whole Z rows.  BF16: <= 16 KB and <= what one converter
+  // pass covers (kPQuads quads per thread); FP8: up to kF8MaxRows rows (all
+  // row slots of the converter warps) and 20 KB, fewer where that does not fit
   const uint32_t row_bytes = (uint32_t)p.H * 4;
   const uint32_t span_bytes = row_bytes * p.zrows;
-  int nchunk = (int)((span_bytes + 16383) / 16384);
-  int ch = (p.zrows + nchunk - 1) / nchunk;
-  // (BF16: one converter pass covers <= kPQuads quads per thread; FP8: at
-  // most two sets of four rows per warp)
-  const int max_rows = fp8 ? kF8MaxRows : kPQuads * kPCvtThreads * 4 / p.H;
-  if (ch > max_rows) ch = std::max(1, max_rows);
-  p.CH = ch;
-  p.NCHUNK = (p.zrows + ch - 1) / ch;
-  p.st_bytes = row_bytes * ch;
+  int chs[3] = {0, 0, 0}, nch_c = 0;
+  if (fp8) {
+    for (int c8 = std::max(1, std::min(kF8MaxRows, (int)(20480u / row_bytes))); c8 >= 1 && nch_c < 3; c8 /= 2)
+      chs[nch_c++] = c8;
+  } else {
+    const int nchunk = (int)((span_bytes + 16383) / 16384);
+    int ch = (p.zrows + nchunk - 1) / nchunk;
+    const int max_rows = kPQuads * kPCvtThreads * 4 / p.H;
+    if (ch > max_rows) ch = std::max(1, max_rows);
+    chs[nch_c++] = ch;
+  }
   p.codes_stride = fp8 ? align_up((uint32_t)p.zrows + 3, 16) : 0u;
-  for (int ns = 8; ns >= 2; --ns) {
-    const PairBars B(ns, p.ZB, p.KS);
-    uint32_t off = 0;
-    p.off_a = off;
-    off += align_up(p.abuf_bytes * p.ZB, 128);
-    p.off_st = off;
-    off += align_up(p.st_bytes * ns, 128);
-    p.off_b = off;
-    off += align_up(p.step_bytes * p.KS, 128);
-    p.off_mlp = off;
-    off += p.Hd > 0 ? align_up(p.mlp_half, 128) : 0u;
-    p.off_bar = off;
-    off += align_up(8 * B.total, 128);
-    p.off_tab = off;
-    off += align_up(8 * p.KS, 128);
-    p.off_misc = off;
-    off += 128;
-    p.off_codes = off;  // FP8: the scale code of every Z row of the tile, per A buffer
-    off += fp8 ? align_up(p.codes_stride * (uint32_t)p.ZB, 128) : 0u;
-    p.off_dct = off;
-    off += align_up(4 * n_mfcc * p.MP, 128);
-    if (off + 128 > kSmemLimit) continue;
-    p.NS = ns;
-    p.smem_total = off + 128;
-    p.tmem_cols = fp8 ? 512 : p.NC <= 32 ? 64 : p.NC <= 64 ? 128 : p.NC <= 128 ? 256 : 512;
-    p.acc_stride = p.tmem_cols / 2;
-    p.idesc = fp8 ? idesc_mxf8(2 * kF, p.NC) : idesc_f32acc(1u, 2 * kF, p.NC);  // M = 256 over the pair
-    p.desc_hi = (128u >> 4) | (1u << 14);
-    return true;
+  for (int ci = 0; ci < nch_c; ++ci) {
+    const int ch = chs[ci];
+    p.CH = ch;
+    p.NCHUNK = (p.zrows + ch - 1) / ch;
+    p.st_bytes = row_bytes * ch;
+    for (int ns = 8; ns >= 2; --ns) {
+      const PairBars B(ns, p.ZB, p.KS);
+      uint32_t off = 0;
+      p.off_a = off;
+      off += align_up(p.abuf_bytes * p.ZB, 128);
+      p.off_st = off;
+      off += align_up(p.st_bytes * ns, 128);
+      p.off_b = off;
+      off += align_up(p.step_bytes * p.KS, 128);
+      p.off_mlp = off;
+      off += p.Hd > 0 ? align_up(p.mlp_half, 128) : 0u;
+      p.off_bar = off;
+      off += align_up(8 * B.total, 128);
+      p.off_tab = off;
+      off += align_up(8 * p.KS, 128);
+      p.off_misc = off;
+      off += 128;
+      p.off_codes = off;  // FP8: the scale code of every Z row of the tile, per A buffer
+      off += fp8 ? align_up(p.codes_stride * (uint32_t)p.ZB, 128) : 0u;
+      p.off_dct = off;
+      off += align_up(4 * n_mfcc * p.MP, 128);
+      if (off + 128 > kSmemLimit) continue;
+      p.NS = ns;
+      p.smem_total = off + 128;
+      p.tmem_cols = fp8 ? 512 : p.NC <= 32 ? 64 : p.NC <= 64 ? 128 : p.NC <= 128 ? 256 : 512;
+      p.acc_stride = p.tmem_cols / 2;
+      p.idesc = fp8 ? idesc_mxf8(2 * kF, p.NC) : idesc_f32acc(1u, 2 * kF, p.NC);  // M = 256 over the pair
+      p.desc_hi = (128u >> 4) | (1u << 14);
+      return true;
+    }
   }
   return false;
 }
@@ -517,7 +527,7 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
   attr[1].val.clusterDim.x = 2;
   attr[1].val.clusterDim.y = 1;
   attr[1].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(pair_threads(fused), 1, 1);
+  cfg.blockDim = dim3(pair_threads(fused, tb->precision, L.n_mfcc > 0, p.MP / 16), 1, 1);
   cfg.numAttrs = 2;
   TcBasis* mtb = const_cast<TcBasis*>(tb);
   if (mtb->pair_clusters < 0 || mtb->pair_smem != smem) {

@@ -58,7 +58,16 @@ namespace tc {
 constexpr int kPCvtWarps = 4;
 constexpr int kPCvtThreads = 32 * kPCvtWarps;  // 128
 __host__ __device__ constexpr int pair_epi_warps(bool mlp) { return mlp ? 8 : 4; }
-__host__ __device__ constexpr int pair_threads(bool mlp) { return 32 * (pair_epi_warps(mlp) + 3 + kPCvtWarps); }
+// Converter warps: 4 (BF16: each sample converted once, short chains), 8 for
+// FP8, whose per-row max makes each chunk one dependent chain per row set
+// (twice the warps, half the chain), unless the MFCC epilogue of M > 80 needs
+// more registers than 480 threads leave (136 a thread).
+__host__ __device__ constexpr int pair_cvt_warps(int prec, bool mfcc, int nch) {
+  return prec == MELT_FP8E4M3 && !(mfcc && nch > 5) ? 8 : 4;
+}
+__host__ __device__ constexpr int pair_threads(bool mlp, int prec = MELT_BF16, bool mfcc = false, int nch = 1) {
+  return 32 * (pair_epi_warps(mlp) + 3 + pair_cvt_warps(prec, mfcc, nch));
+}
 constexpr int kPQuads = 8;  // float4s per converter thread per staged chunk (<= 16 KB)
 constexpr uint32_t kSfOne = 0x7F7F7F7Fu;    // four UE8M0 codes of 2^0
 constexpr uint32_t kSfBasis = 0x77777777u;  // four UE8M0 codes of 2^-8 (the e4m3 basis holds W 2^8)
@@ -544,29 +553,30 @@ constexpr int kF8MaxRows = 32;   // rows per staged chunk: two sets of 4 rows pe
 // One staged chunk of the FP8 converter (rows [r0, r0 + rows) of the tile's
 // Z rows): NQ = quads per lane per row (ceil(H / 32)), a compile-time count
 // so that every load is issued unconditionally and all are in flight at once.
-template <int NQ>
+template <int NQ, int CW>
 static __device__ __forceinline__ void fp8_convert_chunk(const TcParams& p, uint32_t st, uint32_t zaddr,
                                                          uint32_t codes_s, int r0, int rows, int nsamp, int cw,
                                                          int g, int l8) {
+  constexpr int NS = kF8MaxRows / (4 * CW);  // row sets per warp: rows 4 cw + g + 4 CW h
   const int h4 = p.H >> 2;
   const int s_base = r0 * p.H;
   const bool tail = s_base + rows * p.H > nsamp;
   // loads at clamped (always valid) addresses; quads outside the chunk's rows
   // or past H are zeroed by selects after
-  float4 x[2][NQ];
+  float4 x[NS][NQ];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int u = min(4 * cw + g + 16 * h, rows - 1);
+  for (int h = 0; h < NS; ++h) {
+    const int u = min(4 * cw + g + 4 * CW * h, rows - 1);
 #pragma unroll
     for (int q = 0; q < NQ; ++q)
       asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                    : "=f"(x[h][q].x), "=f"(x[h][q].y), "=f"(x[h][q].z), "=f"(x[h][q].w)
                    : "r"(st + 16u * (uint32_t)(u * h4 + min(kF8LanesPerRow * q + l8, h4 - 1))));
   }
-  float m[2];
+  float m[NS];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int u = 4 * cw + g + 16 * h;
+  for (int h = 0; h < NS; ++h) {
+    const int u = 4 * cw + g + 4 * CW * h;
     m[h] = 0.f;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -585,10 +595,10 @@ static __device__ __forceinline__ void fp8_convert_chunk(const TcParams& p, uint
 #pragma unroll
   for (int o = 1; o < kF8LanesPerRow; o <<= 1)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) m[h] = fmaxf(m[h], __shfl_xor_sync(0xffffffffu, m[h], o));
+    for (int h = 0; h < NS; ++h) m[h] = fmaxf(m[h], __shfl_xor_sync(0xffffffffu, m[h], o));
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int u = 4 * cw + g + 16 * h;
+  for (int h = 0; h < NS; ++h) {
+    const int u = 4 * cw + g + 4 * CW * h;
     const bool row_live = u < rows;
     const uint32_t code = fp8_row_code(__float_as_uint(m[h]));
     const float inv = __uint_as_float((254u - code) << 23);  // 2^-e, e = code - 127
@@ -603,23 +613,26 @@ static __device__ __forceinline__ void fp8_convert_chunk(const TcParams& p, uint
   }
 }
 
+template <int CW>
 static __device__ __forceinline__ void fp8_convert_chunk_any(const TcParams& p, int nqr, uint32_t st, uint32_t zaddr,
                                                              uint32_t codes_s, int r0, int rows, int nsamp, int cw,
                                                              int g, int l8) {
   switch (nqr) {
-    case 1: fp8_convert_chunk<1>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
-    case 2: fp8_convert_chunk<2>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
-    case 3: fp8_convert_chunk<3>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
-    case 4: fp8_convert_chunk<4>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
-    case 5: fp8_convert_chunk<5>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
-    case 6: fp8_convert_chunk<6>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
-    case 7: fp8_convert_chunk<7>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
-    default: fp8_convert_chunk<8>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    case 1: fp8_convert_chunk<1, CW>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    case 2: fp8_convert_chunk<2, CW>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    case 3: fp8_convert_chunk<3, CW>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    case 4: fp8_convert_chunk<4, CW>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    case 5: fp8_convert_chunk<5, CW>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    case 6: fp8_convert_chunk<6, CW>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    case 7: fp8_convert_chunk<7, CW>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
+    default: fp8_convert_chunk<8, CW>(p, st, zaddr, codes_s, r0, rows, nsamp, cw, g, l8); break;
   }
 }
 
+template <int CW>
 static __device__ void pair_convert_fp8(const TcParams& p, uint8_t* gbase, const PairCtx& c,
                                         const PairBars& B, int cvt0, uint32_t tmem_base) {
+  constexpr int kThr = 32 * CW;
   const int cw = (int)(threadIdx.x >> 5) - cvt0, lane = threadIdx.x & 31;
   const int quarter = (threadIdx.x >> 5) & 3;  // the TMEM lanes this warp may access
   const int g = lane >> 3, l8 = lane & 7;
@@ -628,7 +641,7 @@ static __device__ void pair_convert_fp8(const TcParams& p, uint8_t* gbase, const
   const uint32_t st0 = c.sbase + p.off_st;
   uint8_t* codes_all = gbase + p.off_codes;
   // zero both A buffers once: bytes past H in a row's last core columns stay zero
-  for (uint32_t o = 16u * (uint32_t)(threadIdx.x - 32 * cvt0); o < p.abuf_bytes * p.ZB; o += 16u * kPCvtThreads)
+  for (uint32_t o = 16u * (uint32_t)(threadIdx.x - 32 * cvt0); o < p.abuf_bytes * p.ZB; o += 16u * kThr)
     sts128(c.sbase + p.off_a + o, make_uint4(0u, 0u, 0u, 0u));
   fence_proxy_async();
   int slot = 0;
@@ -638,7 +651,7 @@ static __device__ void pair_convert_fp8(const TcParams& p, uint8_t* gbase, const
     const int qp = k == 0 ? c.cluster : pair_next_warp(p, c, B, k, okq);
     // every converter warp reads the same entry and takes every named barrier
     // below, or none: a timeout in any of them stops all of them here
-    if (!named_barrier_and(1, kPCvtThreads, okq) || qp >= p.n_pairs) break;
+    if (!named_barrier_and(1, kThr, okq) || qp >= p.n_pairs) break;
     const int zb = p.ZB == 2 ? (k & 1) : 0;
     bool ok = warp_wait_cl(pbar(p, c, B.z_empty + zb), ((p.ZB == 2 ? (k >> 1) : k) & 1) ^ 1, c.abort, p.err);
     const TileDesc td = pair_tile(p, c, qp);
@@ -652,8 +665,8 @@ static __device__ void pair_convert_fp8(const TcParams& p, uint8_t* gbase, const
         break;
       }
       const int r0 = ch * p.CH;
-      fp8_convert_chunk_any(p, nqr, st0 + slot * p.st_bytes, zaddr, codes_s, r0, min(p.CH, p.zrows - r0), nsamp,
-                            cw, g, l8);
+      fp8_convert_chunk_any<CW>(p, nqr, st0 + slot * p.st_bytes, zaddr, codes_s, r0, min(p.CH, p.zrows - r0),
+                                nsamp, cw, g, l8);
       warp_arrive(pbar(p, c, B.s_empty + slot));
       if (++slot == p.NS) {
         slot = 0;
@@ -662,8 +675,8 @@ static __device__ void pair_convert_fp8(const TcParams& p, uint8_t* gbase, const
     }
     // all leave together when a wait gave up; otherwise every row's code is in
     // shared memory: the scale words of this warp's TMEM lanes
-    if (!named_barrier_and(1, kPCvtThreads, ok)) break;
-    if (td.n_frames > 0) {
+    if (!named_barrier_and(1, kThr, ok)) break;
+    if (td.n_frames > 0 && cw < 4) {  // one warp per TMEM lane quarter
       const int t = 32 * quarter + lane;
       for (int gg = 0; gg < p.sfg; ++gg) {
         uint32_t w = 0u;
@@ -926,9 +939,10 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
 }
 
 template <int NCH, bool MFCC, bool MLP, int PREC = MELT_BF16>
-__global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH), 1) melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
   constexpr int EPW = pair_epi_warps(MLP);
   constexpr int kPMmaWarp = EPW, kPBWarp = EPW + 1, kPProdWarp = EPW + 2, kPCvtWarp0 = EPW + 3;
+  constexpr int CW = pair_cvt_warps(PREC, MFCC, NCH);
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 127u) & ~127u;
@@ -947,10 +961,10 @@ __global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(cons
     auto bar = [&](int i) { return sbase + p.off_bar + 8 * i; };
     for (int i = 0; i < p.NS; ++i) {
       mbar_init(bar(B.s_full + i), 1);
-      mbar_init(bar(B.s_empty + i), kPCvtWarps);
+      mbar_init(bar(B.s_empty + i), CW);
     }
     for (int i = 0; i < p.ZB; ++i) {
-      mbar_init(bar(B.z_full + i), 2 * kPCvtWarps);  // converters of both CTAs (even CTA's copy is used)
+      mbar_init(bar(B.z_full + i), 2 * CW);  // converters of both CTAs (even CTA's copy is used)
       mbar_init(bar(B.z_empty + i), 1);
     }
     mbar_init(bar(B.b_full), 1);
@@ -1043,7 +1057,7 @@ __global__ void __launch_bounds__(pair_threads(MLP), 1) melt_tc_pair_kernel(cons
   } else if (warp >= kPCvtWarp0) {
     pdl_wait();
     if constexpr (PREC == MELT_FP8E4M3)
-      pair_convert_fp8(p, gbase, c, B, kPCvtWarp0, tmem_base);
+      pair_convert_fp8<CW>(p, gbase, c, B, kPCvtWarp0, tmem_base);
     else
       pair_convert(p, c, B, kPCvtWarp0);
     __syncwarp();

@@ -19,8 +19,10 @@ LOGF_REL = 4 * 2.0 ** -23  # ... and <= 3 ulp of the result elsewhere
 # sweep (1,021,952 frames, levels -60..0 dBFS), rounded up by 10-30 %: their
 # kernels differ from that oracle only by FP32 accumulation, which the
 # element-wise parity tests bound separately.  FP32 is held to 1e-3 dB within
-# 60 dB; deeper bins carry the FP32 rounding of the basis itself (up to
-# 4.1e-3 dB at 100 dB over the sweep with exact sums).
+# 60 dB of the frame maximum; its figures are the GPU's own over 32 clips of
+# the sweep (FP32 accumulation dominates: 3.3e-6 dB RMS within 10 dB), and
+# deeper bins also carry the FP32 rounding of the basis itself (up to
+# 4.1e-3 dB at 100 dB over the whole sweep with exact sums).
 FORM_TOL_DB = {
     "bf16": {"within_10dB": {"max": 0.5, "rms": 0.006}, "within_30dB": {"max": 6.0, "rms": 0.035},
              "within_60dB": {"max": 30.0, "rms": 0.32}, "within_100dB": {"max": 50.0, "rms": 0.6},
@@ -31,9 +33,9 @@ FORM_TOL_DB = {
     "fp8": {"within_10dB": {"max": 9.0, "rms": 0.09}, "within_30dB": {"max": 55.0, "rms": 0.5},
             "within_60dB": {"max": 70.0, "rms": 3.0}, "within_100dB": {"max": 70.0, "rms": 3.9},
             "all": {"max": 80.0, "rms": 3.9}},
-    "fp32": {"within_10dB": {"max": 1e-4, "rms": 1e-6}, "within_30dB": {"max": 2e-4, "rms": 2e-6},
-             "within_60dB": {"max": 1e-3, "rms": 1e-5}, "within_100dB": {"max": 8e-3, "rms": 2e-5},
-             "all": {"max": 2.5e-2, "rms": 2e-5}},
+    "fp32": {"within_10dB": {"max": 1e-4, "rms": 1e-5}, "within_30dB": {"max": 2e-4, "rms": 1e-5},
+             "within_60dB": {"max": 1e-3, "rms": 2e-5}, "within_100dB": {"max": 8e-3, "rms": 4e-5},
+             "all": {"max": 2.5e-2, "rms": 4e-5}},
 }
 TOL_DEPTHS = (10.0, 30.0, 60.0, 100.0)
 
