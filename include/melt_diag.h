@@ -26,6 +26,21 @@ extern "C" {
 melt_status melt_diag_wait_timeout(melt_basis* basis, void* stream);
 
 /*
+ * melt_diag_gelu - evaluates, on n device floats h, the GELU that the CTA-pair
+ *   kernel's fused correction epilogue applies to the hidden layer: GELU(h) =
+ *   h Phi(h) (the exact-erf form the model is trained with), computed as
+ *   max(h, 0) - |h| phi(|h|) R(|h|) with a polynomial R for the Mills ratio of
+ *   the normal tail.  Stated accuracy against the exact function: relative
+ *   error <= 7e-5 for |h| <= 5, absolute error <= 5e-6 everywhere.  The paper
+ *   has no counterpart (it evaluates no correction layer); this entry point
+ *   lets a test check that bound.
+ *   h, y    device float[n] (may be the same array)
+ *   stream  cudaStream_t as void*; asynchronous
+ *   Errors: MELT_ERR_ARG for n < 0 or NULL pointers, MELT_ERR_CUDA if the launch fails.
+ */
+melt_status melt_diag_gelu(const float* h, float* y, int64_t n, void* stream);
+
+/*
  * melt_diag_alloc_count - number of device allocations (cudaMalloc) and
  *   page-locked host allocations (cudaMallocHost) the library has made in
  *   this process so far, over all devices and threads.  The paper has no

@@ -57,6 +57,7 @@ SIGNATURES = {
     "melt_pad_reflect": (C.c_int, [_VP, _I64P, _I64P, C.c_int, C.c_int, _VP, _I64P, _VP]),
     "melt_diag_wait_timeout": (C.c_int, [_VP, _VP]),
     "melt_diag_alloc_count": (C.c_longlong, []),
+    "melt_diag_gelu": (C.c_int, [_VP, _VP, C.c_int64, _VP]),
     "melt_plan_get": (C.c_int, [_VP, _VP]),
     "melt_plan_set": (C.c_int, [_VP, _VP]),
     "melt_autotune": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP, C.c_int, _VP]),
@@ -229,6 +230,12 @@ def melt_pad_reflect(wave, offsets, lengths, pad, out, out_offsets=None, stream=
 def melt_diag_wait_timeout(basis, stream=None):
     """Run the failure path of the bounded waits: the next melt_sync reports MELT_ERR_TIMEOUT."""
     _check(lib.melt_diag_wait_timeout(basis, _stream_ptr(stream)), "melt_diag_wait_timeout")
+
+
+def melt_diag_gelu(h, y, stream=None):
+    """The fused correction epilogue's GELU on device tensors h -> y (float32)."""
+    _check(lib.melt_diag_gelu(C.c_void_p(h.data_ptr()), C.c_void_p(y.data_ptr()), int(h.numel()), _stream_ptr(stream)),
+           "melt_diag_gelu")
 
 
 def melt_diag_alloc_count() -> int:
