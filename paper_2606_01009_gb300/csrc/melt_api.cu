@@ -15,7 +15,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/melt_diag.h"
+#include "melt_diag.h"
 #include "melt_internal.h"
 #include "melt_tc.h"
 #include "sm100_ptx.cuh"

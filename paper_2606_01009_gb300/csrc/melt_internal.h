@@ -6,7 +6,7 @@
 
 #include <vector>
 
-#include "../../include/melt.h"
+#include "melt.h"
 
 namespace melt {
 

@@ -1,6 +1,6 @@
 // Instantiations of the CTA-pair tensor-core MelT kernel with the correction
 // MLP fused in its epilogue (BF16).
-#include "../../include/melt_diag.h"
+#include "melt_diag.h"
 #include "melt_tc2_kernel.cuh"
 
 namespace melt {
