@@ -106,6 +106,12 @@ def parse():
                     help="also time every other operand form")
     ap.add_argument("--stft", action=argparse.BooleanOptionalAction, default=True,
                     help="also time torch.stft + Mel matmul on the same GPU (context)")
+    ap.add_argument("--configs", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the M = 128 and MFCC variants and the 1024 x 10 s precision sweep")
+    ap.add_argument("--sweeps", action=argparse.BooleanOptionalAction, default=True,
+                    help="also run the batch sweep (4 s clips) and the Mel-count sweep (160 s clip)")
+    ap.add_argument("--energy", action=argparse.BooleanOptionalAction, default=True,
+                    help="also measure J per frame with NVML's total-energy counter")
     return ap.parse_args()
 
 
@@ -350,7 +356,7 @@ def time_form(args, W, precision, steps, warmup, world, want_e2e):
     ms_total, value = whole_job(ms_total, T, steps, world, dev)
     res = {"precision": precision, "T": T, "n_out": n_out, "copies": copies, "steps": steps,
            "ms_total": ms_total, "ms_per_step": ms_total / steps, "launch_ms": launch_ms,
-           "value": value, "clocks": ck, "trials": trial_stats(trial_ms, steps),
+           "value": value, "clocks": ck, "trials": trial_stats(trial_ms, steps), "step": step,
            "out_sample": outs[0], "fe": fe}
 
     if want_e2e:
@@ -472,11 +478,11 @@ def run_melt(args, rank, world):
                          f"({head['copies'] * (W.in_bytes + T * n_out * 4) / 1e6:.0f} MB > 129 MB L2)",
                    "parallelism": f"replicas x{world}"},
         "e2e": head["e2e"],
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * head["trials"]["count"],
         "roofline": roofline(cfg, W, head, peaks, peak_kind),
         "clocks": {k: head["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples")},
         "trials": head["trials"],
-        "energy": energy_estimate(head),
+        "energy": None,
     }
     if args.forms:
         res["forms"] = {}
@@ -490,7 +496,20 @@ def run_melt(args, rank, world):
                                   "roofline_frac": rf["frac"], "bound": rf["bound"],
                                   "achieved": rf["achieved"], "unit": rf["unit"],
                                   "clocks_sm_mhz": r["clocks"]["sm_mhz"],
-                                  "energy": energy_estimate(r)}
+                                  "energy": None}
+    if args.energy and rank == 0:
+        nv = NvmlEnergy(dev.index)
+        for name in [args.precision] + [f for f in ("fp8", "fp32", "bf16", "bf16x3") if f != args.precision]:
+            r = forms.get(name)
+            if not r or "error" in r:
+                continue
+            e = measure_energy(nv, r["step"], r["T"], torch.cuda.current_stream(dev), dev)
+            if "unavailable" in e:
+                e["estimate"] = energy_estimate(r)
+            if name == args.precision:
+                res["energy"] = e
+            if args.forms and name in res.get("forms", {}):
+                res["forms"][name]["energy"] = e
     return res, W, forms
 
 
@@ -621,14 +640,19 @@ def time_torch_stft(W, dev, steps=20, warmup=3, eps=1e-10):
     and clips - torch.stft (cuFFT, no centring), |X|^2, a dense Mel matmul and
     the log, in FP32 - timed like the headline (CUDA events around the loop,
     two input copies rotated).  Its output is [B, M, T] rather than frame-major."""
-    import torch
     cfg = W.cfg
-    n_fft, hop, M = cfg["n_fft"], cfg["hop"], cfg["n_mels"]
     lens, offs = W.lens, W.offs
     B, L = len(lens), int(lens[0])
     if not (np.all(lens == L) and np.array_equal(offs, np.arange(B, dtype=np.int64) * L)):
         return {"skipped": "the batch is not B clips of one length packed back to back"}
-    x = W.wave_h[: B * L].view(B, L)
+    return time_stft_batch(W.wave_h[: B * L].view(B, L), cfg, dev, steps, warmup, eps)
+
+
+def time_stft_batch(x, cfg, dev, steps=20, warmup=3, eps=1e-10):
+    """torch.stft + |X|^2 + dense HTK Mel matmul + log on a [B, L] host batch (context)."""
+    import torch
+    n_fft, hop, M = cfg["n_fft"], cfg["hop"], cfg["n_mels"]
+    B, L = x.shape
     xs = [x.to(dev) for _ in range(2)]
     win = torch.hann_window(n_fft, periodic=True, dtype=torch.float32, device=dev)
     fb = torch.from_numpy(htk_mel_filterbank(cfg["sr"], n_fft, M, cfg["fmin"], cfg["fmax"])).to(dev, torch.float32)
@@ -659,6 +683,241 @@ def time_torch_stft(W, dev, steps=20, warmup=3, eps=1e-10):
     return {"pipeline": "torch.stft (cuFFT) + |X|^2 + dense HTK Mel matmul + log, FP32, no centring",
             "frames_per_step": B * T, "ms_per_step": ms, "frames_per_s": B * T / (ms / 1e3),
             "device": str(dev)}
+
+
+# ----------------------------------------------------- energy (NVML counter)
+class NvmlEnergy:
+    """Board energy from NVML's total-energy counter (millijoules since the
+    driver loaded; a read-only query, as in the paper's energy protocol).  The
+    device is found by its UUID, else by index when NVML sees one device."""
+
+    def __init__(self, dev_index):
+        import ctypes as C
+        self.C, self.ok, self.why = C, False, ""
+        try:
+            self.lib = C.CDLL("libnvidia-ml.so.1")
+        except OSError as e:
+            self.why = f"libnvidia-ml not loadable: {e}"
+            return
+        if self.lib.nvmlInit_v2() != 0:
+            self.why = "nvmlInit failed"
+            return
+        h = C.c_void_p()
+        st = 1
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(dev_index).uuid)
+            uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            st = self.lib.nvmlDeviceGetHandleByUUID(C.c_char_p(uuid.encode()), C.byref(h))
+        except Exception:
+            st = 1
+        if st != 0:
+            n = C.c_uint(0)
+            self.lib.nvmlDeviceGetCount_v2(C.byref(n))
+            if n.value != 1:
+                self.why = f"GPU not found by UUID and NVML sees {n.value} devices"
+                return
+            st = self.lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(0), C.byref(h))
+        if st != 0:
+            self.why = f"no NVML handle (status {st})"
+            return
+        self.h = h
+        self.ok = self.read_mj() is not None
+        if not self.ok:
+            self.why = "nvmlDeviceGetTotalEnergyConsumption unsupported"
+
+    def read_mj(self):
+        v = self.C.c_ulonglong(0)
+        st = self.lib.nvmlDeviceGetTotalEnergyConsumption(self.h, self.C.byref(v))
+        return int(v.value) if st == 0 else None
+
+
+def measure_energy(nv, step, frames_per_step, stream, dev, min_quanta=30, min_s=1.5, max_s=8.0):
+    """Joules per frame over a window of back-to-back launches that spans at
+    least `min_quanta` updates of the energy counter (polled every 2 ms on a
+    host thread) and `min_s` seconds: (E_end - E_start) / frames."""
+    import torch
+    if not nv.ok:
+        return {"unavailable": nv.why}
+    seen = {"n": 0, "run": True}
+
+    def poll():
+        last = nv.read_mj()
+        while seen["run"]:
+            v = nv.read_mj()
+            if v is not None and v != last:
+                seen["n"] += 1
+                last = v
+            time.sleep(0.002)
+
+    th = threading.Thread(target=poll, daemon=True)
+    torch.cuda.synchronize(dev)
+    th.start()
+    e0, t0, steps = nv.read_mj(), time.perf_counter(), 0
+    while True:
+        for _ in range(50):
+            step(steps)
+            steps += 1
+        torch.cuda.synchronize(dev)
+        el = time.perf_counter() - t0
+        if (el >= min_s and seen["n"] >= min_quanta) or el >= max_s:
+            break
+    e1 = nv.read_mj()
+    seen["run"] = False
+    th.join()
+    joules = (e1 - e0) / 1e3
+    frames = frames_per_step * steps
+    return {"joules_per_frame": joules / frames, "frames_per_joule": frames / joules if joules > 0 else None,
+            "watts": joules / el, "window_s": el, "counter_updates": seen["n"], "launches": steps,
+            "method": "NVML total-energy counter over back-to-back launches (>= 30 counter updates)"}
+
+
+# --------------------------------------------------------- config legs, sweeps
+def time_launches(fn, dev, steps, trials=7, warmup=3):
+    """Median over `trials` of the per-launch time (ms) of `steps` back-to-back calls of fn(i)."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    for i in range(warmup):
+        fn(i)
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(trials + 1)]
+    ev[0].record(stream)
+    i = 0
+    for t in range(trials):
+        for _ in range(steps):
+            fn(i)
+            i += 1
+        ev[t + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    return statistics.median(ev[t].elapsed_time(ev[t + 1]) / steps for t in range(trials))
+
+
+def _gen_levels(first, n):
+    from paper_2606_01009_gb300 import inputs as G
+    return G.workload("levels_1024x10s", clips=n, first=first)[0]
+
+
+def levels_clips(workers=16):
+    """The 1024 x 10 s precision-sweep clips, generated by a pool of spawned
+    processes (generation only; the clips are identical to a serial draw)."""
+    import multiprocessing as mp
+    n = max(1, min(workers, os.cpu_count() or 1))
+    parts = [(i * 1024 // n, (i + 1) * 1024 // n - i * 1024 // n) for i in range(n)]
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.starmap(_gen_levels, parts)
+    return [c for part in res for c in part]
+
+
+def frontend_leg(melt, dev, clips, cfg, precision, n_mfcc=0, steps=10, peaks=None, oracle_clips=0):
+    """Launch time, frames/s and roofline fraction of one Frontend on a batch of
+    clips (inputs + outputs rotated over copies that exceed L2); with
+    oracle_clips > 0, the form's dB error against the FP64 oracle on the first
+    oracle_clips clips."""
+    import torch
+    from paper_2606_01009_gb300 import inputs as G
+    pk = G.pack_clips(clips)
+    fe = melt.Frontend(sr=cfg["sr"], n_fft=cfg["n_fft"], hop=cfg["hop"], n_mels=cfg["n_mels"], fmin=cfg["fmin"],
+                       fmax=cfg["fmax"], precision=precision, n_mfcc=n_mfcc)
+    T = fe.total_frames(pk.lengths)
+    in_b, out_b = pk.wave.nbytes, T * fe.n_out * 4
+    copies = max(2, math.ceil(2.5 * L2_BYTES / max(in_b + out_b, 1)))
+    waves = [torch.from_numpy(pk.wave).to(dev) for _ in range(copies)]
+    outs = [torch.empty((T, fe.n_out), device=dev) for _ in range(copies)]
+    ms = time_launches(lambda i: fe(waves[i % copies], pk.offsets, pk.lengths, out=outs[i % copies]), dev, steps)
+    fe.sync()
+    alg = algorithmic_bytes(pk.lengths, cfg["n_fft"], cfg["hop"], fe.n_out)
+    res = {"precision": precision, "n_mels": cfg["n_mels"], "n_mfcc": n_mfcc, "frames": T, "launch_us": ms * 1e3,
+           "frames_per_s": T / (ms / 1e3), "hbm_gbs": alg / (ms / 1e3) / 1e9}
+    if peaks:
+        if precision == "fp32":
+            flops = 2 * cfg["n_fft"] * 2 * cfg["n_mels"] * T
+            peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+            res["roofline_frac"], res["bound"] = flops / (ms / 1e3) / peak, "alu"
+        else:
+            res["roofline_frac"], res["bound"] = res["hbm_gbs"] / peaks["hbm_gbs"], "hbm"
+    if oracle_clips:
+        from oracle import melt_oracle as O
+        spec = O.MelTSpec(sr=cfg["sr"], n_fft=cfg["n_fft"], hop=cfg["hop"], n_mels=cfg["n_mels"], fmin=cfg["fmin"],
+                          fmax=cfg["fmax"], n_mfcc=n_mfcc)
+        ref = np.concatenate([O.melt_clip(c, spec) for c in clips[:oracle_clips]])
+        fe(waves[0], pk.offsets, pk.lengths, out=outs[0])
+        fe.sync()
+        got = outs[0][: ref.shape[0]].cpu().numpy().astype(np.float64)
+        err = {"all": O.err_db(got, ref)}
+        if not n_mfcc:
+            for d in (10.0, 30.0, 60.0, 100.0):
+                err[f"within_{int(d)}dB"] = O.err_db(got, ref, O.within_db_of_frame_max(ref, d))
+        res["error_db_vs_fp64"] = {k: {"max": v[0], "rms": v[1]} for k, v in err.items()}
+        res["error_sample"] = f"first {oracle_clips} clips ({ref.shape[0]} frames)"
+    fe.close()
+    return res
+
+
+def config_legs(args, dev, peaks):
+    """The other configurations of the workload list, as bench legs: the
+    64 x 30 s batch at M = 128 and with the MFCC variant (K = 40), and every
+    operand form on the 1024 x 10 s precision sweep (levels -60..0 dBFS)."""
+    from paper_2606_01009_gb300 import inputs as G
+    from paper_2606_01009_gb300 import melt
+    base = dict(sr=16000.0, n_fft=400, hop=160, n_mels=80, fmin=0.0, fmax=8000.0)
+    out = {}
+    rich, _ = G.workload("rich_64x30s")
+    out["rich_64x30s_bf16_m128"] = frontend_leg(melt, dev, rich, dict(base, n_mels=128), "bf16", steps=20,
+                                               peaks=peaks, oracle_clips=1)
+    out["rich_64x30s_bf16_mfcc40"] = frontend_leg(melt, dev, rich, base, "bf16", n_mfcc=40, steps=20, peaks=peaks,
+                                                 oracle_clips=1)
+    levels = levels_clips()
+    sweep = {}
+    for prec in ("fp32", "bf16", "bf16x3", "fp8"):
+        sweep[prec] = frontend_leg(melt, dev, levels, base, prec, steps=3 if prec == "fp32" else 10, peaks=peaks,
+                                   oracle_clips=4)
+    out["levels_1024x10s"] = sweep
+    return out
+
+
+def sweeps(args, dev):
+    """Paper's scaling figures on synthetic clips: the batch sweep (1..256 clips
+    of 4 s) and the Mel-count sweep (one 160 s clip), MelT (BF16, FP32)
+    against the torch.stft context pipeline on the same GPU."""
+    import torch
+    from paper_2606_01009_gb300 import inputs as G
+    from paper_2606_01009_gb300 import melt
+    base = dict(sr=16000.0, n_fft=400, hop=160, n_mels=80, fmin=0.0, fmax=8000.0)
+    res = {"batch_4s": [], "mels_160s": []}
+    clips = [G.rich_clip(4242, i, 64000) for i in range(256)]
+    fes = {p: melt.Frontend(precision=p) for p in ("bf16", "fp32")}
+    for b in (1, 2, 4, 8, 16, 32, 64, 128, 256):
+        pk = G.pack_clips(clips[:b])
+        wave = torch.from_numpy(pk.wave).to(dev)
+        row = {"batch": b, "frames": fes["bf16"].total_frames(pk.lengths)}
+        for p, fe in fes.items():
+            out = torch.empty((row["frames"], 80), device=dev)
+            ms = time_launches(lambda i: fe(wave, pk.offsets, pk.lengths, out=out), dev, 10 if p == "bf16" else 3)
+            row[f"melt_{p}_us"] = ms * 1e3
+        x = torch.from_numpy(np.stack([c for c in clips[:b]]))
+        row["torch_stft_us"] = time_stft_batch(x, base, dev, steps=10)["ms_per_step"] * 1e3
+        row["speedup_bf16_vs_stft"] = row["torch_stft_us"] / row["melt_bf16_us"]
+        res["batch_4s"].append(row)
+    for fe in fes.values():
+        fe.close()
+    clip = G.rich_clip(4243, 0, 160 * 16000)
+    pk = G.pack_clips([clip])
+    wave = torch.from_numpy(pk.wave).to(dev)
+    for M in (40, 64, 80, 128):
+        cfg = dict(base, n_mels=M)
+        row = {"n_mels": M}
+        for p in ("bf16", "fp32"):
+            fe = melt.Frontend(precision=p, n_mels=M)
+            T = fe.total_frames(pk.lengths)
+            out = torch.empty((T, M), device=dev)
+            row[f"melt_{p}_us"] = time_launches(lambda i: fe(wave, pk.offsets, pk.lengths, out=out), dev,
+                                                10 if p == "bf16" else 3) * 1e3
+            fe.close()
+        row["frames"] = T
+        row["torch_stft_us"] = time_stft_batch(torch.from_numpy(clip[None, :].copy()), cfg, dev, steps=10)["ms_per_step"] * 1e3
+        row["speedup_bf16_vs_stft"] = row["torch_stft_us"] / row["melt_bf16_us"]
+        res["mels_160s"].append(row)
+    return res
 
 
 def time_correction(args, W, dev, steps=200, warmup=5):
@@ -750,6 +1009,19 @@ def main():
                     W, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
             except Exception as e:  # reported, not fatal: the headline line above stands
                 res["torch_stft_context"] = {"error": str(e)}
+        if args.configs:
+            import torch
+            try:
+                res["configs"] = config_legs(args, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))),
+                                             load_peaks()[0])
+            except Exception as e:  # reported, not fatal
+                res["configs"] = {"error": repr(e)}
+        if args.sweeps:
+            import torch
+            try:
+                res["sweeps"] = sweeps(args, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
+            except Exception as e:  # reported, not fatal
+                res["sweeps"] = {"error": repr(e)}
         print(json.dumps(res, default=_jsonable), flush=True)
     if world > 1:
         import torch.distributed as dist
