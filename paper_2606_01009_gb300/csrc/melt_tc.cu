@@ -134,7 +134,7 @@ bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) 
   p.off_misc = off;
   off += 128;
   p.off_dct = off;
-  off += align_up(4 * n_mfcc * p.MP, 128);
+  off += align_up(4 * ((n_mfcc + 3) & ~3) * p.MP, 128);
   if (off + 128 > kSmemLimit) return false;
   p.smem_total = off + 128;
   p.tmem_cols = p.NC <= 32 ? 64 : p.NC <= 64 ? 128 : p.NC <= 128 ? 256 : 512;
@@ -232,7 +232,7 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
       p.off_codes = off;  // FP8: the scale code of every Z row of the tile, per A buffer
       off += fp8 ? align_up(p.codes_stride * (uint32_t)p.ZB, 128) : 0u;
       p.off_dct = off;
-      off += align_up(4 * n_mfcc * p.MP, 128);
+      off += align_up(4 * ((n_mfcc + 3) & ~3) * p.MP, 128);
       if (off + 128 > kSmemLimit) continue;
       p.NS = ns;
       p.smem_total = off + 128;

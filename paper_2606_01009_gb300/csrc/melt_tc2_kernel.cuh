@@ -57,16 +57,21 @@ namespace tc {
 // converters epw+3 .. epw+6.
 constexpr int kPCvtWarps = 4;
 constexpr int kPCvtThreads = 32 * kPCvtWarps;  // 128
-__host__ __device__ constexpr int pair_epi_warps(bool mlp) { return mlp ? 8 : 4; }
+// Epilogue warps: 8 (two per TMEM lane quarter) with the fused MLP, and for
+// the MFCC epilogue where M <= 80 (the two split the DCT coefficients); 4
+// otherwise.
+__host__ __device__ constexpr int pair_epi_warps(bool mlp, bool mfcc = false, int nch = 1) {
+  return mlp || (mfcc && nch <= 5) ? 8 : 4;
+}
 // Converter warps: 4 (BF16: each sample converted once, short chains), 8 for
-// FP8, whose per-row max makes each chunk one dependent chain per row set
-// (twice the warps, half the chain), unless the MFCC epilogue of M > 80 needs
-// more registers than 480 threads leave (136 a thread).
+// FP8's log-Mel kernel, whose per-row max makes each chunk one dependent
+// chain per row set (twice the warps, half the chain).  The MFCC kernels keep
+// 4 (their epilogue warps and registers fill the block).
 __host__ __device__ constexpr int pair_cvt_warps(int prec, bool mfcc, int nch) {
-  return prec == MELT_FP8E4M3 && !(mfcc && nch > 5) ? 8 : 4;
+  return prec == MELT_FP8E4M3 && !mfcc ? 8 : 4;
 }
 __host__ __device__ constexpr int pair_threads(bool mlp, int prec = MELT_BF16, bool mfcc = false, int nch = 1) {
-  return 32 * (pair_epi_warps(mlp) + 3 + pair_cvt_warps(prec, mfcc, nch));
+  return 32 * (pair_epi_warps(mlp, mfcc, nch) + 3 + pair_cvt_warps(prec, mfcc, nch));
 }
 constexpr int kPQuads = 8;  // float4s per converter thread per staged chunk (<= 16 KB)
 constexpr uint32_t kSfOne = 0x7F7F7F7Fu;    // four UE8M0 codes of 2^0
@@ -712,6 +717,7 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
   const int row = 32 * quarter + lane;
   const float* dct = reinterpret_cast<const float*>(gbase + p.off_dct);
   const bool vec8 = ((p.n_out & 7) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 31) == 0);
+  const bool vec4 = ((p.n_out & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 15) == 0);
   const int nch = p.MP >> 4;
   int c_lo, c_hi;
   half_chunks(nch, EPW / 4, half, c_lo, c_hi);
@@ -729,8 +735,8 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
     const bool valid = row < td.n_frames;
     const uint32_t t0 = tmem_base + ((uint32_t)(32 * quarter) << 16) + acc * p.acc_stride;
     float* orow = p.out + (size_t)(td.out_row + row) * p.n_out;
-    // an empty tile, or the second half of the MFCC epilogue (the DCT needs whole rows): no reads
-    if (td.n_frames == 0 || (MFCC && half == 1)) {
+    // an empty tile: no reads
+    if (td.n_frames == 0) {
       tc_fence_before();
       warp_arrive_leader(pbar(p, c, B.t_empty + acc));
       continue;
@@ -797,19 +803,12 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
       }
       tc_fence_before();
       warp_arrive_leader(pbar(p, c, B.t_empty + acc));
+      // the two warps of a lane quarter (EPW = 8) each read the whole row and
+      // take alternate groups of four coefficients
 #pragma unroll 1
-      for (int kk = 0; kk < p.n_mfcc; ++kk) {
-        const float4* d4 = reinterpret_cast<const float4*>(dct + kk * 16 * NCH);
-        float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-        for (int qq = 0; qq < 4 * NCH; ++qq) {
-          const float4 d = d4[qq];
-          a0 = fmaf(lm[4 * qq], d.x, a0);
-          a1 = fmaf(lm[4 * qq + 1], d.y, a1);
-          a0 = fmaf(lm[4 * qq + 2], d.z, a0);
-          a1 = fmaf(lm[4 * qq + 3], d.w, a1);
-        }
-        if (valid) orow[kk] = a0 + a1;
+      for (int kk0 = 4 * half; kk0 < p.n_mfcc; kk0 += 4 * (EPW / 4)) {
+        const float4 v = dct_quad<NCH>(lm, dct, kk0);
+        if (valid) store_quad(orow, kk0, p.n_mfcc, v, vec4);
       }
     }
   }
@@ -976,7 +975,7 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
 
 template <int NCH, bool MFCC, bool MLP, int PREC = MELT_BF16>
 __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH), 1) melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
-  constexpr int EPW = pair_epi_warps(MLP);
+  constexpr int EPW = pair_epi_warps(MLP, MFCC, NCH);
   constexpr int kPMmaWarp = EPW, kPBWarp = EPW + 1, kPProdWarp = EPW + 2, kPCvtWarp0 = EPW + 3;
   constexpr int CW = pair_cvt_warps(PREC, MFCC, NCH);
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -1043,11 +1042,7 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH), 1) melt_tc
   }
   if constexpr (MFCC) {
     if (warp < EPW) {
-      float* dct = reinterpret_cast<float*>(gbase + p.off_dct);
-      for (int i = threadIdx.x; i < p.n_mfcc * p.MP; i += 32 * EPW) {
-        const int kk = i / p.MP, m = i - kk * p.MP;
-        dct[i] = m < p.M ? p.dct[kk * p.M + m] : 0.f;
-      }
+      fill_dct(p, reinterpret_cast<float*>(gbase + p.off_dct), threadIdx.x, 32 * EPW);
     }
   }
   tc_fence_before();

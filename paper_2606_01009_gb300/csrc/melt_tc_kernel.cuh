@@ -502,6 +502,53 @@ static __device__ void role_convert_bf16(const TcParams& p, uint32_t sbase, cons
   }
 }
 
+// MFCC (Eq. 9): coefficients kk0 .. kk0+3 of one frame, C[kk] = sum_m lm[m]
+// D[kk][m], from its log-Mel row in registers and the DCT-II matrix in shared
+// memory (rows of 16 NCH floats, zero past M; the matrix is padded with zero
+// rows to a multiple of four).  Four independent sums, each in order m = 0,
+// 1, ..., so that one FMA issues per cycle.
+template <int NCH>
+static __device__ __forceinline__ float4 dct_quad(const float (&lm)[16 * NCH], const float* dct, int kk0) {
+  float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int qq = 0; qq < 4 * NCH; ++qq) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float4 d = reinterpret_cast<const float4*>(dct + (kk0 + r) * 16 * NCH)[qq];
+      a[r] = fmaf(lm[4 * qq], d.x, a[r]);
+      a[r] = fmaf(lm[4 * qq + 1], d.y, a[r]);
+      a[r] = fmaf(lm[4 * qq + 2], d.z, a[r]);
+      a[r] = fmaf(lm[4 * qq + 3], d.w, a[r]);
+    }
+  }
+  return make_float4(a[0], a[1], a[2], a[3]);
+}
+
+// Stores coefficients kk0 .. kk0+3 (those below n_mfcc) of a frame's row:
+// one 16-byte store when the row is 16-byte aligned and all four exist.
+static __device__ __forceinline__ void store_quad(float* orow, int kk0, int n_mfcc, float4 v, bool vec4) {
+  if (vec4 && kk0 + 4 <= n_mfcc) {
+    asm volatile("st.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(orow + kk0), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+  } else {
+    const float a[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (kk0 + r < n_mfcc) orow[kk0 + r] = a[r];
+  }
+}
+
+// Fills the shared-memory DCT-II matrix: n_mfcc rows of MP floats (zero past
+// M), then zero rows up to a multiple of four.
+static __device__ __forceinline__ void fill_dct(const TcParams& p, float* dct, int t0, int nt) {
+  const int rows = (p.n_mfcc + 3) & ~3;
+  for (int i = t0; i < rows * p.MP; i += nt) {
+    const int kk = i / p.MP, m = i - kk * p.MP;
+    dct[i] = (kk < p.n_mfcc && m < p.M) ? p.dct[kk * p.M + m] : 0.f;
+  }
+}
+
 template <int PREC, int NCH, bool MFCC>
 __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase, const Bars& B,
                               uint32_t tmem_base, volatile int* abort) {
@@ -509,6 +556,7 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
   const int row = 32 * warp + lane;
   const float* dct = reinterpret_cast<const float*>(gbase + p.off_dct);  // [n_mfcc][dct_ld]
   const bool vec8 = ((p.n_out & 7) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 31) == 0);
+  const bool vec4 = ((p.n_out & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 15) == 0);
   const int nch = p.MP >> 4;
   int k = 0;
   TileDesc td_next;
@@ -586,18 +634,9 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
       tc_fence_before();
       warp_arrive(sbase + p.off_bar + 8 * (B.t_empty + acc));
 #pragma unroll 1
-      for (int kk = 0; kk < p.n_mfcc; ++kk) {
-        const float4* d4 = reinterpret_cast<const float4*>(dct + kk * 16 * NCH);
-        float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-        for (int q = 0; q < 4 * NCH; ++q) {
-          const float4 d = d4[q];  // zero past n_mels
-          a0 = fmaf(lm[4 * q], d.x, a0);
-          a1 = fmaf(lm[4 * q + 1], d.y, a1);
-          a0 = fmaf(lm[4 * q + 2], d.z, a0);
-          a1 = fmaf(lm[4 * q + 3], d.w, a1);
-        }
-        if (valid) orow[kk] = a0 + a1;
+      for (int kk0 = 0; kk0 < p.n_mfcc; kk0 += 4) {
+        const float4 v = dct_quad<NCH>(lm, dct, kk0);
+        if (valid) store_quad(orow, kk0, p.n_mfcc, v, vec4);
       }
     }
   }
@@ -652,11 +691,7 @@ __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_const
   if constexpr (MFCC) {
     // DCT-II rows padded with zeros to MP columns (16-byte aligned rows)
     if (warp < kEpiWarps) {
-      float* dct = reinterpret_cast<float*>(gbase + p.off_dct);
-      for (int i = threadIdx.x; i < p.n_mfcc * p.MP; i += kEpiThreads) {
-        const int kk = i / p.MP, m = i - kk * p.MP;
-        dct[i] = m < p.M ? p.dct[kk * p.M + m] : 0.f;
-      }
+      fill_dct(p, reinterpret_cast<float*>(gbase + p.off_dct), threadIdx.x, kEpiThreads);
     }
   }
   tc_fence_before();
