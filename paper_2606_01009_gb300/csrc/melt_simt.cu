@@ -10,7 +10,8 @@
 // tx + 16j, j < MJ, for both R and I (16*MJ FP32 accumulators).
 // K loop in chunks of 32 samples: the chunk of the frame matrix is
 // transposed into shared memory (Xs[k][f]) with coalesced loads, the basis
-// chunk (row-major [k][2*mp], R/I interleaved) is copied beside it.
+// chunk (row-major [k][2*mp], R/I interleaved) is copied beside it; the next
+// chunk's loads are in flight while the current one is computed.
 #include "melt_internal.h"
 
 namespace melt {
@@ -22,15 +23,67 @@ constexpr int kKC = 32;          // samples per K chunk
 constexpr int kXPad = 4;         // Xs row padding (keeps float4 alignment)
 constexpr int kThreads = 256;
 
+// K chunks are double-buffered: the global loads of chunk c + 1 are issued
+// into registers before chunk c is computed and stored into the other
+// shared-memory buffer after it, so one barrier per chunk separates them and
+// the loads' latency hides behind the FFMAs.
+template <int MJ>
+struct SimtChunk {
+  static constexpr int kXq = kF * kKC / kThreads;        // frame samples per thread (16)
+  static constexpr int kWq = (kKC * 2 * 16 * MJ / 4 + kThreads - 1) / kThreads;  // basis float4s per thread
+  float x[kXq];
+  float4 w[kWq];
+};
+
+template <int MJ>
+static __device__ __forceinline__ void simt_load_chunk(const SimtParams& p, const TileDesc& td, int k0, int tid,
+                                                       SimtChunk<MJ>& c) {
+  const int N = p.n_fft, H = p.hop, W2 = 2 * p.mp, row4 = W2 / 4;
+#pragma unroll
+  for (int i = 0; i < SimtChunk<MJ>::kXq; ++i) {
+    const int idx = tid + i * kThreads;
+    const int k = idx % kKC, f = idx / kKC;
+    const int n = k0 + k;
+    c.x[i] = (f < td.n_frames && n < N) ? __ldg(p.wave + td.in_off + (int64_t)f * H + n) : 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < SimtChunk<MJ>::kWq; ++i) {
+    const int idx = tid + i * kThreads;
+    const int k = idx / row4, c4 = idx - k * row4;
+    c.w[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (idx < kKC * row4 && k0 + k < N) c.w[i] = __ldg(reinterpret_cast<const float4*>(p.w32 + (size_t)(k0 + k) * W2) + c4);
+  }
+}
+
+template <int MJ>
+static __device__ __forceinline__ void simt_store_chunk(const SimtParams& p, int tid, const SimtChunk<MJ>& c,
+                                                        float* Xs, float* Ws) {
+  const int W2 = 2 * p.mp, row4 = W2 / 4;
+#pragma unroll
+  for (int i = 0; i < SimtChunk<MJ>::kXq; ++i) {
+    const int idx = tid + i * kThreads;
+    Xs[(idx % kKC) * (kF + kXPad) + idx / kKC] = c.x[i];
+  }
+#pragma unroll
+  for (int i = 0; i < SimtChunk<MJ>::kWq; ++i) {
+    const int idx = tid + i * kThreads;
+    if (idx < kKC * row4) {
+      const int k = idx / row4, c4 = idx - k * row4;
+      reinterpret_cast<float4*>(Ws + k * W2)[c4] = c.w[i];
+    }
+  }
+}
+
 template <int MJ>
 __global__ void __launch_bounds__(kThreads, 1) melt_simt_kernel(SimtParams p) {
   extern __shared__ __align__(16) float smem[];
   constexpr int kXs = kKC * (kF + kXPad);
-  float* Xs = smem;             // [kKC][kF + kXPad]
-  float* Ws = smem + kXs;       // [kKC][2*mp]
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int N = p.n_fft, H = p.hop, M = p.n_mels, W2 = 2 * p.mp;
+  const int N = p.n_fft, M = p.n_mels, W2 = 2 * p.mp;
+  const int kWs = kKC * W2;
+  float* Xbuf[2] = {smem, smem + kXs + kWs};          // [kKC][kF + kXPad], then the basis chunk [kKC][2 mp]
+  float* Wbuf[2] = {smem + kXs, smem + 2 * kXs + kWs};
 
   for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
     const TileDesc td = p.tiles[tile];
@@ -40,27 +93,17 @@ __global__ void __launch_bounds__(kThreads, 1) melt_simt_kernel(SimtParams p) {
 #pragma unroll
       for (int j = 0; j < MJ; ++j) acc[i][j][0] = acc[i][j][1] = 0.f;
 
-    for (int k0 = 0; k0 < N; k0 += kKC) {
-      __syncthreads();
-      // Frame chunk, transposed: Xs[k][f] = x[in_off + f*H + k0 + k]
-#pragma unroll 4
-      for (int i = 0; i < kF * kKC / kThreads; ++i) {
-        const int idx = tid + i * kThreads;
-        const int k = idx % kKC, f = idx / kKC;
-        const int n = k0 + k;
-        float v = 0.f;
-        if (f < td.n_frames && n < N) v = __ldg(p.wave + td.in_off + (int64_t)f * H + n);
-        Xs[k * (kF + kXPad) + f] = v;
-      }
-      // Basis chunk: rows k0..k0+31 of w32 (zero past N)
-      const int row4 = W2 / 4;
-      for (int idx = tid; idx < kKC * row4; idx += kThreads) {
-        const int k = idx / row4, c4 = idx - k * row4;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k0 + k < N) v = __ldg(reinterpret_cast<const float4*>(p.w32 + (size_t)(k0 + k) * W2) + c4);
-        reinterpret_cast<float4*>(Ws + k * W2)[c4] = v;
-      }
-      __syncthreads();
+    SimtChunk<MJ> nxt;
+    simt_load_chunk<MJ>(p, td, 0, tid, nxt);
+    __syncthreads();  // the previous tile's readers of both buffers (and the MFCC staging) are done
+    simt_store_chunk<MJ>(p, tid, nxt, Xbuf[0], Wbuf[0]);
+    __syncthreads();
+    int b = 0;
+    for (int k0 = 0; k0 < N; k0 += kKC, b ^= 1) {
+      const bool more = k0 + kKC < N;
+      if (more) simt_load_chunk<MJ>(p, td, k0 + kKC, tid, nxt);
+      const float* Xs = Xbuf[b];
+      const float* Ws = Wbuf[b];
       const int kn = min(kKC, N - k0);
 #pragma unroll 4
       for (int k = 0; k < kn; ++k) {
@@ -76,6 +119,10 @@ __global__ void __launch_bounds__(kThreads, 1) melt_simt_kernel(SimtParams p) {
             acc[i][j][1] = fmaf(xv[i], w.y, acc[i][j][1]);
           }
         }
+      }
+      if (more) {
+        simt_store_chunk<MJ>(p, tid, nxt, Xbuf[b ^ 1], Wbuf[b ^ 1]);  // its last readers finished a chunk ago
+        __syncthreads();
       }
     }
 
@@ -110,7 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1) melt_simt_kernel(SimtParams p) {
       continue;
     }
     // MFCC: stage the tile's log-Mel rows in shared memory, then apply D.
-    __syncthreads();
+    __syncthreads();  // every thread is done reading the chunk buffers
     float* L = smem;  // [kF][M]
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -141,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1) melt_simt_kernel(SimtParams p) {
 
 int simt_smem_bytes(int mj, int n_mels, int n_mfcc) {
   const int mp = 16 * mj;
-  int bytes = (kKC * (kF + kXPad) + kKC * 2 * mp) * (int)sizeof(float);
+  int bytes = 2 * (kKC * (kF + kXPad) + kKC * 2 * mp) * (int)sizeof(float);  // two chunk buffers
   if (n_mfcc > 0) {
     const int l = kF * n_mels * (int)sizeof(float);
     if (l > bytes) bytes = l;
