@@ -877,8 +877,9 @@ def config_legs(args, dev, peaks):
 
 def sweeps(args, dev):
     """Paper's scaling figures on synthetic clips: the batch sweep (1..256 clips
-    of 4 s) and the Mel-count sweep (one 160 s clip), MelT (BF16, FP32)
-    against the torch.stft context pipeline on the same GPU."""
+    of 4 s) and the Mel-count sweep (one 160 s clip, M = 40..512), MelT (BF16;
+    FP32 up to M = 128) against the torch.stft context pipeline on the same
+    GPU."""
     import torch
     from paper_2606_01009_gb300 import inputs as G
     from paper_2606_01009_gb300 import melt
@@ -903,10 +904,10 @@ def sweeps(args, dev):
     clip = G.rich_clip(4243, 0, 160 * 16000)
     pk = G.pack_clips([clip])
     wave = torch.from_numpy(pk.wave).to(dev)
-    for M in (40, 64, 80, 128):
+    for M in (40, 64, 80, 128, 256, 512):
         cfg = dict(base, n_mels=M)
         row = {"n_mels": M}
-        for p in ("bf16", "fp32"):
+        for p in (("bf16", "fp32") if M <= 128 else ("bf16",)):  # FP32 kernels hold M <= 128
             fe = melt.Frontend(precision=p, n_mels=M)
             T = fe.total_frames(pk.lengths)
             out = torch.empty((T, M), device=dev)

@@ -157,8 +157,12 @@ melt_status create_common(double sr, int n_fft, int hop, const double* freqs, in
                           double eps, melt_basis** out) {
   if (!out) return MELT_ERR_ARG;
   *out = nullptr;
+  // more than 128 frequencies: BF16 forms only, log-Mel (the kernels' blocks of 128 bins)
+  if (n_freqs > 128 && (precision == MELT_FP32 || precision == MELT_FP8E4M3 || n_mfcc > 0) && n_freqs <= 512 &&
+      sr > 0 && n_fft >= 16)
+    return MELT_ERR_UNSUPPORTED;
   if (!(sr > 0) || n_fft < 16 || n_fft > 4096 || (n_fft & 3) || hop < 1 || hop > n_fft ||
-      (hop & 3) || n_freqs < 1 || n_freqs > 128 || n_mfcc < 0 || n_mfcc > n_freqs ||
+      (hop & 3) || n_freqs < 1 || n_freqs > 512 || n_mfcc < 0 || n_mfcc > n_freqs ||
       !(eps >= 0) || (window != MELT_WIN_HANN_PERIODIC && window != MELT_WIN_HANN_SYMMETRIC) ||
       precision < MELT_FP32 || precision > MELT_FP8E4M3)
     return MELT_ERR_ARG;
@@ -419,7 +423,7 @@ melt_status melt_basis_create_ex(double sr, int n_fft, int hop, int n_mels, doub
                                  double eps, melt_basis** out) {
   if (!out) return MELT_ERR_ARG;
   *out = nullptr;
-  if (n_mels < 1 || n_mels > 128 || !(sr > 0) || !(fmin >= 0) || !(fmax > fmin) ||
+  if (n_mels < 1 || n_mels > 512 || !(sr > 0) || !(fmin >= 0) || !(fmax > fmin) ||
       !(fmax <= sr / 2))
     return MELT_ERR_ARG;
   // M interior points of M+2 points uniform on the Mel scale (Sec. III-A)

@@ -68,6 +68,8 @@ bool plan_smem(const TcBasis* tb, TcParams& p, int n_mfcc) {
   p.M = tb->n_mels;
   p.MP = (p.M + 15) / 16 * 16;
   p.NC = 2 * p.MP;
+  p.nblk = (p.MP + 127) / 128;  // accumulator blocks of 128 Mel bins (one when M <= 128)
+  p.wbl = p.MP - 128 * (p.nblk - 1);
   p.J = tb->J;
   p.KS = tb->ksteps;
   p.zrows = kF + p.J - 1;
@@ -115,12 +117,17 @@ bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) 
     return false;
   if (!c.basis_resident && (c.basis_slots < 2 || c.basis_slots > 32 || c.ksteps_per_slot < 1))
     return false;
+  const bool wide = p.nblk > 1;  // more than 128 Mel bins: streamed basis, no MFCC
+  if (wide && (c.basis_resident || n_mfcc != 0)) return false;
   p.b_resident = c.basis_resident ? 1 : 0;
   p.ZB = c.a_buffers;
   p.pf = c.prefetch_tiles;
   p.kps = p.b_resident ? 1 : std::min(c.ksteps_per_slot, p.KS);
   p.NB = p.b_resident ? p.KS : c.basis_slots;
-  p.bslot_bytes = p.b_resident ? p.step_bytes : p.step_bytes * p.kps;
+  const uint32_t parts = P == MELT_BF16X3 ? 2u : 1u;
+  p.blk_step = wide ? 256u * 32u * parts : p.step_bytes;
+  p.blk_step_last = wide ? 2u * (uint32_t)p.wbl * 32u * parts : p.step_bytes;
+  p.bslot_bytes = p.b_resident ? p.step_bytes : p.blk_step * p.kps;
   const Bars B(p.ZB, p.NB);
   uint32_t off = 0;
   p.off_a = off;
@@ -139,7 +146,8 @@ bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) 
   p.smem_total = off + 128;
   p.tmem_cols = p.NC <= 32 ? 64 : p.NC <= 64 ? 128 : p.NC <= 128 ? 256 : 512;
   p.acc_stride = p.tmem_cols / 2;
-  p.idesc = idesc_f32acc(1u, kF, p.NC);
+  p.idesc = idesc_f32acc(1u, kF, wide ? 256u : (uint32_t)p.NC);
+  p.idesc_last = idesc_f32acc(1u, kF, wide ? 2u * (uint32_t)p.wbl : (uint32_t)p.NC);
   p.desc_hi = (128u >> 4) | (1u << 14);  // SBO = 128 B; version bit (descriptor bit 46)
   return true;
 }
@@ -149,7 +157,7 @@ bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) 
 // takes every slot that still fits (2..8).
 bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) {
   const bool fp8 = tb->precision == MELT_FP8E4M3;
-  if (c.cta_pair != 1 || (tb->precision != MELT_BF16 && !fp8) || !tb->d_b2) return false;
+  if (c.cta_pair != 1 || (tb->precision != MELT_BF16 && !fp8) || !tb->d_b2 || p.nblk > 1) return false;
   // FP8: a converter lane holds at most two quads of a Z row
   if (fp8 && p.H > 256) return false;
   if (c.basis_resident != 1 || c.a_buffers < 1 || c.a_buffers > 2) return false;
@@ -157,6 +165,7 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
   if (c.schedule != 0 && c.schedule != 1) return false;
   p.dyn = c.schedule;
   p.b_resident = 1;
+  p.blk_step = p.blk_step_last = 0;
   p.ZB = c.a_buffers;
   p.pf = c.schedule ? 0 : c.prefetch_tiles;  // L2 prefetch stream of the waveform producer (static schedule)
   p.kps = 1;
@@ -262,7 +271,9 @@ int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap
   auto add = [&](int res, int zb, int pf, int nb, int kps) {
     if (n < cap) out[n++] = melt_plan{res, zb, pf, nb, kps, 0, 0};
   };
-  const int sb = (int)std::max(1u, p.kstep_bytes * (tb->precision == MELT_BF16X3 ? 2u : 1u));
+  const uint32_t parts = tb->precision == MELT_BF16X3 ? 2u : 1u;
+  // bytes of one streamed K-step: all basis rows, or one block of 128 Mel bins when M > 128
+  const int sb = (int)std::max(1u, p.nblk > 1 ? 256u * 32u * parts : p.kstep_bytes * parts);
   melt_plan alts[2];
   int n_alt = 0;
   if ((tb->precision == MELT_BF16 || tb->precision == MELT_FP8E4M3) && tb->d_b2) {
@@ -311,8 +322,11 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
   const int N = c.n_fft, H = c.hop, M = c.n_mels, P = c.precision;
   if (P != MELT_BF16 && P != MELT_BF16X3 && P != MELT_FP8E4M3) return MELT_ERR_ARG;
   if (P != MELT_FP8E4M3 && (H % 16) != 0) return MELT_ERR_UNSUPPORTED;
-  if (M > 128) return MELT_ERR_UNSUPPORTED;
+  // M > 128 (up to 512): BF16 forms only, as blocks of 128 Mel bins (FP8 runs in CTA pairs, M <= 128)
+  if (M > 512 || (M > 128 && P == MELT_FP8E4M3)) return MELT_ERR_UNSUPPORTED;
+  if (M > 128 && c.n_mfcc > 0) return MELT_ERR_UNSUPPORTED;
   const int MP = (M + 15) / 16 * 16, NC = 2 * MP;
+  const int nblk = (MP + 127) / 128;
   const int J = (N + H - 1) / H;
   // K-steps in (slice j, first sample r0 of the step) order; a step covers
   // 16 samples of slice j (BF16 forms) or 32 (FP8)
@@ -332,28 +346,42 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
     const int m = row - MP;
     return m < M ? w64[(size_t)(M + m) * N + n] : 0.0;
   };
+  // Image layout: one block per K-step of all NC rows, [part][core column
+  // cc][row][16 B] (parts: hi, then lo for BF16x3).  With more than 128 Mel
+  // bins the image is block-major instead: block b (Mel bins [128 b, 128 b +
+  // wb), R rows then I rows, 2 wb rows) holds all its K-steps contiguously.
+  auto blk_rows = [&](int b) { return nblk == 1 ? NC : 2 * std::min(128, MP - 128 * b); };
+  auto stacked_row = [&](int b, int r) {  // row of the stacked [W_r (MP rows); W_i (MP rows)] basis
+    if (nblk == 1) return r;
+    const int wb = blk_rows(b) / 2;
+    return r < wb ? 128 * b + r : MP + 128 * b + (r - wb);
+  };
+  for (int b = 0; b < nblk; ++b)
   for (int s = 0; s < KS; ++s) {
-    uint8_t* blk = img.data() + (size_t)s * parts * kstep_bytes;
+    const int rows_b = blk_rows(b);
+    const size_t part_b = (size_t)rows_b * 32;  // one part of one K-step of block b
+    uint8_t* blk = img.data() + (size_t)b * KS * parts * 256 * 32 + (size_t)s * parts * part_b;
     const int j = steps[s].first, r0 = steps[s].second;
     const int kj = std::min(H, N - j * H);  // samples of slice j; zero past them
     for (int cc = 0; cc < 2; ++cc)
-      for (int row = 0; row < NC; ++row) {
+      for (int brow = 0; brow < rows_b; ++brow) {
+        const int row = stacked_row(b, brow);
         if (P == MELT_FP8E4M3) {
           // 16 e4m3 values per core-column row: W 2^8 (the MMA scales by 2^-8)
           for (int e = 0; e < 16; ++e) {
             const int r = r0 + 16 * cc + e;
             const double w = r < kj ? std::ldexp(wval(row, j * H + r), 8) : 0.0;
-            blk[(size_t)cc * NC * 16 + row * 16 + e] = e4m3_bits(w);
+            blk[(size_t)cc * rows_b * 16 + brow * 16 + e] = e4m3_bits(w);
           }
         } else {
           for (int e = 0; e < 8; ++e) {
             const int r = r0 + 8 * cc + e;
             const double w = (r < H) ? wval(row, j * H + r) : 0.0;
             const uint16_t hi = bf16_bits(w);
-            std::memcpy(blk + (size_t)cc * NC * 16 + row * 16 + e * 2, &hi, 2);
+            std::memcpy(blk + (size_t)cc * rows_b * 16 + brow * 16 + e * 2, &hi, 2);
             if (P == MELT_BF16X3) {
               const uint16_t lo = bf16_bits(w - bf16_value(hi));
-              std::memcpy(blk + kstep_bytes + (size_t)cc * NC * 16 + row * 16 + e * 2, &lo, 2);
+              std::memcpy(blk + part_b + (size_t)cc * rows_b * 16 + brow * 16 + e * 2, &lo, 2);
             }
           }
         }
@@ -374,7 +402,7 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
     if (cudaMemcpy(tb->d_b, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
       return MELT_ERR_CUDA;
   }
-  if (P == MELT_BF16 || P == MELT_FP8E4M3) {
+  if ((P == MELT_BF16 || P == MELT_FP8E4M3) && nblk == 1) {
     // CTA-pair image: the K-step blocks of basis rows [0, MP) (W_r), then those
     // of rows [MP, 2 MP) (W_i); each block is 2 core columns x MP rows x 16 B
     const size_t half_step = (size_t)MP * 32;

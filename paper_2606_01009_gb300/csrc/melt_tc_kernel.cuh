@@ -92,6 +92,13 @@ struct TcParams {
   int NB;                // basis slots (resident: NB == KS)
   int b_resident;        // 1: the whole basis stays in shared memory for the CTA's life
   uint32_t tmem_cols, acc_stride, idesc;
+  // More than 128 Mel bins (BF16 forms, streamed basis): the accumulator is
+  // cut into nblk blocks of 128 bins (the last of wbl bins), each holding its
+  // bins' R then I columns (N = 2 x 128, last 2 wbl); the basis image is
+  // block-major, blk_step (blk_step_last) bytes per K-step of a block; a
+  // tile's blocks alternate between the two accumulators.  nblk = 1 otherwise.
+  int nblk, wbl;
+  uint32_t idesc_last, blk_step, blk_step_last;
   uint32_t desc_hi;      // high word of every operand descriptor (SBO = 128 B, version)
   uint32_t off_a, off_b, off_bar, off_misc, off_tab, off_dct;
   uint32_t smem_total;   // dynamic shared memory bytes (incl. alignment slack)
@@ -265,21 +272,25 @@ static __device__ void role_basis_producer(const TcParams& p, uint32_t sbase, co
   int issued = 0;
   bool ok = true;
   for (int tile = blockIdx.x; ok && tile < p.n_tiles; tile += gridDim.x) {
-    for (int s0 = 0; s0 < p.KS; s0 += p.kps) {
-      const uint32_t full = sbase + p.off_bar + 8 * (B.b_full + slot);
-      const uint32_t empty = sbase + p.off_bar + 8 * (B.b_empty + slot);
-      if (!mbar_wait(empty, phase ^ 1, abort, p.err, kErrTimeout)) {
-        ok = false;
-        break;
-      }
-      const uint32_t bytes = (uint32_t)min(p.kps, p.KS - s0) * p.step_bytes;
-      mbar_arrive_expect_tx(full, bytes);
-      bulk_g2s_hint(sbase + p.off_b + slot * p.bslot_bytes, p.bimg + (size_t)s0 * p.step_bytes,
-                    bytes, full, pol);
-      ++issued;
-      if (++slot == p.NB) {
-        slot = 0;
-        phase ^= 1;
+    for (int b = 0; ok && b < p.nblk; ++b) {
+      // block b's K-steps are contiguous in the image (one block: the whole image)
+      const uint32_t step = b + 1 < p.nblk ? p.blk_step : p.blk_step_last;
+      const uint8_t* src = p.bimg + (size_t)b * p.KS * p.blk_step;
+      for (int s0 = 0; s0 < p.KS; s0 += p.kps) {
+        const uint32_t full = sbase + p.off_bar + 8 * (B.b_full + slot);
+        const uint32_t empty = sbase + p.off_bar + 8 * (B.b_empty + slot);
+        if (!mbar_wait(empty, phase ^ 1, abort, p.err, kErrTimeout)) {
+          ok = false;
+          break;
+        }
+        const uint32_t bytes = (uint32_t)min(p.kps, p.KS - s0) * step;
+        mbar_arrive_expect_tx(full, bytes);
+        bulk_g2s_hint(sbase + p.off_b + slot * p.bslot_bytes, src + (size_t)s0 * step, bytes, full, pol);
+        ++issued;
+        if (++slot == p.NB) {
+          slot = 0;
+          phase ^= 1;
+        }
       }
     }
   }
@@ -294,86 +305,97 @@ __device__ void role_mma(const TcParams& p, uint8_t* gbase, uint32_t sbase, cons
   const uint2* tab = reinterpret_cast<const uint2*>(gbase + p.off_tab);
   const uint64_t hi = (uint64_t)p.desc_hi << 32;
   const uint32_t a_lo0 = ((sbase + p.off_a) >> 4) | ((p.lbo_a >> 4) << 16);
-  const uint32_t b_lo0 = ((sbase + p.off_b) >> 4) | (((uint32_t)p.NC * 16 >> 4) << 16);
   const uint32_t abuf16 = p.abuf_bytes >> 4, apart16 = p.a_bytes >> 4;
   const uint32_t bslot16 = p.bslot_bytes >> 4, bpart16 = p.kstep_bytes >> 4;
   int bslot = 0;
   uint32_t bphase = 0;
-  int k = 0;
+  int k = 0, kb = 0;  // tile ordinal; accumulator-block ordinal (kb == k with one block)
   for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++k) {
     const int zb = p.ZB == 2 ? (k & 1) : 0;
-    const int acc = k & 1;
     if (!mbar_wait(sbase + p.off_bar + 8 * (B.z_full + zb), (p.ZB == 2 ? (k >> 1) : k) & 1,
                    abort, p.err, kErrTimeout))
       break;
-    if (!mbar_wait(sbase + p.off_bar + 8 * (B.t_empty + acc), ((k >> 1) & 1) ^ 1, abort, p.err,
-                   kErrTimeout))
-      break;
     bool ok = true;
-    if (p.b_resident && k == 0) ok = mbar_wait(sbase + p.off_bar + 8 * B.b_full, 0, abort, p.err, kErrTimeout);
-    if (!ok) break;
-    tc_fence_after();
-    const uint32_t d = tmem_base + acc * p.acc_stride;
     const uint32_t alo = a_lo0 + zb * abuf16;
-    if (p.b_resident) {
-      // descriptors from the K-step table, eight at a time: the loads are issued
-      // ahead of the MMAs so that the issue loop is not latency bound
-      const uint32_t tab_s = smem_u32(tab);
+    for (int b = 0; ok && b < p.nblk; ++b, ++kb) {
+      const int acc = kb & 1;
+      if (!mbar_wait(sbase + p.off_bar + 8 * (B.t_empty + acc), ((kb >> 1) & 1) ^ 1, abort, p.err,
+                     kErrTimeout)) {
+        ok = false;
+        break;
+      }
+      if (p.b_resident && k == 0) ok = mbar_wait(sbase + p.off_bar + 8 * B.b_full, 0, abort, p.err, kErrTimeout);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t d = tmem_base + acc * p.acc_stride;
+      if (p.b_resident) {
+        // descriptors from the K-step table, eight at a time: the loads are issued
+        // ahead of the MMAs so that the issue loop is not latency bound
+        const uint32_t tab_s = smem_u32(tab);
 #pragma unroll 1
-      for (int s0 = 0; s0 < p.KS; s0 += 8) {
-        uint32_t tx[8], ty[8];
+        for (int s0 = 0; s0 < p.KS; s0 += 8) {
+          uint32_t tx[8], ty[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-          asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
-                       : "=r"(tx[u]), "=r"(ty[u])
-                       : "r"(tab_s + 8u * min(s0 + u, p.KS - 1)));
+          for (int u = 0; u < 8; ++u)
+            asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                         : "=r"(tx[u]), "=r"(ty[u])
+                         : "r"(tab_s + 8u * min(s0 + u, p.KS - 1)));
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int s = s0 + u;
-          if (s < p.KS) {
-            const uint64_t ad = hi | (alo + tx[u]);
-            const uint64_t bd = hi | ty[u];
-            mma_f16(d, ad, bd, p.idesc, s > 0);
-            if constexpr (PREC == MELT_BF16X3) {
-              mma_f16(d, ad, hi | (ty[u] + bpart16), p.idesc, 1);
-              mma_f16(d, hi | (alo + tx[u] + apart16), bd, p.idesc, 1);
+          for (int u = 0; u < 8; ++u) {
+            const int s = s0 + u;
+            if (s < p.KS) {
+              const uint64_t ad = hi | (alo + tx[u]);
+              const uint64_t bd = hi | ty[u];
+              mma_f16(d, ad, bd, p.idesc, s > 0);
+              if constexpr (PREC == MELT_BF16X3) {
+                mma_f16(d, ad, hi | (ty[u] + bpart16), p.idesc, 1);
+                mma_f16(d, hi | (alo + tx[u] + apart16), bd, p.idesc, 1);
+              }
             }
           }
         }
-      }
-    } else {
-      const uint32_t step16 = p.step_bytes >> 4;
-      for (int s0 = 0; s0 < p.KS && ok; s0 += p.kps) {
-        if (!mbar_wait(sbase + p.off_bar + 8 * (B.b_full + bslot), bphase, abort, p.err,
-                       kErrTimeout)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t blo0 = b_lo0 + bslot * bslot16;
-        const int n = min(p.kps, p.KS - s0);
-        for (int u = 0; u < n; ++u) {
-          const int s = s0 + u;
-          const uint2 t = tab[s];
-          const uint32_t blo = blo0 + u * step16;
-          const uint64_t ad = hi | (alo + t.x);
-          const uint64_t bd = hi | blo;
-          mma_f16(d, ad, bd, p.idesc, s > 0);
-          if constexpr (PREC == MELT_BF16X3) {
-            mma_f16(d, ad, hi | (blo + bpart16), p.idesc, 1);
-            mma_f16(d, hi | (alo + t.x + apart16), bd, p.idesc, 1);
+      } else {
+        // block b: N = 2 x (its Mel bins) rows, their K-steps streamed through the slot ring
+        const bool last = b + 1 == p.nblk;
+        const uint32_t step = last ? p.blk_step_last : p.blk_step;
+        const uint32_t rows = last ? 2u * (uint32_t)p.wbl : (p.nblk > 1 ? 256u : (uint32_t)p.NC);
+        const uint32_t idesc = last ? p.idesc_last : p.idesc;
+        const uint32_t step16 = step >> 4;
+        const uint32_t part16 = PREC == MELT_BF16X3 ? step16 / 2 : 0u;  // lo part of a K-step block
+        const uint32_t blo_b = ((sbase + p.off_b) >> 4) | (((rows * 16u) >> 4) << 16);
+        for (int s0 = 0; s0 < p.KS && ok; s0 += p.kps) {
+          if (!mbar_wait(sbase + p.off_bar + 8 * (B.b_full + bslot), bphase, abort, p.err,
+                         kErrTimeout)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t blo0 = blo_b + bslot * bslot16;
+          const int n = min(p.kps, p.KS - s0);
+          for (int u = 0; u < n; ++u) {
+            const int s = s0 + u;
+            const uint2 t = tab[s];
+            const uint32_t blo = blo0 + u * step16;
+            const uint64_t ad = hi | (alo + t.x);
+            const uint64_t bd = hi | blo;
+            mma_f16(d, ad, bd, idesc, s > 0);
+            if constexpr (PREC == MELT_BF16X3) {
+              mma_f16(d, ad, hi | (blo + part16), idesc, 1);
+              mma_f16(d, hi | (alo + t.x + apart16), bd, idesc, 1);
+            }
+          }
+          mma_commit(sbase + p.off_bar + 8 * (B.b_empty + bslot));
+          if (++bslot == p.NB) {
+            bslot = 0;
+            bphase ^= 1;
           }
         }
-        mma_commit(sbase + p.off_bar + 8 * (B.b_empty + bslot));
-        if (++bslot == p.NB) {
-          bslot = 0;
-          bphase ^= 1;
-        }
       }
+      if (!ok) break;
+      mma_commit(sbase + p.off_bar + 8 * (B.t_full + acc));
     }
     if (!ok) break;
     mma_commit(sbase + p.off_bar + 8 * (B.z_empty + zb));
-    mma_commit(sbase + p.off_bar + 8 * (B.t_full + acc));
   }
   // no MMA may still be running when TMEM is released
   mma_commit(sbase + p.off_bar + 8 * B.drain);
@@ -557,67 +579,83 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
   const float* dct = reinterpret_cast<const float*>(gbase + p.off_dct);  // [n_mfcc][dct_ld]
   const bool vec8 = ((p.n_out & 7) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 31) == 0);
   const bool vec4 = ((p.n_out & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 15) == 0);
-  const int nch = p.MP >> 4;
-  int k = 0;
+  int k = 0, kb = 0;  // tile ordinal; accumulator-block ordinal (kb == k with one block)
   TileDesc td_next;
   if ((int)blockIdx.x < p.n_tiles) td_next = p.tiles[blockIdx.x];
   for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x, ++k) {
-    const int acc = k & 1;
     const TileDesc td = td_next;  // loaded one tile early
     if (tile + (int)gridDim.x < p.n_tiles) td_next = p.tiles[tile + gridDim.x];
-    if (!warp_wait(sbase + p.off_bar + 8 * (B.t_full + acc), (k >> 1) & 1, abort, p.err)) break;
-    tc_fence_after();
     const bool valid = row < td.n_frames;
-    const uint32_t t0 = tmem_base + ((uint32_t)(32 * warp) << 16) + acc * p.acc_stride;
     float* orow = p.out + (size_t)(td.out_row + row) * p.n_out;
     if constexpr (!MFCC) {
-      // groups of up to kEpiGroup 16-column chunks: all of a group's TMEM loads
-      // are issued before one wait; TMEM is released after the last group's wait
+      bool ok = true;
+      for (int b = 0; b < p.nblk; ++b, ++kb) {
+        const int acc = kb & 1;
+        if (!warp_wait(sbase + p.off_bar + 8 * (B.t_full + acc), (kb >> 1) & 1, abort, p.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // block b: Mel bins m0 .. m0 + wb - 1, R in columns [0, wb), I in [wb, 2 wb)
+        const int wb = b + 1 == p.nblk ? (p.nblk > 1 ? p.wbl : p.MP) : 128;
+        const int m0 = 128 * b;
+        const int nch = wb >> 4;
+        const uint32_t t0 = tmem_base + ((uint32_t)(32 * warp) << 16) + acc * p.acc_stride;
+        // groups of up to kEpiGroup 16-column chunks: all of a group's TMEM loads
+        // are issued before one wait; TMEM is released after the last group's wait
 #pragma unroll 1
-      for (int c0 = 0; c0 < nch; c0 += kEpiGroup) {
-        float re[kEpiGroup][16], im[kEpiGroup][16];
+        for (int c0 = 0; c0 < nch; c0 += kEpiGroup) {
+          float re[kEpiGroup][16], im[kEpiGroup][16];
 #pragma unroll
-        for (int g = 0; g < kEpiGroup; ++g) {
-          if (c0 + g < nch) {
-            tmem_ld16(t0 + 16 * (c0 + g), re[g]);
-            tmem_ld16(t0 + p.MP + 16 * (c0 + g), im[g]);
-          }
-        }
-        tmem_ld_wait();
-#pragma unroll
-        for (int g = 0; g < kEpiGroup; ++g) {
-          reg_fence16(re[g]);
-          reg_fence16(im[g]);
-        }
-        if (c0 + kEpiGroup >= nch) {
-          tc_fence_before();
-          warp_arrive(sbase + p.off_bar + 8 * (B.t_empty + acc));
-        }
-#pragma unroll
-        for (int g = 0; g < kEpiGroup; ++g) {
-          const int cc = c0 + g;
-          if (cc < nch) {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const float r = re[g][e], i = im[g][e];
-              re[g][e] = __logf(fmaf(r, r, fmaf(i, i, p.eps)));
+          for (int g = 0; g < kEpiGroup; ++g) {
+            if (c0 + g < nch) {
+              tmem_ld16(t0 + 16 * (c0 + g), re[g]);
+              tmem_ld16(t0 + wb + 16 * (c0 + g), im[g]);
             }
-            if (valid) {
-              if (vec8 && 16 * cc + 16 <= p.M) {
-                stg256(orow + 16 * cc, re[g]);
-                stg256(orow + 16 * cc + 8, re[g] + 8);
-              } else {
+          }
+          tmem_ld_wait();
 #pragma unroll
-                for (int e = 0; e < 16; ++e)
-                  if (16 * cc + e < p.M) orow[16 * cc + e] = re[g][e];
+          for (int g = 0; g < kEpiGroup; ++g) {
+            reg_fence16(re[g]);
+            reg_fence16(im[g]);
+          }
+          if (c0 + kEpiGroup >= nch) {
+            tc_fence_before();
+            warp_arrive(sbase + p.off_bar + 8 * (B.t_empty + acc));
+          }
+#pragma unroll
+          for (int g = 0; g < kEpiGroup; ++g) {
+            const int cc = c0 + g;
+            if (cc < nch) {
+#pragma unroll
+              for (int e = 0; e < 16; ++e) {
+                const float r = re[g][e], i = im[g][e];
+                re[g][e] = __logf(fmaf(r, r, fmaf(i, i, p.eps)));
+              }
+              const int m = m0 + 16 * cc;
+              if (valid) {
+                if (vec8 && m + 16 <= p.M) {
+                  stg256(orow + m, re[g]);
+                  stg256(orow + m + 8, re[g] + 8);
+                } else {
+#pragma unroll
+                  for (int e = 0; e < 16; ++e)
+                    if (m + e < p.M) orow[m + e] = re[g][e];
+                }
               }
             }
           }
         }
       }
+      if (!ok) break;
       continue;
     } else {
-      // MFCC: the frame's log-Mel row stays in registers; C[k] = sum_m lm[m] D[k][m]
+      // MFCC (one accumulator block): the frame's log-Mel row stays in
+      // registers; C[k] = sum_m lm[m] D[k][m]
+      const int acc = k & 1;
+      if (!warp_wait(sbase + p.off_bar + 8 * (B.t_full + acc), (k >> 1) & 1, abort, p.err)) break;
+      tc_fence_after();
+      const uint32_t t0 = tmem_base + ((uint32_t)(32 * warp) << 16) + acc * p.acc_stride;
       float lm[16 * NCH];
 #pragma unroll
       for (int c = 0; c < NCH; ++c) {

@@ -147,3 +147,20 @@ def test_precision_sweep_1024x10s(melt, levels, prec):
     print(prec, "levels_1024x10s (32 clips) vs FP64:",
           {k: (round(v[0], 6), round(v[1], 7)) for k, v in rep.items()})
     assert not check_form_tolerance(prec, rep), check_form_tolerance(prec, rep)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("n_mels", [144, 256, 400, 512])
+def test_more_than_128_mel_bins(melt, prec, n_mels):
+    """More than 128 Mel bins (the accumulator in blocks of 128 bins, the basis
+    streamed block by block): element by element against the rounded-operand
+    oracle, clips ending mid-tile included."""
+    clips = [G.rich_clip(33, i, L) for i, L in enumerate((30000, 128 * 160 + 240, 16000))]
+    _check(melt, prec, clips, n_mels=n_mels)
+
+
+def test_more_than_128_mel_bins_needs_bf16_log_mel(melt):
+    for kw in (dict(precision="fp32"), dict(precision="fp8"), dict(precision="bf16", n_mfcc=40)):
+        with pytest.raises(melt.MeltError) as ei:
+            melt.Frontend(n_mels=256, **kw)
+        assert ei.value.status == melt.MELT_ERR_UNSUPPORTED, kw
