@@ -406,6 +406,35 @@ def stft_mel_clip(x, spec: MelTSpec, scale: str = "htk", frames=None) -> np.ndar
     return np.log(P @ F.T + spec.eps)
 
 
+def stft_mel_clip_rounded(x, spec: MelTSpec, scale: str = "htk", precision: str = "fp64") -> np.ndarray:
+    """The conventional pipeline with the GEMM operands rounded as the fused
+    STFT+Mel comparator does: the DFT is the projection of the frames onto the
+    window-folded cos/sin rows (Eq. 5) at the uniform frequencies f_k = k sr/N,
+    k = 0..N/2, with the operand rounding of ``melt_clip_rounded``; then
+    |X_k|^2, the triangular Mel filterbank and log(. + eps), exactly.  With
+    precision "fp64" this is ``stft_mel_clip``."""
+    fk = np.arange(spec.n_fft // 2 + 1, dtype=np.float64) * spec.sr / spec.n_fft
+    Wr, Wi = dmp_weights(fk, spec.n_fft, spec.sr, spec.window)
+    W = np.concatenate([Wr, Wi], axis=0)
+    K = fk.shape[0]
+    X = frame_signal(x, spec.n_fft, spec.hop)
+    if precision == "fp64":
+        Y = X @ W.T
+    elif precision == "fp32":
+        Y = X @ f32(W).T
+    elif precision == "bf16":
+        Y = round_bf16(X) @ round_bf16(W).T
+    elif precision == "bf16x3":
+        xh, xl = split_bf16(X)
+        wh, wl = split_bf16(W)
+        Y = xh @ wh.T + xh @ wl.T + xl @ wh.T
+    else:
+        raise ValueError(precision)
+    P = dmp_energy(Y[:, :K], Y[:, K:])
+    F = triangular_filterbank(spec.n_mels, spec.n_fft, spec.sr, spec.fmin, spec.fmax, scale)
+    return np.log(P @ F.T + spec.eps)
+
+
 # --------------------------------------------------------------------------
 # Metrics (Sec. IV-F, Table "equiv_features"): cosine, Lin's CCC, RMSE in dB
 # --------------------------------------------------------------------------

@@ -458,3 +458,22 @@ def test_fp8_row_and_frame_scaling_agree_in_the_normal_range():
     x = (0.6 + 0.3 * np.sin(2 * math.pi * 440 * n / 16000.0)).astype(np.float32)   # all in [0.3, 0.9]
     np.testing.assert_allclose(O.melt_clip_rounded(x, spec, "fp8"), O.melt_clip_rounded(x, spec, "fp8_frame"),
                                rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("scale", ["htk", "slaney"])
+def test_rounded_stft_mel_reduces_to_the_pipeline_and_library_products(scale):
+    """The comparator's rounded-operand form: with no rounding it is the
+    conventional pipeline itself (window, |DFT|^2, filterbank, log); with BF16
+    it is torch's bfloat16 operands multiplied in float64."""
+    spec = O.MelTSpec(n_mels=40)
+    x = np.random.default_rng(23).standard_normal(400 + 5 * 160 + 7).astype(np.float32)
+    np.testing.assert_allclose(O.stft_mel_clip_rounded(x, spec, scale, "fp64"), O.stft_mel_clip(x, spec, scale),
+                               rtol=1e-11, atol=1e-10)
+    fk = np.arange(201) * 16000.0 / 400
+    Wr, Wi = O.dmp_weights(fk, 400, 16000.0, O.hann(400, True))
+    tb = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(torch.bfloat16).to(torch.float64)
+    X = O.frame_signal(x, 400, 160)
+    Y = (tb(X) @ tb(np.concatenate([Wr, Wi])).T).numpy()
+    F = O.triangular_filterbank(40, 400, 16000.0, 0.0, 8000.0, scale)
+    ref = np.log((Y[:, :201] ** 2 + Y[:, 201:] ** 2) @ F.T + spec.eps)
+    np.testing.assert_allclose(O.stft_mel_clip_rounded(x, spec, scale, "bf16"), ref, rtol=1e-12, atol=1e-12)
