@@ -875,6 +875,29 @@ def config_legs(args, dev, peaks):
     return out
 
 
+def time_fused_stft(W, dev, peaks):
+    """The fused STFT + triangular Mel comparator (melt_stft_create: tensor-core
+    DFT at N/2 + 1 bins, power, HTK filterbank and log in one kernel) on the
+    headline batch, BF16, beside the MelT headline and the torch.stft context."""
+    import torch
+    from paper_2606_01009_gb300 import melt
+    cfg = W.cfg
+    fe = melt.StftMelFrontend(sr=cfg["sr"], n_fft=cfg["n_fft"], hop=cfg["hop"], n_mels=cfg["n_mels"],
+                              fmin=cfg["fmin"], fmax=cfg["fmax"], precision="bf16", scale="htk")
+    T = fe.total_frames(W.lens)
+    waves, outs, copies = W.device_copies(fe.n_out, T)
+    ms = time_launches(lambda i: fe(waves[i % copies], W.offs, W.lens, out=outs[i % copies]), dev, 20)
+    fe.sync()
+    fe.close()
+    alg = algorithmic_bytes(W.lens, cfg["n_fft"], cfg["hop"], cfg["n_mels"])
+    bins = cfg["n_fft"] // 2 + 1
+    return {"pipeline": f"fused STFT ({bins} DFT bins, BF16 tensor cores) + |X|^2 + HTK triangular Mel + log, "
+                        "one kernel (melt_stft_create)",
+            "frames_per_step": T, "launch_us": ms * 1e3, "frames_per_s": T / (ms / 1e3),
+            "hbm_frac": alg / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+            "tensor_tflops": 2 * cfg["n_fft"] * 2 * bins * T / (ms / 1e3) / 1e12}
+
+
 def sweeps(args, dev):
     """Paper's scaling figures on synthetic clips: the batch sweep (1..256 clips
     of 4 s) and the Mel-count sweep (one 160 s clip, M = 40..512), MelT (BF16;
@@ -1010,6 +1033,13 @@ def main():
                     W, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
             except Exception as e:  # reported, not fatal: the headline line above stands
                 res["torch_stft_context"] = {"error": str(e)}
+        if args.stft:
+            import torch
+            try:
+                res["fused_stft_comparator"] = time_fused_stft(
+                    W, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))), load_peaks()[0])
+            except Exception as e:  # reported, not fatal
+                res["fused_stft_comparator"] = {"error": repr(e)}
         if args.configs:
             import torch
             try:

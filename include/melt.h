@@ -83,6 +83,8 @@ melt_status melt_basis_create(double sr, int n_fft, int hop, int n_mels, double 
  * melt_basis_create_ex - as melt_basis_create, plus:
  *   precision   melt_precision of the projection GEMM
  *   n_mfcc      K > 0 appends the DCT-II of Eq. 9 (K <= n_mels); 0 = log-Mel
+ * More than 128 Mel bins (up to 1024) are supported by MELT_BF16 and
+ * MELT_BF16X3 log-Mel bases only (MELT_ERR_UNSUPPORTED otherwise).
  *   eps         additive eps of Eq. 8 (>= 0)
  */
 melt_status melt_basis_create_ex(double sr, int n_fft, int hop, int n_mels, double fmin,
@@ -284,6 +286,36 @@ melt_status melt_forward_host(melt_basis* basis, const float* wave, const int64_
  */
 melt_status melt_pad_reflect(const float* wave, const int64_t* offsets, const int64_t* lengths,
                              int batch, int pad, float* out, const int64_t* out_offsets, void* stream);
+
+/*
+ * Conventional STFT + triangular Mel pipeline, fused into one kernel: the
+ * comparator the paper names as future work (Sec. "Threats to Validity",
+ * baseline and comparison fairness: a fused STFT+Mel kernel as a stronger
+ * conventional baseline), built from this library's own parts.
+ *
+ * melt_stft_create - a basis whose melt_forward computes, per frame,
+ *     out[m] = log( sum_k F[m][k] |X_k|^2 + eps ),   m < n_mels,
+ *   |X_k|^2 the power of the DFT of the windowed frame at the N/2 + 1 uniform
+ *   frequencies k sr / N (k = 0 .. N/2): the projection of Eq. 6 onto the
+ *   window-folded cos/sin rows at those frequencies, a tensor-core GEMM with
+ *   the power, the filterbank and the log fused in its epilogue.  F is the
+ *   triangular filterbank with n_mels bands on n_mels + 2 edges spaced
+ *   uniformly between fmin and fmax on the Mel scale chosen by `scale`:
+ *     0  HTK scale (Eq. 1), peak-1 triangles
+ *     1  Slaney scale (linear below 1 kHz, logarithmic above), triangles of
+ *        unit area (weights 2 / (edge[m+2] - edge[m]))
+ *   Band m rises from edge m to edge m+1 and falls to edge m+2.
+ *   sr, n_fft, hop, window, eps   as melt_basis_create_ex (N/2 + 1 <= 1024)
+ *   n_mels      bands, 1..512
+ *   precision   MELT_BF16 or MELT_BF16X3
+ *   out         receives the basis; melt_num_outputs(basis) = n_mels
+ * Framing, batching and the forward entry points (melt_forward and its
+ * variants) are those of any basis; a correction MLP cannot be attached.
+ * MELT_ERR_UNSUPPORTED for another precision or n_fft; MELT_ERR_ARG for a
+ * bad parameter.
+ */
+melt_status melt_stft_create(double sr, int n_fft, int hop, int n_mels, double fmin, double fmax, int window,
+                             int precision, int scale, double eps, melt_basis** out);
 
 /*
  * melt_forward_components - debug form: the raw projection (Eq. 6) for every

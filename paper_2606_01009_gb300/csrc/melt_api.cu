@@ -25,6 +25,7 @@ using namespace melt;
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxFreqs = 1024;  // analysis frequencies of a basis (BF16 forms above 128)
 constexpr int kStagingSlots = 4;
 
 // ---- Eq. 1 and Eq. 2: HTK Mel map and its inverse
@@ -63,6 +64,10 @@ struct melt_basis {
   std::vector<TileDesc> plan;  // host scratch for planning
   int64_t plan_rows = 0;       // output rows of the planned batch
   const melt_mlp* correction = nullptr;  // applied in place after the log-Mel (not owned)
+  // fused STFT + triangular Mel comparator (melt_stft_create): bands per frame
+  // and, per DFT bin, {weight of band b0, weight of band b0 + 1, b0 as int bits, 0}
+  int stft_bands = 0;
+  float4* d_fb = nullptr;
   HostPipe* host_pipe = nullptr;         // melt_forward_host buffers and streams
 };
 
@@ -86,6 +91,7 @@ void free_basis(melt_basis* b) {
   cudaFree(b->d_w32);
   cudaFree(b->d_dct);
   cudaFree(b->d_err);
+  cudaFree(b->d_fb);
   tc_free(&b->tc);
   for (auto& s : b->staging) {
     if (s.done) cudaEventSynchronize(s.done), cudaEventDestroy(s.done);
@@ -154,15 +160,15 @@ melt_status check_device(int* dev, int* sms) {
 
 melt_status create_common(double sr, int n_fft, int hop, const double* freqs, int n_freqs,
                           double fmin, double fmax, int window, int precision, int n_mfcc,
-                          double eps, melt_basis** out) {
+                          double eps, melt_basis** out, int stft_bands = 0) {
   if (!out) return MELT_ERR_ARG;
   *out = nullptr;
   // more than 128 frequencies: BF16 forms only, log-Mel (the kernels' blocks of 128 bins)
-  if (n_freqs > 128 && (precision == MELT_FP32 || precision == MELT_FP8E4M3 || n_mfcc > 0) && n_freqs <= 512 &&
+  if (n_freqs > 128 && (precision == MELT_FP32 || precision == MELT_FP8E4M3 || n_mfcc > 0) && n_freqs <= kMaxFreqs &&
       sr > 0 && n_fft >= 16)
     return MELT_ERR_UNSUPPORTED;
   if (!(sr > 0) || n_fft < 16 || n_fft > 4096 || (n_fft & 3) || hop < 1 || hop > n_fft ||
-      (hop & 3) || n_freqs < 1 || n_freqs > 512 || n_mfcc < 0 || n_mfcc > n_freqs ||
+      (hop & 3) || n_freqs < 1 || n_freqs > kMaxFreqs || n_mfcc < 0 || n_mfcc > n_freqs ||
       !(eps >= 0) || (window != MELT_WIN_HANN_PERIODIC && window != MELT_WIN_HANN_SYMMETRIC) ||
       precision < MELT_FP32 || precision > MELT_FP8E4M3)
     return MELT_ERR_ARG;
@@ -184,7 +190,7 @@ melt_status create_common(double sr, int n_fft, int hop, const double* freqs, in
   if (st == MELT_OK) st = upload_dct(b);
   if (st == MELT_OK && precision != MELT_FP32 && n_mfcc > tc_max_mfcc()) st = MELT_ERR_UNSUPPORTED;
   if (st == MELT_OK && precision != MELT_FP32) {
-    TcConfig c{n_fft, hop, n_freqs, precision, n_mfcc};
+    TcConfig c{n_fft, hop, n_freqs, precision, n_mfcc, stft_bands};
     st = tc_build(&b->tc, c, b->w64.data());
   }
   if (st == MELT_OK) {
@@ -312,6 +318,8 @@ melt_status forward_impl(melt_basis* b, const float* wave, const int64_t* offset
     L.sm_count = b->sm_count;
     L.mlp = mode == 0 ? b->correction : nullptr;
     L.fused = &fused;
+    L.fb = b->d_fb;
+    L.stft_bands = b->stft_bands;
     e = tc_launch(&b->tc, L, stream);
   }
   if (e != cudaSuccess) return cuda_status(e);
@@ -395,6 +403,8 @@ melt_status launch_forward_tiles(melt_basis* b, const float* wave, const TileDes
     L.sm_count = b->sm_count;
     L.mlp = b->correction;
     L.fused = &fused;
+    L.fb = b->d_fb;
+    L.stft_bands = b->stft_bands;
     e = tc_launch(&b->tc, L, stream);
   }
   if (e != cudaSuccess) return cuda_status(e);
@@ -410,6 +420,61 @@ HostPipe*& basis_host_pipe(melt_basis* b) { return b->host_pipe; }
 
 }  // namespace melt
 
+namespace {
+
+// HTK Mel scale (Eq. 1) and the Slaney scale (linear, 200/3 Hz per mel, below
+// 1 kHz; logarithmic, ln(6.4)/27 per mel, above), and their inverses.
+double slaney_mel(double f) {
+  const double logstep = std::log(6.4) / 27.0;
+  return f >= 1000.0 ? 15.0 + std::log(f / 1000.0) / logstep : f / (200.0 / 3.0);
+}
+double slaney_hz(double m) {
+  const double logstep = std::log(6.4) / 27.0;
+  return m >= 15.0 ? 1000.0 * std::exp(logstep * (m - 15.0)) : m * (200.0 / 3.0);
+}
+
+// Per DFT bin k (frequency k sr / N): the bin lies between edges e[i] and
+// e[i+1] of the n_bands + 2 filterbank edges, in the falling side of band i-1
+// (weight (e[i+1] - f) / (e[i+1] - e[i])) and the rising side of band i
+// (weight (f - e[i]) / (e[i+1] - e[i])); bands past either end get weight 0.
+// Entry {w(band i-1), w(band i), i-1 as int bits, 0}; a bin outside [e[0],
+// e[n_bands+1]] gets band index -2 (no band).
+std::vector<float4> stft_filterbank(double sr, int n_fft, int n_bands, double fmin, double fmax, int scale) {
+  std::vector<double> e(n_bands + 2);
+  const double lo = scale ? slaney_mel(fmin) : hz_to_mel(fmin), hi = scale ? slaney_mel(fmax) : hz_to_mel(fmax);
+  for (int i = 0; i < n_bands + 2; ++i) {
+    const double mu = lo + (hi - lo) * i / (n_bands + 1);
+    e[i] = scale ? slaney_hz(mu) : mel_to_hz(mu);
+  }
+  const int K = n_fft / 2 + 1;
+  std::vector<float4> fb(K);
+  for (int k = 0; k < K; ++k) {
+    const double f = (double)k * sr / n_fft;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    int b0 = -2;
+    if (f >= e[0] && f <= e[n_bands + 1]) {
+      int i = 0;
+      while (i < n_bands && f >= e[i + 1]) ++i;  // e[i] <= f < e[i+1] (or the last interval)
+      const double span = e[i + 1] - e[i];
+      double wfall = span > 0 ? (e[i + 1] - f) / span : 0.0, wrise = span > 0 ? (f - e[i]) / span : 0.0;
+      wfall = std::max(0.0, wfall);
+      wrise = std::max(0.0, wrise);
+      if (scale) {  // unit area: band j scaled by 2 / (e[j+2] - e[j])
+        if (i >= 1) wfall *= 2.0 / (e[i + 1] - e[i - 1]);
+        if (i < n_bands) wrise *= 2.0 / (e[i + 2] - e[i]);
+      }
+      v.x = i >= 1 ? (float)wfall : 0.f;
+      v.y = i < n_bands ? (float)wrise : 0.f;
+      b0 = i - 1;
+    }
+    std::memcpy(&v.z, &b0, sizeof(float));  // the band index's int bits
+    fb[k] = v;
+  }
+  return fb;
+}
+
+}  // namespace
+
 extern "C" {
 
 melt_status melt_basis_create(double sr, int n_fft, int hop, int n_mels, double fmin,
@@ -423,7 +488,7 @@ melt_status melt_basis_create_ex(double sr, int n_fft, int hop, int n_mels, doub
                                  double eps, melt_basis** out) {
   if (!out) return MELT_ERR_ARG;
   *out = nullptr;
-  if (n_mels < 1 || n_mels > 512 || !(sr > 0) || !(fmin >= 0) || !(fmax > fmin) ||
+  if (n_mels < 1 || n_mels > kMaxFreqs || !(sr > 0) || !(fmin >= 0) || !(fmax > fmin) ||
       !(fmax <= sr / 2))
     return MELT_ERR_ARG;
   // M interior points of M+2 points uniform on the Mel scale (Sec. III-A)
@@ -443,6 +508,35 @@ melt_status melt_basis_create_freqs(double sr, int n_fft, int hop, const double*
                        eps, out);
 }
 
+melt_status melt_stft_create(double sr, int n_fft, int hop, int n_mels, double fmin, double fmax, int window,
+                             int precision, int scale, double eps, melt_basis** out) {
+  if (!out) return MELT_ERR_ARG;
+  *out = nullptr;
+  if (n_mels < 1 || n_mels > 512 || !(sr > 0) || !(fmin >= 0) || !(fmax > fmin) || !(fmax <= sr / 2) ||
+      (scale != 0 && scale != 1) || n_fft < 16 || n_fft > 4096)
+    return MELT_ERR_ARG;
+  if ((precision != MELT_BF16 && precision != MELT_BF16X3) || n_fft / 2 + 1 > kMaxFreqs) return MELT_ERR_UNSUPPORTED;
+  const int K = n_fft / 2 + 1;
+  std::vector<double> f(K);
+  for (int k = 0; k < K; ++k) f[k] = (double)k * sr / n_fft;
+  // the projection needs more than 128 frequencies: the blocked BF16 path
+  melt_basis* b = nullptr;
+  melt_status st = create_common(sr, n_fft, hop, f.data(), K, 0.0, sr / 2, window, precision, 0, eps, &b, n_mels);
+  if (st != MELT_OK) return st;
+  b->fmin = fmin;
+  b->fmax = fmax;
+  const std::vector<float4> fb = stft_filterbank(sr, n_fft, n_mels, fmin, fmax, scale);
+  cudaError_t e = melt::dev_alloc(&b->d_fb, fb.size() * sizeof(float4));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_fb, fb.data(), fb.size() * sizeof(float4), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_basis(b);
+    return cuda_status(e);
+  }
+  b->stft_bands = n_mels;
+  *out = b;
+  return MELT_OK;
+}
+
 int64_t melt_num_frames(const melt_basis* basis, int64_t length) {
   if (!basis) return 0;
   return frames_of(basis, length);
@@ -450,6 +544,7 @@ int64_t melt_num_frames(const melt_basis* basis, int64_t length) {
 
 int melt_num_outputs(const melt_basis* basis) {
   if (!basis) return 0;
+  if (basis->stft_bands) return basis->stft_bands;
   return basis->n_mfcc ? basis->n_mfcc : basis->n_mels;
 }
 
@@ -554,7 +649,7 @@ melt_status melt_autotune(melt_basis* b, const float* wave, const int64_t* offse
 melt_status melt_basis_set_correction(melt_basis* b, const melt_mlp* mlp) {
   if (!b) return MELT_ERR_ARG;
   if (mlp) {
-    if (b->n_mfcc != 0) return MELT_ERR_UNSUPPORTED;  // the correction acts on log-Mel bands
+    if (b->n_mfcc != 0 || b->stft_bands) return MELT_ERR_UNSUPPORTED;  // the correction acts on MelT log-Mel bands
     if (mlp_inputs(mlp) != b->n_mels || mlp_device(mlp) != b->device) return MELT_ERR_ARG;
   }
   // the BF16 image for the fused epilogue is allocated here, so that forward

@@ -142,6 +142,8 @@ bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) 
   off += 128;
   p.off_dct = off;
   off += align_up(4 * ((n_mfcc + 3) & ~3) * p.MP, 128);
+  p.off_fb = off;  // fused STFT + Mel comparator: one 16-byte filterbank entry per DFT bin
+  off += tb->stft_bands > 0 ? align_up(16u * (uint32_t)p.MP, 128) : 0u;
   if (off + 128 > kSmemLimit) return false;
   p.smem_total = off + 128;
   p.tmem_cols = p.NC <= 32 ? 64 : p.NC <= 64 ? 128 : p.NC <= 128 ? 256 : 512;
@@ -157,7 +159,8 @@ bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) 
 // takes every slot that still fits (2..8).
 bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) {
   const bool fp8 = tb->precision == MELT_FP8E4M3;
-  if (c.cta_pair != 1 || (tb->precision != MELT_BF16 && !fp8) || !tb->d_b2 || p.nblk > 1) return false;
+  if (c.cta_pair != 1 || (tb->precision != MELT_BF16 && !fp8) || !tb->d_b2 || p.nblk > 1 || tb->stft_bands > 0)
+    return false;
   // FP8: a converter lane holds at most two quads of a Z row
   if (fp8 && p.H > 256) return false;
   if (c.basis_resident != 1 || c.a_buffers < 1 || c.a_buffers > 2) return false;
@@ -322,8 +325,8 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
   const int N = c.n_fft, H = c.hop, M = c.n_mels, P = c.precision;
   if (P != MELT_BF16 && P != MELT_BF16X3 && P != MELT_FP8E4M3) return MELT_ERR_ARG;
   if (P != MELT_FP8E4M3 && (H % 16) != 0) return MELT_ERR_UNSUPPORTED;
-  // M > 128 (up to 512): BF16 forms only, as blocks of 128 Mel bins (FP8 runs in CTA pairs, M <= 128)
-  if (M > 512 || (M > 128 && P == MELT_FP8E4M3)) return MELT_ERR_UNSUPPORTED;
+  // M > 128 (up to 1024): BF16 forms only, as blocks of 128 Mel bins (FP8 runs in CTA pairs, M <= 128)
+  if (M > 1024 || (M > 128 && P == MELT_FP8E4M3)) return MELT_ERR_UNSUPPORTED;
   if (M > 128 && c.n_mfcc > 0) return MELT_ERR_UNSUPPORTED;
   const int MP = (M + 15) / 16 * 16, NC = 2 * MP;
   const int nblk = (MP + 127) / 128;
@@ -397,6 +400,7 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
   tb->n_cols = NC;
   tb->kstep_bytes = kstep_bytes;
   tb->n_mfcc = c.n_mfcc;
+  tb->stft_bands = c.stft_bands;
   if (P != MELT_FP8E4M3) {  // the single-CTA image (FP8 runs in CTA pairs only)
     if (melt::dev_alloc(&tb->d_b, img.size()) != cudaSuccess) return MELT_ERR_OOM;
     if (cudaMemcpy(tb->d_b, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -498,7 +502,9 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
   p.err = L.err;
   p.eps = L.eps;
   p.n_mfcc = L.n_mfcc;
-  p.n_out = L.n_mfcc ? L.n_mfcc : tb->n_mels;
+  p.n_out = L.stft_bands ? L.stft_bands : L.n_mfcc ? L.n_mfcc : tb->n_mels;
+  p.fb = L.fb;
+  p.stft_bands = L.stft_bands;
   const bool fused = pair && p.Hd > 0 && L.mlp != nullptr;
   if (pair && p.Hd > 0 && !L.mlp) p.Hd = 0;  // plan made for a correction that is not passed
   KernelFn fn = fused ? kernel_for_pair_mlp(p.MP / 16)

@@ -10,6 +10,7 @@ namespace melt {
 
 struct TcConfig {
   int n_fft, hop, n_mels, precision, n_mfcc;
+  int stft_bands;  // > 0: the fused STFT + Mel comparator's epilogue (n_mels = DFT bins)
 };
 
 // Device-resident operand images of one basis for the tensor-core kernels.
@@ -24,6 +25,7 @@ struct TcBasis {
   void* d_b = nullptr;     // B operand blocks, one per K-step (BF16x3: hi and lo parts)
   void* d_b2 = nullptr;    // BF16 CTA-pair image: W_r rows' blocks, then W_i rows' blocks
   int n_mfcc = 0;
+  int stft_bands = 0;      // fused STFT + Mel comparator: bands per frame (its table sits in shared memory)
   int pair_clusters = -1;  // co-resident 2-CTA clusters of the pair kernel (-1: not queried)
   int pair_smem = 0;       // shared memory size that count was queried for
   // correction MLP fused in the CTA-pair kernel's epilogue (0 hidden units: none)
@@ -56,6 +58,8 @@ struct TcLaunch {
   int sm_count;
   bool pdl = true;    // launch with programmatic stream serialisation
   const melt_mlp* mlp = nullptr;  // correction attached to the basis (fused when the layout allows)
+  const float4* fb = nullptr;     // fused STFT + Mel comparator: per-bin filterbank entries (device)
+  int stft_bands = 0;
   bool* fused = nullptr;          // out: true when the kernel applied `mlp` itself
 };
 

@@ -99,6 +99,13 @@ struct TcParams {
   // tile's blocks alternate between the two accumulators.  nblk = 1 otherwise.
   int nblk, wbl;
   uint32_t idesc_last, blk_step, blk_step_last;
+  // Fused STFT + Mel comparator (stft_bands > 0; the M analysis frequencies
+  // are the DFT bins k sr / N): per bin k the filterbank entry {weight of band
+  // b0, weight of band b0 + 1, b0 as int bits (-2: no band), 0}, copied to
+  // shared memory at off_fb; the epilogue writes stft_bands values per frame.
+  const float4* fb;
+  int stft_bands;
+  uint32_t off_fb;
   uint32_t desc_hi;      // high word of every operand descriptor (SBO = 128 B, version)
   uint32_t off_a, off_b, off_bar, off_misc, off_tab, off_dct;
   uint32_t smem_total;   // dynamic shared memory bytes (incl. alignment slack)
@@ -571,6 +578,33 @@ static __device__ __forceinline__ void fill_dct(const TcParams& p, float* dct, i
   }
 }
 
+// Fused STFT + Mel comparator, epilogue state of one frame: the bands run in
+// order; acc0 holds band c, acc1 band c + 1.  A bin k adds w0 |X_k|^2 to band
+// b0(k) and w1 |X_k|^2 to band b0(k) + 1 (b0 is the same for every frame, so
+// the control flow is uniform); bands below b0(k) are complete and are
+// written (log(E + eps)) as c moves up to b0(k).
+struct StftBands {
+  float acc0, acc1;
+  int c;
+};
+
+static __device__ __forceinline__ void stft_flush(StftBands& st, float* orow, int nb, float eps, bool valid) {
+  if (valid && st.c >= 0 && st.c < nb) orow[st.c] = __logf(st.acc0 + eps);
+  st.acc0 = st.acc1;
+  st.acc1 = 0.f;
+  ++st.c;
+}
+
+static __device__ __forceinline__ void stft_bin(StftBands& st, const float4* fbs, int k, float s2, float* orow,
+                                                int nb, float eps, bool valid) {
+  const float4 f = fbs[k];
+  const int b0 = __float_as_int(f.z);
+  if (b0 < -1) return;  // outside every triangle
+  while (st.c < b0) stft_flush(st, orow, nb, eps, valid);
+  st.acc0 = fmaf(f.x, s2, st.acc0);
+  st.acc1 = fmaf(f.y, s2, st.acc1);
+}
+
 template <int PREC, int NCH, bool MFCC>
 __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase, const Bars& B,
                               uint32_t tmem_base, volatile int* abort) {
@@ -589,6 +623,7 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
     float* orow = p.out + (size_t)(td.out_row + row) * p.n_out;
     if constexpr (!MFCC) {
       bool ok = true;
+      StftBands stb{0.f, 0.f, -1};  // fused STFT + Mel comparator: no band started yet
       for (int b = 0; b < p.nblk; ++b, ++kb) {
         const int acc = kb & 1;
         if (!warp_wait(sbase + p.off_bar + 8 * (B.t_full + acc), (kb >> 1) & 1, abort, p.err)) {
@@ -623,6 +658,24 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
             tc_fence_before();
             warp_arrive(sbase + p.off_bar + 8 * (B.t_empty + acc));
           }
+          if (p.stft_bands) {
+            // the comparator: |X_k|^2 of DFT bin k into the triangular bands, in bin order
+            const float4* fbs = reinterpret_cast<const float4*>(gbase + p.off_fb);
+#pragma unroll
+            for (int g = 0; g < kEpiGroup; ++g) {
+              const int cc = c0 + g;
+              if (cc < nch) {
+#pragma unroll 4
+                for (int e = 0; e < 16; ++e) {
+                  const int kbin = m0 + 16 * cc + e;
+                  if (kbin < p.M)
+                    stft_bin(stb, fbs, kbin, fmaf(re[g][e], re[g][e], im[g][e] * im[g][e]), orow, p.stft_bands,
+                             p.eps, valid);
+                }
+              }
+            }
+            continue;
+          }
 #pragma unroll
           for (int g = 0; g < kEpiGroup; ++g) {
             const int cc = c0 + g;
@@ -648,6 +701,8 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
         }
       }
       if (!ok) break;
+      if (p.stft_bands)
+        while (stb.c < p.stft_bands) stft_flush(stb, orow, p.stft_bands, p.eps, valid);
       continue;
     } else {
       // MFCC (one accumulator block): the frame's log-Mel row stays in
@@ -725,6 +780,10 @@ __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_const
   if (warp == kMmaWarp) {
     tmem_alloc(smem_u32(tmem_slot), p.tmem_cols);
     tmem_relinquish();
+  }
+  if (p.stft_bands > 0 && warp < kEpiWarps) {  // the comparator's filterbank table
+    float4* fbs = reinterpret_cast<float4*>(gbase + p.off_fb);
+    for (int i = threadIdx.x; i < p.M; i += kEpiThreads) fbs[i] = p.fb[i];
   }
   if constexpr (MFCC) {
     // DCT-II rows padded with zeros to MP columns (16-byte aligned rows)

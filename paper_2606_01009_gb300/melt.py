@@ -51,6 +51,8 @@ SIGNATURES = {
     "melt_basis_info": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "melt_basis_get_fp64": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "melt_forward": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
+    "melt_stft_create": (C.c_int, [C.c_double, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
+                                   C.c_int, C.c_int, C.c_double, C.POINTER(_VP)]),
     "melt_forward_components": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
     "melt_forward_noalloc": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
     "melt_forward_host": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
@@ -163,6 +165,15 @@ def melt_basis_create_freqs(sr, n_fft, hop, freqs, window=MELT_WIN_HANN_PERIODIC
     _check(lib.melt_basis_create_freqs(sr, n_fft, hop, f.ctypes.data_as(C.POINTER(C.c_double)),
                                        int(f.shape[0]), window, precision, n_mfcc, eps,
                                        C.byref(h)), "melt_basis_create_freqs")
+    return h
+
+
+def melt_stft_create(sr, n_fft, hop, n_mels, fmin, fmax, window=MELT_WIN_HANN_PERIODIC, precision=MELT_BF16,
+                     scale=0, eps=1e-10):
+    """The fused STFT + triangular Mel comparator (scale 0: HTK peak-1, 1: Slaney area)."""
+    h = C.c_void_p()
+    _check(lib.melt_stft_create(sr, n_fft, hop, n_mels, fmin, fmax, window, precision, scale, eps, C.byref(h)),
+           "melt_stft_create")
     return h
 
 
@@ -489,6 +500,22 @@ class Frontend:
             self.close()
         except Exception:
             pass
+
+
+class StftMelFrontend(Frontend):
+    """Owns a fused STFT + triangular Mel comparator basis (melt_stft_create):
+    log(F |DFT|^2 + eps) per frame, n_mels bands; same call interface as
+    Frontend.  ``scale`` is "htk" (peak-1 triangles) or "slaney" (unit area)."""
+
+    def __init__(self, sr=16000.0, n_fft=400, hop=160, n_mels=80, fmin=0.0, fmax=8000.0,
+                 window=MELT_WIN_HANN_PERIODIC, precision="bf16", scale="htk", eps=1e-10):
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        sc = {"htk": 0, "slaney": 1}[scale] if isinstance(scale, str) else int(scale)
+        self.handle = melt_stft_create(sr, n_fft, hop, n_mels, fmin, fmax, window, p, sc, eps)
+        self.n_out = melt_num_outputs(self.handle)
+        self.center = False
+        self.pad = 0
+        self._pad_buf = None
 
 
 class GroupedFrontend:
