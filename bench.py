@@ -110,6 +110,9 @@ def parse():
                     help="also time the M = 128 and MFCC variants and the 1024 x 10 s precision sweep")
     ap.add_argument("--sweeps", action=argparse.BooleanOptionalAction, default=True,
                     help="also run the batch sweep (4 s clips) and the Mel-count sweep (160 s clip)")
+    ap.add_argument("--plan-cache", default=os.environ.get("MELT_AUTOTUNE_CACHE",
+                                                           os.path.join(tempfile.gettempdir(), "melt_plans.txt")),
+                    help="on-disk plan cache of melt_group_autotune (grouped leg)")
     ap.add_argument("--energy", action=argparse.BooleanOptionalAction, default=True,
                     help="also measure J per frame with NVML's total-energy counter")
     return ap.parse_args()
@@ -587,6 +590,17 @@ def time_grouped(args, dev, steps=20, warmup=3, per_clip_steps=2):
         torch.cuda.synchronize(dev)
         return a.elapsed_time(b) / k
 
+    # default plans, then the plans melt_group_autotune picks by timing this
+    # grouped launch (kept in the on-disk plan cache for later processes)
+    gf = melt.GroupedFrontend(fes, graphs=True)
+    ms = timed(lambda: gf(wave, pk.offsets, pk.lengths, ids, out=out, stream=stream), steps, warmup)
+    res["grouped_graph_default_plans"] = {"ms_per_step": ms, "frames_per_s": T / (ms / 1e3),
+                                          "plans": [melt.melt_plan_get(fe.handle) for fe in fes]}
+    t0 = time.perf_counter()
+    plans, hit = gf.autotune(wave, pk.offsets, pk.lengths, ids, out, path=args.plan_cache, stream=stream)
+    res["autotune"] = {"plans": plans, "cache_hit": hit, "seconds": round(time.perf_counter() - t0, 3),
+                       "plan_cache": args.plan_cache}
+    gf.close()
     for name, graphs in (("grouped_graph", True), ("grouped_direct", False)):
         gf = melt.GroupedFrontend(fes, graphs=graphs)
         ms = timed(lambda: gf(wave, pk.offsets, pk.lengths, ids, out=out, stream=stream), steps, warmup)

@@ -182,6 +182,25 @@ melt_status melt_autotune(melt_basis* basis, const float* wave, const int64_t* o
                           melt_plan* best);
 
 /*
+ * melt_autotune_file - melt_autotune with a plan cache on disk, so that a
+ *   process tunes a configuration once and later processes reuse the plan.
+ *   The file at `path` (text, one line per tuned configuration, created if
+ *   missing) is read first.  A line for this GPU (by name), this basis
+ *   configuration (n_fft, hop, frequency count, precision, n_mfcc, fused
+ *   correction's hidden units, comparator bands) and this batch size class
+ *   (log2 of the batch's tile count) that still fits the device sets its plan
+ *   without timing (*hit = 1).  Otherwise melt_autotune runs (arguments as
+ *   there) and its plan is appended as one line (*hit = 0).  The plan in
+ *   effect is returned in *best.  `best` and `hit` may be NULL.
+ *   Errors: those of melt_autotune; MELT_ERR_ARG for a NULL path;
+ *   MELT_ERR_CUDA if the device name cannot be read.  A file that cannot be
+ *   written only skips the append.
+ */
+melt_status melt_autotune_file(melt_basis* basis, const float* wave, const int64_t* offsets,
+                               const int64_t* lengths, int batch, float* out, void* stream, int reps,
+                               const char* path, melt_plan* best, int* hit);
+
+/*
  * melt_forward - MelT (Eq. 8) or MFCCT (Eq. 9) features of a batch of clips.
  *   wave     device float[]: clip b occupies wave[offsets[b] .. offsets[b]+lengths[b]);
  *            the whole 4-float-aligned span [offsets[b], offsets[b]+round_up(lengths[b],4))
@@ -368,6 +387,31 @@ melt_status melt_group_create(melt_basis* const* bases, int n_bases, int flags, 
 melt_status melt_forward_grouped(melt_group* group, const float* wave, const int64_t* offsets,
                                  const int64_t* lengths, const int32_t* basis_of, int batch,
                                  float* out, void* stream);
+
+/*
+ * melt_group_autotune - layout plans for the bases of a group, chosen by
+ *   timing melt_forward_grouped's launches on the given batch (arguments as
+ *   there), so that each basis is tuned as it runs beside the others.  The
+ *   bases are tuned one at a time: each of a basis's candidate plans is set
+ *   (melt_plan_set), the whole grouped launch runs once as warm-up and then
+ *   `reps` times under events, and the fastest candidate stays set before
+ *   the next basis is tuned.  FP32 bases have no plans and keep theirs.
+ *   The plans stay set on the bases (as melt_plan_set leaves them), and the
+ *   group's cached work lists and graphs are dropped, so the next
+ *   melt_forward_grouped captures the tuned launches.
+ *   path   plan cache file (text, created if missing) or NULL.  A line for this
+ *          GPU (by name), these basis configurations and the size class of each
+ *          basis's share of the batch (floor(log2) of its tile count) sets its
+ *          plans without timing (*hit = 1); after tuning, one line is appended.
+ *          A file that cannot be written only skips the append.
+ *   hit    may be NULL.
+ *   Writes `out` (as the forward would), synchronises `stream`.  Not for use
+ *   inside stream capture.  Errors: those of melt_forward_grouped;
+ *   MELT_ERR_ARG for reps < 1.
+ */
+melt_status melt_group_autotune(melt_group* group, const float* wave, const int64_t* offsets,
+                                const int64_t* lengths, const int32_t* basis_of, int batch, float* out,
+                                void* stream, int reps, const char* path, int* hit);
 
 /* melt_group_sync - melt_sync of every basis of the group; first error wins. */
 melt_status melt_group_sync(melt_group* group, void* stream);

@@ -416,6 +416,69 @@ int basis_device(const melt_basis* b) { return b->device; }
 
 const melt_mlp* basis_correction(const melt_basis* b) { return b->correction; }
 
+int basis_plan_candidates(const melt_basis* b, melt_plan* out, int cap) {
+  if (b->precision == MELT_FP32) return 0;
+  return tc_candidates(&b->tc, out, cap);
+}
+
+bool device_token(int device, char* buf, size_t n) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return false;
+  std::snprintf(buf, n, "%s", prop.name);
+  for (char* ch = buf; *ch; ++ch)
+    if (*ch == ' ' || *ch == '\t' || *ch == ':') *ch = '_';
+  return true;
+}
+
+void basis_plan_key(const melt_basis* b, char* buf, size_t n) {
+  std::snprintf(buf, n, "%d %d %d %d %d %d %d", b->n_fft, b->hop, b->n_mels, b->precision, b->n_mfcc,
+                b->correction ? mlp_hidden(b->correction) : 0, b->stft_bands);
+}
+
+int tile_class(long long tiles) {
+  int c = 0;
+  while (c < 62 && (1ll << (c + 1)) <= tiles) ++c;
+  return c;
+}
+
+int format_plan(const melt_plan& p, char* buf, size_t n) {
+  return std::snprintf(buf, n, "%d %d %d %d %d %d %d", p.basis_resident, p.a_buffers, p.prefetch_tiles,
+                       p.basis_slots, p.ksteps_per_slot, p.cta_pair, p.schedule);
+}
+
+bool parse_plan(const char* s, melt_plan* p, int* used) {
+  int k = 0;
+  if (std::sscanf(s, " %d %d %d %d %d %d %d%n", &p->basis_resident, &p->a_buffers, &p->prefetch_tiles,
+                  &p->basis_slots, &p->ksteps_per_slot, &p->cta_pair, &p->schedule, &k) != 7)
+    return false;
+  *used = k;
+  return true;
+}
+
+bool cache_lookup(const char* path, const char* key, char* rest, size_t n) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[2048];
+  const size_t kl = std::strlen(key);
+  bool found = false;
+  while (!found && std::fgets(line, sizeof(line), f)) {
+    if (std::strncmp(line, key, kl) != 0 || std::strncmp(line + kl, " : ", 3) != 0) continue;
+    std::snprintf(rest, n, "%s", line + kl + 3);
+    found = true;
+  }
+  std::fclose(f);
+  return found;
+}
+
+void cache_append(const char* path, const char* key, const char* rest) {
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  char line[2048];
+  const int k = std::snprintf(line, sizeof(line), "%s : %s\n", key, rest);
+  if (k > 0 && (size_t)k < sizeof(line)) std::fwrite(line, 1, (size_t)k, f);  // one write: appends stay whole lines
+  std::fclose(f);
+}
+
 HostPipe*& basis_host_pipe(melt_basis* b) { return b->host_pipe; }
 
 }  // namespace melt
@@ -643,6 +706,35 @@ melt_status melt_autotune(melt_basis* b, const float* wave, const int64_t* offse
   b->tc.plan = cands[best_i];
   b->tc.forced = true;
   if (best) *best = cands[best_i];
+  return MELT_OK;
+}
+
+melt_status melt_autotune_file(melt_basis* b, const float* wave, const int64_t* offsets,
+                               const int64_t* lengths, int batch, float* out, void* stream_v, int reps,
+                               const char* path, melt_plan* best, int* hit) {
+  if (hit) *hit = 0;
+  if (!b || !path || reps < 1 || batch < 0 || (batch > 0 && !lengths)) return MELT_ERR_ARG;
+  if (b->precision == MELT_FP32) return MELT_ERR_UNSUPPORTED;
+  char gpu[256], cfg[160], key[512], rest[256];
+  if (!device_token(b->device, gpu, sizeof(gpu))) return MELT_ERR_CUDA;
+  basis_plan_key(b, cfg, sizeof(cfg));
+  long long tiles = 0;
+  for (int c = 0; c < batch; ++c) tiles += (frames_of(b, lengths[c]) + kTileFrames - 1) / kTileFrames;
+  std::snprintf(key, sizeof(key), "melt-plan-v1 %s %s %d", gpu, cfg, tile_class(tiles));
+  melt_plan pl;
+  int used = 0;
+  if (cache_lookup(path, key, rest, sizeof(rest)) && parse_plan(rest, &pl, &used) && tc_plan_fits(&b->tc, pl)) {
+    b->tc.plan = pl;
+    b->tc.forced = true;
+    if (best) *best = pl;
+    if (hit) *hit = 1;
+    return MELT_OK;
+  }
+  const melt_status st = melt_autotune(b, wave, offsets, lengths, batch, out, stream_v, reps, &pl);
+  if (st != MELT_OK) return st;
+  if (best) *best = pl;
+  format_plan(pl, rest, sizeof(rest));
+  cache_append(path, key, rest);
   return MELT_OK;
 }
 

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -239,6 +240,127 @@ melt_status melt_forward_grouped(melt_group* g, const float* wave, const int64_t
   if (st != MELT_OK) return st;
   if (cudaEventRecord(e->done, stream) != cudaSuccess) return MELT_ERR_CUDA;
   return MELT_OK;
+}
+
+melt_status melt_group_autotune(melt_group* g, const float* wave, const int64_t* offsets, const int64_t* lengths,
+                                const int32_t* basis_of, int batch, float* out, void* stream_v, int reps,
+                                const char* path, int* hit) {
+  if (hit) *hit = 0;
+  if (!g || reps < 1 || batch < 0 || (batch > 0 && (!lengths || !basis_of || !wave || !out))) return MELT_ERR_ARG;
+  if (((uintptr_t)wave & 15) || ((uintptr_t)out & 15)) return MELT_ERR_ARG;
+  if (batch == 0) return MELT_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MELT_ERR_CUDA;
+  if (dev != g->device) return MELT_ERR_ARG;
+  for (melt_basis* b : g->bases)
+    if (basis_correction(b)) return MELT_ERR_UNSUPPORTED;
+  cudaStream_t stream = (cudaStream_t)stream_v;
+  const int nb = (int)g->bases.size();
+  // the batch's work lists, without a graph: plans change between launches
+  const int flags = g->flags;
+  g->flags |= MELT_GROUP_NO_GRAPH;
+  GroupEntry* e = nullptr;
+  melt_status st = make_entry(g, wave, offsets, lengths, basis_of, batch, out, stream, &e);
+  g->flags = flags;
+  if (st != MELT_OK) return st;
+  // key: device, then each basis's configuration and tile-count class
+  char key[4096], part[256], rest[2048];
+  int kl = 0;
+  if (!device_token(g->device, part, sizeof(part))) st = MELT_ERR_CUDA;
+  if (st == MELT_OK) kl = std::snprintf(key, sizeof(key), "melt-group-plan-v1 %s %d", part, nb);
+  for (int k = 0; st == MELT_OK && k < nb; ++k) {
+    basis_plan_key(g->bases[k], part, sizeof(part));
+    kl += std::snprintf(key + kl, sizeof(key) - kl, " | %s %d", part, tile_class(e->count[k]));
+    if (kl >= (int)sizeof(key)) st = MELT_ERR_ARG;
+  }
+  // a cached line: one plan per basis ("-" for a basis without plans)
+  bool applied = false;
+  if (st == MELT_OK && path && cache_lookup(path, key, rest, sizeof(rest))) {
+    std::vector<melt_plan> pl(nb);
+    std::vector<char> has(nb, 0);
+    const char* r = rest;
+    bool ok = true;
+    for (int k = 0; ok && k < nb; ++k) {
+      while (*r == ' ') ++r;
+      if (*r == '-') {
+        ++r;
+        continue;
+      }
+      int used = 0;
+      ok = parse_plan(r, &pl[k], &used);
+      r += used;
+      has[k] = 1;
+    }
+    for (int k = 0; ok && k < nb; ++k)
+      if (has[k]) {
+        melt_plan cur;
+        ok = melt_plan_get(g->bases[k], &cur) == MELT_OK;  // rejects bases without plans
+      }
+    if (ok) {
+      // all or nothing: every plan must fit before any is set
+      std::vector<melt_plan> prev(nb);
+      for (int k = 0; ok && k < nb; ++k)
+        if (has[k]) {
+          melt_plan_get(g->bases[k], &prev[k]);
+          ok = melt_plan_set(g->bases[k], &pl[k]) == MELT_OK;
+        }
+      if (!ok)
+        for (int k = 0; k < nb; ++k)
+          if (has[k]) melt_plan_set(g->bases[k], &prev[k]);
+      applied = ok;
+    }
+  }
+  // otherwise tune one basis at a time, timing the whole grouped launch
+  std::vector<melt_plan> chosen(nb);
+  std::vector<char> tuned(nb, 0);
+  if (st == MELT_OK && !applied) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = MELT_ERR_CUDA;
+    melt_plan cands[64];
+    for (int k = 0; st == MELT_OK && k < nb; ++k) {
+      const int n = e->count[k] > 0 ? basis_plan_candidates(g->bases[k], cands, 64) : 0;
+      if (n < 1) continue;
+      float best_ms = 1e30f;
+      int best_i = -1;
+      for (int i = 0; st == MELT_OK && i < n; ++i) {
+        if (melt_plan_set(g->bases[k], &cands[i]) != MELT_OK) continue;
+        st = launch_all(g, e, stream);  // warm-up
+        if (st == MELT_OK && cudaEventRecord(e0, stream) != cudaSuccess) st = MELT_ERR_CUDA;
+        for (int r = 0; r < reps && st == MELT_OK; ++r) st = launch_all(g, e, stream);
+        if (st == MELT_OK && cudaEventRecord(e1, stream) != cudaSuccess) st = MELT_ERR_CUDA;
+        if (st == MELT_OK && cudaEventSynchronize(e1) != cudaSuccess) st = MELT_ERR_CUDA;
+        float ms = 0.f;
+        if (st == MELT_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+          best_ms = ms;
+          best_i = i;
+        }
+      }
+      if (st == MELT_OK && best_i >= 0) {
+        melt_plan_set(g->bases[k], &cands[best_i]);
+        chosen[k] = cands[best_i];
+        tuned[k] = 1;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st == MELT_OK) st = melt_group_sync(g, stream);
+    if (st == MELT_OK && path) {
+      int rl = 0;
+      for (int k = 0; k < nb && rl < (int)sizeof(rest); ++k) {
+        if (rl) rest[rl++] = ' ';
+        if (tuned[k]) rl += format_plan(chosen[k], rest + rl, sizeof(rest) - rl);
+        else rl += std::snprintf(rest + rl, sizeof(rest) - rl, "-");
+      }
+      if (rl < (int)sizeof(rest)) cache_append(path, key, rest);
+    }
+  }
+  // every cached layout (this batch's included; graphs captured with the
+  // earlier plans too) is dropped, so the next call plans and captures anew
+  cudaStreamSynchronize(stream);
+  for (GroupEntry* c : g->cache) free_entry(c);
+  g->cache.clear();
+  if (st == MELT_OK && hit) *hit = applied ? 1 : 0;
+  return st;
 }
 
 melt_status melt_group_sync(melt_group* g, void* stream) {

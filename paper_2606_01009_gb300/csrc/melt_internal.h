@@ -90,6 +90,25 @@ int basis_device(const melt_basis* b);
 // Correction MLP attached to the basis (melt_basis_set_correction), or nullptr.
 const melt_mlp* basis_correction(const melt_basis* b);
 
+// Layout plans of the basis's tensor-core launch that fit the device, into
+// out[0..cap); returns their count (0 for the FP32 form, which has no plans).
+int basis_plan_candidates(const melt_basis* b, melt_plan* out, int cap);
+
+// Plan cache files of melt_autotune_file / melt_group_autotune: the device
+// name as one token, the basis configuration ("n_fft hop n_mels precision
+// n_mfcc hidden bands"), the size class of a tile count (floor(log2)), and
+// the seven fields of a plan written / read as text.
+bool device_token(int device, char* buf, size_t n);
+void basis_plan_key(const melt_basis* b, char* buf, size_t n);
+int tile_class(long long tiles);
+int format_plan(const melt_plan& p, char* buf, size_t n);
+bool parse_plan(const char* s, melt_plan* p, int* used);
+// Looks up the line starting with `key` + " : " in the file at `path`;
+// copies what follows the colon into rest.  False if the file or line is missing.
+bool cache_lookup(const char* path, const char* key, char* rest, size_t n);
+// Appends "key : rest\n" to the file at `path` in one write (ignored if it cannot be opened).
+void cache_append(const char* path, const char* key, const char* rest);
+
 // Correction MLP (melt_mlp.cu): y = x + W2 GELU(W1 (x - mu)/sd + b1) + b2 over
 // n rows of n_in bands; y == x allowed.
 melt_status mlp_apply(const melt_mlp* p, const float* x, float* y, long long n, cudaStream_t s);

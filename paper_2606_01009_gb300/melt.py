@@ -63,9 +63,13 @@ SIGNATURES = {
     "melt_plan_get": (C.c_int, [_VP, _VP]),
     "melt_plan_set": (C.c_int, [_VP, _VP]),
     "melt_autotune": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP, C.c_int, _VP]),
+    "melt_autotune_file": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP, C.c_int, C.c_char_p, _VP,
+                                     C.POINTER(C.c_int)]),
     "melt_group_create": (C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, C.POINTER(_VP)]),
     "melt_forward_grouped": (C.c_int, [_VP, _VP, _I64P, _I64P, C.POINTER(C.c_int32), C.c_int, _VP, _VP]),
     "melt_group_sync": (C.c_int, [_VP, _VP]),
+    "melt_group_autotune": (C.c_int, [_VP, _VP, _I64P, _I64P, C.POINTER(C.c_int32), C.c_int, _VP, _VP, C.c_int,
+                                      C.c_char_p, C.POINTER(C.c_int)]),
     "melt_group_destroy": (C.c_int, [_VP]),
     "melt_mlp_num_params": (C.c_int64, [C.c_int, C.c_int]),
     "melt_mlp_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float),
@@ -311,6 +315,19 @@ def melt_autotune(basis, wave, offsets, lengths, out, stream=None, reps=5) -> di
     return pl.as_dict()
 
 
+def melt_autotune_file(basis, wave, offsets, lengths, out, path, stream=None, reps=5):
+    """melt_autotune with the on-disk plan cache at `path`; returns (plan dict, hit)."""
+    lens, lp = _i64(lengths)
+    offs, op = _i64(offsets)
+    pl = MeltPlan()
+    hit = C.c_int(0)
+    _check(lib.melt_autotune_file(basis, C.c_void_p(wave.data_ptr()), op, lp, int(lens.shape[0]),
+                                  C.c_void_p(out.data_ptr()),
+                                  _stream_ptr(stream), int(reps), os.fsencode(path), C.byref(pl), C.byref(hit)),
+           "melt_autotune_file")
+    return pl.as_dict(), bool(hit.value)
+
+
 def melt_group_create(bases, flags=0):
     """bases: sequence of basis handles (or Frontends)."""
     hs = [b.handle if hasattr(b, "handle") else b for b in bases]
@@ -331,6 +348,22 @@ def melt_forward_grouped(group, wave, offsets, lengths, basis_of, out, stream=No
     _check(lib.melt_forward_grouped(group, C.c_void_p(wp), op, lp, ids.ctypes.data_as(C.POINTER(C.c_int32)),
                                     int(lens.shape[0]), C.c_void_p(outp), _stream_ptr(stream)),
            "melt_forward_grouped")
+
+
+def melt_group_autotune(group, wave, offsets, lengths, basis_of, out, path=None, stream=None, reps=3) -> bool:
+    """Tunes the plans of the group's bases on this batch; returns True on a plan-cache hit."""
+    lens, lp = _i64(lengths)
+    offs, op = _i64(offsets)
+    ids = np.ascontiguousarray(np.asarray(basis_of, dtype=np.int32))
+    if ids.shape[0] != lens.shape[0]:
+        raise ValueError("basis_of and lengths differ in length")
+    hit = C.c_int(0)
+    _check(lib.melt_group_autotune(group, C.c_void_p(wave.data_ptr()), op, lp,
+                                   ids.ctypes.data_as(C.POINTER(C.c_int32)), int(lens.shape[0]),
+                                   C.c_void_p(out.data_ptr()), _stream_ptr(stream), int(reps),
+                                   None if path is None else os.fsencode(path), C.byref(hit)),
+           "melt_group_autotune")
+    return bool(hit.value)
 
 
 def melt_group_sync(group, stream=None):
@@ -538,6 +571,18 @@ class GroupedFrontend:
                               dtype=torch.float32)
         melt_forward_grouped(self.handle, wave, offsets, lengths, basis_of, out, stream)
         return out
+
+    def autotune(self, wave, offsets, lengths, basis_of, out, path=None, stream=None, reps=3):
+        """Plans of every basis tuned on this batch (melt_group_autotune); returns
+        (plans per basis, cache hit)."""
+        hit = melt_group_autotune(self.handle, wave, offsets, lengths, basis_of, out, path, stream, reps)
+        plans = []
+        for fe in self.frontends:
+            try:
+                plans.append(melt_plan_get(fe.handle))
+            except MeltError:
+                plans.append(None)
+        return plans, hit
 
     def sync(self, stream=None):
         melt_group_sync(self.handle, stream)

@@ -161,3 +161,52 @@ def test_grouped_rejects_bad_arguments(melt):
     other.close()
     for fe in fes:
         fe.close()
+
+
+def test_group_autotune_and_plan_cache(melt, tmp_path):
+    """melt_group_autotune times the grouped launch one basis at a time, keeps
+    the chosen plans set, appends one cache line, and a later group of the same
+    configurations reads the line back without timing.  The features under
+    the tuned plans equal the per-group launches bit for bit, and a mixed
+    FP32 + BF16 group tunes only the BF16 basis ("-" in the line)."""
+    import torch
+    clips, ids = G.mixed_groups(n=40)
+    fes = _frontends(melt)
+    ref = _per_clip_reference(fes, clips, ids)
+    pk = G.pack_clips(clips)
+    wave = torch.from_numpy(pk.wave).cuda()
+    path = str(tmp_path / "plans.txt")
+    gf = melt.GroupedFrontend(fes)
+    T = gf.total_frames(pk.lengths, ids)
+    out = torch.empty((T, gf.n_out), device="cuda")
+    gf(wave, pk.offsets, pk.lengths, ids, out=out)        # a cached layout and graph before tuning
+    plans, hit = gf.autotune(wave, pk.offsets, pk.lengths, ids, out, path=path, reps=1)
+    assert not hit and all(p is not None for p in plans)
+    lines = open(path).read().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("melt-group-plan-v1 ")
+    out.fill_(float("nan"))
+    gf(wave, pk.offsets, pk.lengths, ids, out=out)        # captured anew with the tuned plans
+    gf.sync()
+    assert np.array_equal(out.cpu().numpy(), ref)
+    gf.close()
+    fes2 = _frontends(melt)
+    gf2 = melt.GroupedFrontend(fes2)
+    plans2, hit2 = gf2.autotune(wave, pk.offsets, pk.lengths, ids, out, path=path, reps=1)
+    assert hit2 and plans2 == plans
+    assert len(open(path).read().splitlines()) == 1
+    out.fill_(float("nan"))
+    gf2(wave, pk.offsets, pk.lengths, ids, out=out)
+    gf2.sync()
+    assert np.array_equal(out.cpu().numpy(), ref)
+    gf2.close()
+    for fe in fes + fes2:
+        fe.close()
+    mixed = _frontends(melt, ("fp32", "bf16"))
+    gm = melt.GroupedFrontend(mixed)
+    plans3, hit3 = gm.autotune(wave, pk.offsets, pk.lengths, ids, out, path=path, reps=1)
+    assert not hit3 and plans3[0] is None and plans3[1] is not None
+    last = open(path).read().splitlines()[-1]
+    assert last.split(" : ")[1].startswith("- ")
+    gm.close()
+    for fe in mixed:
+        fe.close()

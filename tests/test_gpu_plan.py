@@ -163,3 +163,41 @@ def test_dynamic_pair_schedule_matches_static(melt, batch):
     for o in outs[:2]:
         assert np.array_equal(o.cpu().numpy(), ref), batch
     fe.close()
+
+
+def test_autotune_file_cache(melt, tmp_path):
+    """melt_autotune_file tunes on a miss and appends one line; a second basis
+    of the same configuration and batch size class reads that line back
+    without timing; lines of other GPUs, other configurations or a malformed
+    plan are skipped; the output under the cached plan equals the default's."""
+    import torch
+    pk, wave = _batch()
+    path = str(tmp_path / "plans.txt")
+    with open(path, "w") as f:     # lines that must not match
+        f.write("melt-plan-v1 Some_Other_GPU 400 160 80 1 0 0 0 0 : 1 2 1 2 1 0 0\n")
+        f.write("not a plan line\n")
+    fe = melt.Frontend(precision="bf16")
+    T = fe.total_frames(pk.lengths)
+    ref = fe(wave, pk.offsets, pk.lengths).cpu().numpy()
+    out = torch.empty((T, fe.n_out), device="cuda")
+    best, hit = melt.melt_autotune_file(fe.handle, wave, pk.offsets, pk.lengths, out, path, reps=2)
+    assert not hit
+    assert melt.melt_plan_get(fe.handle) == best
+    lines = open(path).read().splitlines()
+    assert len(lines) == 3 and lines[-1].startswith("melt-plan-v1 ")
+    fe.close()
+    fe2 = melt.Frontend(precision="bf16")
+    best2, hit2 = melt.melt_autotune_file(fe2.handle, wave, pk.offsets, pk.lengths, out, path, reps=2)
+    assert hit2 and best2 == best
+    assert melt.melt_plan_get(fe2.handle) == best
+    assert len(open(path).read().splitlines()) == 3
+    got = fe2(wave, pk.offsets, pk.lengths).cpu().numpy()
+    fe2.sync()
+    assert np.array_equal(got, ref)
+    fe2.close()
+    # another configuration (128 Mel bins) misses and appends its own line
+    fe3 = melt.Frontend(precision="bf16", n_mels=128)
+    out3 = torch.empty((fe3.total_frames(pk.lengths), 128), device="cuda")
+    _, hit3 = melt.melt_autotune_file(fe3.handle, wave, pk.offsets, pk.lengths, out3, path, reps=1)
+    assert not hit3 and len(open(path).read().splitlines()) == 4
+    fe3.close()
