@@ -185,6 +185,36 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
   p.sfg = fp8 ? (p.J + 3) / 4 : 0;
   const int sf_cols = fp8 ? 4 * p.sfg * p.ZB + kSfBCols : 0;
   p.nacc = (p.Hd > 0 || p.NC + sf_cols > 256) ? 1 : 2;
+  // MFCC: the DCT on the tensor cores where its TMEM columns fit beside the
+  // projection accumulators (two 256 columns apart, else one) and FP8's scale
+  // factors: the coefficient accumulator (dct_n columns) and the split-BF16
+  // log-Mel operand (MP / 2 columns per part), first fit into what is free
+  p.dct_tc = 0;
+  if (n_mfcc > 0 && p.Hd == 0) {
+    const int nd = (n_mfcc + 15) & ~15;
+    for (int na = 2; na >= 1 && !p.dct_tc; --na) {
+      if (na == 2 && p.NC + sf_cols > 256) continue;
+      int iv[2][2] = {{p.NC + (na == 2 ? sf_cols : 0), 256}, {256 + (na == 2 ? p.NC : sf_cols), 512}};
+      auto place = [&](int w, int align, uint32_t& col) {
+        for (auto& v : iv) {
+          const int s0 = (v[0] + align - 1) / align * align;
+          if (s0 + w <= v[1]) {
+            col = (uint32_t)s0;
+            v[0] = s0 + w;
+            return true;
+          }
+        }
+        return false;
+      };
+      if (place(nd, 16, p.dct_c) && place(p.MP / 2, 8, p.dct_ahi) && place(p.MP / 2, 8, p.dct_alo)) {
+        p.dct_tc = 1;
+        p.nacc = na;
+        p.dct_n = nd;
+        p.dct_part = (uint32_t)(p.MP / 8) * (uint32_t)(nd / 2) * 16u;
+        p.idesc_dct = idesc_f32acc(1u, 2 * kF, (uint32_t)nd);
+      }
+    }
+  }
   p.sf_col = (uint32_t)(p.nacc == 2 ? p.NC : 256);
   if (fp8 && (p.nacc == 2 ? p.NC + sf_cols > 256 : p.NC > 256 || 256 + sf_cols > 512)) return false;
   if (p.Hd > 0) {
@@ -244,11 +274,11 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
       p.off_codes = off;  // FP8: the scale code of every Z row of the tile, per A buffer
       off += fp8 ? align_up(p.codes_stride * (uint32_t)p.ZB, 128) : 0u;
       p.off_dct = off;
-      off += align_up(4 * ((n_mfcc + 3) & ~3) * p.MP, 128);
+      off += align_up(p.dct_tc ? 2 * p.dct_part : 4 * ((n_mfcc + 3) & ~3) * p.MP, 128);
       if (off + 128 > kSmemLimit) continue;
       p.NS = ns;
       p.smem_total = off + 128;
-      p.tmem_cols = fp8 ? 512 : p.NC <= 32 ? 64 : p.NC <= 64 ? 128 : p.NC <= 128 ? 256 : 512;
+      p.tmem_cols = fp8 || p.dct_tc ? 512 : p.NC <= 32 ? 64 : p.NC <= 64 ? 128 : p.NC <= 128 ? 256 : 512;
       p.acc_stride = p.tmem_cols / 2;
       p.idesc = fp8 ? idesc_mxf8(2 * kF, p.NC) : idesc_f32acc(1u, 2 * kF, p.NC);  // M = 256 over the pair
       p.desc_hi = (128u >> 4) | (1u << 14);
@@ -508,10 +538,10 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
   const bool fused = pair && p.Hd > 0 && L.mlp != nullptr;
   if (pair && p.Hd > 0 && !L.mlp) p.Hd = 0;  // plan made for a correction that is not passed
   KernelFn fn = fused ? kernel_for_pair_mlp(p.MP / 16)
-                : pair ? (tb->precision == MELT_FP8E4M3 ? kernel_for_pair_fp8(L.n_mfcc > 0, p.MP / 16)
-                                                        : kernel_for_pair(L.n_mfcc > 0, p.MP / 16))
+                : pair ? (tb->precision == MELT_FP8E4M3 ? kernel_for_pair_fp8(L.n_mfcc > 0, p.MP / 16, p.dct_tc)
+                                                        : kernel_for_pair(L.n_mfcc > 0, p.MP / 16, p.dct_tc))
                        : (L.n_mfcc ? kernel_for_mfcc(tb->precision, p.MP / 16)
-                                   : kernel_for_plain(tb->precision, p.MP / 16));
+                                   : kernel_for_plain(tb->precision, p.MP / 16, L.stft_bands > 0));
   if (!fn) return cudaErrorInvalidValue;
   if (fused) {
     // the MLP's current parameters (training may have changed them) as BF16
@@ -561,7 +591,7 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
   attr[1].val.clusterDim.x = 2;
   attr[1].val.clusterDim.y = 1;
   attr[1].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(pair_threads(fused, tb->precision, L.n_mfcc > 0, p.MP / 16), 1, 1);
+  cfg.blockDim = dim3(pair_threads(fused, tb->precision, L.n_mfcc > 0, p.MP / 16, p.dct_tc), 1, 1);
   cfg.numAttrs = 2;
   TcBasis* mtb = const_cast<TcBasis*>(tb);
   if (mtb->pair_clusters < 0 || mtb->pair_smem != smem) {

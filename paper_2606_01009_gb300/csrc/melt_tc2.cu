@@ -4,8 +4,8 @@
 namespace melt {
 namespace tc {
 
-KernelFn kernel_for_pair(bool mfcc, int nch) {
-  return mfcc ? pick_pair_kernel<true>(nch) : pick_pair_kernel<false>(nch);
+KernelFn kernel_for_pair(bool mfcc, int nch, bool dtc) {
+  return mfcc ? pick_pair_kernel<true>(nch, dtc) : pick_pair_kernel<false>(nch);
 }
 
 }  // namespace tc

@@ -5,7 +5,7 @@
 namespace melt {
 namespace tc {
 
-KernelFn kernel_for_pair_fp8(bool mfcc, int nch) { return pick_pair_fp8_kernel<>(mfcc, nch); }
+KernelFn kernel_for_pair_fp8(bool mfcc, int nch, bool dtc) { return pick_pair_fp8_kernel<>(mfcc, nch, dtc); }
 
 }  // namespace tc
 }  // namespace melt

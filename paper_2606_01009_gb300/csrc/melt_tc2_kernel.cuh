@@ -57,11 +57,12 @@ namespace tc {
 // converters epw+3 .. epw+6.
 constexpr int kPCvtWarps = 4;
 constexpr int kPCvtThreads = 32 * kPCvtWarps;  // 128
-// Epilogue warps: 8 (two per TMEM lane quarter) with the fused MLP, and for
-// the MFCC epilogue where M <= 80 (the two split the DCT coefficients); 4
-// otherwise.
-__host__ __device__ constexpr int pair_epi_warps(bool mlp, bool mfcc = false, int nch = 1) {
-  return mlp || (mfcc && nch <= 5) ? 8 : 4;
+// Epilogue warps: 8 (two per TMEM lane quarter) with the fused MLP, for the
+// MFCC epilogue with the DCT on the tensor cores, and for the MFCC epilogue
+// with the DCT on the CUDA cores where M <= 80 (the two split the
+// coefficients); 4 otherwise.
+__host__ __device__ constexpr int pair_epi_warps(bool mlp, bool mfcc = false, int nch = 1, bool dtc = false) {
+  return mlp || (mfcc && (dtc || nch <= 5)) ? 8 : 4;
 }
 // Converter warps: 4 (BF16: each sample converted once, short chains), 8 for
 // FP8's log-Mel kernel, whose per-row max makes each chunk one dependent
@@ -70,8 +71,9 @@ __host__ __device__ constexpr int pair_epi_warps(bool mlp, bool mfcc = false, in
 __host__ __device__ constexpr int pair_cvt_warps(int prec, bool mfcc, int nch) {
   return prec == MELT_FP8E4M3 && !mfcc ? 8 : 4;
 }
-__host__ __device__ constexpr int pair_threads(bool mlp, int prec = MELT_BF16, bool mfcc = false, int nch = 1) {
-  return 32 * (pair_epi_warps(mlp, mfcc, nch) + 3 + pair_cvt_warps(prec, mfcc, nch));
+__host__ __device__ constexpr int pair_threads(bool mlp, int prec = MELT_BF16, bool mfcc = false, int nch = 1,
+                                               bool dtc = false) {
+  return 32 * (pair_epi_warps(mlp, mfcc, nch, dtc) + 3 + pair_cvt_warps(prec, mfcc, nch));
 }
 constexpr int kPQuads = 8;  // float4s per converter thread per staged chunk (<= 16 KB)
 constexpr uint32_t kSfOne = 0x7F7F7F7Fu;    // four UE8M0 codes of 2^0
@@ -340,8 +342,49 @@ static __device__ bool pair_mlp_gemm2(const TcParams& p, const PairCtx& c, const
   return true;
 }
 
+// This CTA's rows of the DCT-II matrix as the B operand of the tensor-core
+// DCT: rows n = rank dct_n / 2 + i (zero for n >= n_mfcc) over the MP Mel
+// bins (zero past M), each value split into BF16 hi = rn(D) and lo =
+// rn(D - hi); K-major core matrices of 8 rows x 8 bins, the two parts
+// dct_part bytes apart.
+static __device__ __forceinline__ void fill_dct_split(const TcParams& p, uint8_t* img, uint32_t rank, int t0,
+                                                      int nt) {
+  const int nh = p.dct_n / 2;
+  __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>(img);
+  __nv_bfloat16* lo = reinterpret_cast<__nv_bfloat16*>(img + p.dct_part);
+  for (int i = t0; i < nh * p.MP; i += nt) {
+    const int r = i / p.MP, m = i - r * p.MP;
+    const int n = (int)rank * nh + r;
+    const float v = (n < p.n_mfcc && m < p.M) ? p.dct[n * p.M + m] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const size_t at = (size_t)(m >> 3) * nh * 8 + (size_t)r * 8 + (m & 7);  // in 2-byte units
+    hi[at] = h;
+    lo[at] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+// MFCC with the DCT on the tensor cores: once both CTAs' epilogues have
+// written a tile's log-Mel rows (split into BF16 hi + lo) to TMEM, the
+// coefficients C = L D^T accumulate as hi*hi + hi*lo + lo*hi over the K-steps
+// of 16 Mel bins (the lo*lo term, below 2^-16 of each product, is dropped).
+static __device__ void pair_dct_gemm(const TcParams& p, const PairCtx& c, const PairBars& B, uint32_t tmem_base) {
+  const uint64_t hi = (uint64_t)p.desc_hi << 32;
+  const uint32_t nh16 = (uint32_t)p.dct_n / 2 * 16;  // bytes between the two K core columns of a K-step
+  const uint32_t dhi = ((c.sbase + p.off_dct) >> 4) | ((nh16 >> 4) << 16);
+  const uint32_t dlo = dhi + (p.dct_part >> 4);
+  const uint32_t step16 = (2 * nh16) >> 4;
+  const uint32_t d = tmem_base + p.dct_c;
+  tc_fence_after();
+  for (int s = 0; s < p.MP / 16; ++s) {
+    mma_f16_pair_ts(d, tmem_base + p.dct_ahi + 8 * s, hi | (dhi + s * step16), p.idesc_dct, s > 0);
+    mma_f16_pair_ts(d, tmem_base + p.dct_ahi + 8 * s, hi | (dlo + s * step16), p.idesc_dct, true);
+    mma_f16_pair_ts(d, tmem_base + p.dct_alo + 8 * s, hi | (dhi + s * step16), p.idesc_dct, true);
+  }
+  mma_commit_pair_mc(pbar(p, c, B.h_full), 3);
+}
+
 // Even CTA only: one thread issues every pair MMA.
-template <bool MLP, int PREC>
+template <bool MLP, int PREC, bool DTC = false>
 static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx& c,
                                 const PairBars& B, uint32_t tmem_base) {
   const uint2* tab = reinterpret_cast<const uint2*>(gbase + p.off_tab);
@@ -400,6 +443,19 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
     }
     mma_commit_pair_mc(pbar(p, c, B.z_empty + zb), 3);
     mma_commit_pair_mc(pbar(p, c, B.t_full + acc), 3);
+    if constexpr (DTC) {
+      // the previous tile's DCT once its epilogues released its accumulator
+      // (their log-Mel rows are in TMEM by then); this tile's projection is
+      // already queued ahead of it
+      if (k > 0) {
+        const int pa = (k - 1) % nacc;
+        if (!mbar_wait_cluster(pbar(p, c, B.t_empty + pa), ((k - 1) / nacc) & 1, c.abort, p.err, kErrTimeout)) {
+          ok = false;
+          break;
+        }
+        pair_dct_gemm(p, c, B, tmem_base);
+      }
+    }
     if constexpr (MLP) {
       // the previous tile's output layer, once its GELU(H) is written
       if (k > 0 && !pair_mlp_gemm2(p, c, B, tmem_base, k - 1)) {
@@ -415,6 +471,13 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
       pair_mlp_gemm1(p, c, B, tmem_base);
       pair_mlp_gemm2(p, c, B, tmem_base, k - 1);
     }
+  }
+  if constexpr (DTC) {
+    // the last tile's DCT
+    if (ok && k > 0 &&
+        mbar_wait_cluster(pbar(p, c, B.t_empty + (k - 1) % nacc), ((k - 1) / nacc) & 1, c.abort, p.err,
+                          kErrTimeout))
+      pair_dct_gemm(p, c, B, tmem_base);
   }
   // no pair MMA may still be running when either CTA releases TMEM
   mma_commit_pair_mc(pbar(p, c, B.drain), 3);
@@ -709,6 +772,100 @@ static __device__ __forceinline__ void half_chunks(int n, int halves, int h, int
   hi = h ? n : first;
 }
 
+// MFCC epilogue with the DCT on the tensor cores: per tile, the log-Mel row
+// (Eq. 8) of this warp's chunks goes to TMEM as BF16 hi and lo parts (the A
+// operand of the DCT MMAs), the accumulator is released, and once the DCT's
+// commit arrives the coefficients (Eq. 9) are read back and stored.  Empty
+// tiles take every step but the loads and stores, so that both CTAs keep the
+// barrier phases in step.
+template <int EPW>
+__device__ void pair_epilogue_dct(const TcParams& p, const PairCtx& c, const PairBars& B, uint32_t tmem_base) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int row = 32 * quarter + lane;
+  const bool vec8 = ((p.n_mfcc & 7) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 31) == 0);
+  const uint32_t tl = tmem_base + ((uint32_t)(32 * quarter) << 16);
+  int c_lo, c_hi, k_lo, k_hi;
+  half_chunks(p.MP >> 4, EPW / 4, half, c_lo, c_hi);
+  half_chunks(p.dct_n >> 4, EPW / 4, half, k_lo, k_hi);
+  for (int k = 0;; ++k) {
+    bool okq = true;
+    const int q = k == 0 ? c.cluster : pair_next_warp(p, c, B, k, okq);
+    if (!okq || q >= p.n_pairs) break;
+    const int acc = p.nacc == 2 ? (k & 1) : 0;
+    const uint32_t tphase = p.nacc == 2 ? ((k >> 1) & 1) : (k & 1);
+    const TileDesc td = pair_tile(p, c, q);
+    if (!warp_wait_cl(pbar(p, c, B.t_full + acc), tphase, c.abort, p.err)) break;
+    sched_release(p, c, B, k);
+    tc_fence_after();
+    const bool live = td.n_frames > 0;
+    const uint32_t t0 = tl + acc * p.acc_stride;
+    if (live) {
+#pragma unroll 1
+      for (int c0 = c_lo; c0 < c_hi; c0 += kEpiGroup) {
+        float re[kEpiGroup][16], im[kEpiGroup][16];
+#pragma unroll
+        for (int g = 0; g < kEpiGroup; ++g) {
+          if (c0 + g < c_hi) {
+            tmem_ld16(t0 + 16 * (c0 + g), re[g]);
+            tmem_ld16(t0 + p.MP + 16 * (c0 + g), im[g]);
+          }
+        }
+        tmem_ld_wait();
+#pragma unroll
+        for (int g = 0; g < kEpiGroup; ++g) {
+          reg_fence16(re[g]);
+          reg_fence16(im[g]);
+          const int cc = c0 + g;
+          if (cc < c_hi) {
+            uint32_t wh[8], wl[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              // bins past M hold zero basis rows: their log is replaced by 0
+              const int m = 16 * cc + 2 * e;
+              const float a = m < p.M ? __logf(fmaf(re[g][2 * e], re[g][2 * e], fmaf(im[g][2 * e], im[g][2 * e], p.eps))) : 0.f;
+              const float b = m + 1 < p.M
+                                  ? __logf(fmaf(re[g][2 * e + 1], re[g][2 * e + 1],
+                                                fmaf(im[g][2 * e + 1], im[g][2 * e + 1], p.eps)))
+                                  : 0.f;
+              wh[e] = pack_bf16(a, b);
+              wl[e] = pack_bf16(a - __uint_as_float(wh[e] << 16), b - __uint_as_float(wh[e] & 0xFFFF0000u));
+            }
+            tmem_st8(tl + p.dct_ahi + 8 * cc, wh);
+            tmem_st8(tl + p.dct_alo + 8 * cc, wl);
+          }
+        }
+      }
+      tmem_st_wait();
+    }
+    tc_fence_before();
+    warp_arrive_leader(pbar(p, c, B.t_empty + acc));
+    if (!warp_wait_cl(pbar(p, c, B.h_full), k & 1, c.abort, p.err)) break;
+    tc_fence_after();
+    if (live) {
+      float* orow = p.out + (size_t)(td.out_row + row) * p.n_mfcc;
+      const bool valid = row < td.n_frames;
+#pragma unroll 1
+      for (int kc = k_lo; kc < k_hi; ++kc) {
+        float v[16];
+        tmem_ld16(tl + p.dct_c + 16 * kc, v);
+        tmem_ld_wait();
+        reg_fence16(v);
+        if (valid) {
+          if (vec8 && 16 * kc + 16 <= p.n_mfcc) {
+            stg256(orow + 16 * kc, v);
+            stg256(orow + 16 * kc + 8, v + 8);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+              if (16 * kc + e < p.n_mfcc) orow[16 * kc + e] = v[e];
+          }
+        }
+      }
+    }
+  }
+}
+
 template <int NCH, bool MFCC, int EPW, int PREC>
 __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& c, const PairBars& B,
                               uint32_t tmem_base) {
@@ -973,9 +1130,10 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
   }
 }
 
-template <int NCH, bool MFCC, bool MLP, int PREC = MELT_BF16>
-__global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH), 1) melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
-  constexpr int EPW = pair_epi_warps(MLP, MFCC, NCH);
+template <int NCH, bool MFCC, bool MLP, int PREC = MELT_BF16, bool DTC = false>
+__global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH, DTC), 1)
+    melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
+  constexpr int EPW = pair_epi_warps(MLP, MFCC, NCH, DTC);
   constexpr int kPMmaWarp = EPW, kPBWarp = EPW + 1, kPProdWarp = EPW + 2, kPCvtWarp0 = EPW + 3;
   constexpr int CW = pair_cvt_warps(PREC, MFCC, NCH);
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -1042,7 +1200,10 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH), 1) melt_tc
   }
   if constexpr (MFCC) {
     if (warp < EPW) {
-      fill_dct(p, reinterpret_cast<float*>(gbase + p.off_dct), threadIdx.x, 32 * EPW);
+      if constexpr (DTC)
+        fill_dct_split(p, gbase + p.off_dct, c.rank, threadIdx.x, 32 * EPW);
+      else
+        fill_dct(p, reinterpret_cast<float*>(gbase + p.off_dct), threadIdx.x, 32 * EPW);
     }
   }
   tc_fence_before();
@@ -1074,7 +1235,7 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH), 1) melt_tc
   // previous kernel of the stream first (programmatic dependent launch).
   if (warp == kPMmaWarp) {
     if (lane == 0) {
-      if (c.rank == 0) pair_mma<MLP, PREC>(p, gbase, c, B, tmem_base);
+      if (c.rank == 0) pair_mma<MLP, PREC, DTC>(p, gbase, c, B, tmem_base);
       drain_wait(pbar(p, c, B.drain), 0, p.err);
     }
     __syncwarp();
@@ -1096,6 +1257,8 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH), 1) melt_tc
     pdl_wait();
     if constexpr (MLP)
       pair_epilogue_mlp<NCH>(p, gbase, c, B, tmem_base);
+    else if constexpr (DTC)
+      pair_epilogue_dct<EPW>(p, c, B, tmem_base);
     else
       pair_epilogue<NCH, MFCC, EPW, PREC>(p, gbase, c, B, tmem_base);
     __syncwarp();
@@ -1119,11 +1282,13 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH), 1) melt_tc
 }
 
 template <bool MFCC>
-KernelFn pick_pair_kernel(int nch) {
+KernelFn pick_pair_kernel(int nch, bool dtc = false) {
   if constexpr (!MFCC) {
     (void)nch;
+    (void)dtc;
     return melt_tc_pair_kernel<1, false, false>;
   } else {
+    if (dtc) return melt_tc_pair_kernel<1, true, false, MELT_BF16, true>;
     switch (nch) {
       case 1: return melt_tc_pair_kernel<1, true, false>;
       case 2: return melt_tc_pair_kernel<2, true, false>;
@@ -1142,8 +1307,9 @@ KernelFn pick_pair_kernel(int nch) {
 // templates so that only the translation unit that calls one instantiates
 // its kernels.
 template <int = 0>
-KernelFn pick_pair_fp8_kernel(bool mfcc, int nch) {
+KernelFn pick_pair_fp8_kernel(bool mfcc, int nch, bool dtc = false) {
   if (!mfcc) return melt_tc_pair_kernel<1, false, false, MELT_FP8E4M3>;
+  if (dtc) return melt_tc_pair_kernel<1, true, false, MELT_FP8E4M3, true>;
   switch (nch) {
     case 1: return melt_tc_pair_kernel<1, true, false, MELT_FP8E4M3>;
     case 2: return melt_tc_pair_kernel<2, true, false, MELT_FP8E4M3>;

@@ -136,6 +136,14 @@ struct TcParams {
   uint32_t w1_step, w2_step;         // bytes per K-step block of this CTA's W1 / W2 rows
   uint32_t idesc1, idesc2;           // the two MLP GEMMs (M = 256, N = Hd / MP)
   uint32_t a1_col, h_col, y_col;     // TMEM columns of x-hat, the hidden layer, the output
+  // CTA-pair kernel, MFCC with the DCT-II on the tensor cores (dct_tc = 1):
+  // the log-Mel row goes to TMEM as a split-BF16 A operand (hi and lo parts,
+  // MP/2 columns each, at dct_ahi / dct_alo), the DCT matrix sits in shared
+  // memory at off_dct as this CTA's dct_n / 2 rows (hi part, then lo part,
+  // dct_part bytes each, K-major core matrices), and the coefficients
+  // accumulate in dct_n TMEM columns at dct_c (M = 256 over the pair)
+  int dct_tc, dct_n;
+  uint32_t dct_ahi, dct_alo, dct_c, dct_part, idesc_dct;
 };
 
 // barrier indices
@@ -605,7 +613,7 @@ static __device__ __forceinline__ void stft_bin(StftBands& st, const float4* fbs
   st.acc1 = fmaf(f.y, s2, st.acc1);
 }
 
-template <int PREC, int NCH, bool MFCC>
+template <int PREC, int NCH, bool MFCC, bool STFT = false>
 __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase, const Bars& B,
                               uint32_t tmem_base, volatile int* abort) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -623,7 +631,7 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
     float* orow = p.out + (size_t)(td.out_row + row) * p.n_out;
     if constexpr (!MFCC) {
       bool ok = true;
-      StftBands stb{0.f, 0.f, -1};  // fused STFT + Mel comparator: no band started yet
+      [[maybe_unused]] StftBands stb{0.f, 0.f, -1};  // fused STFT + Mel comparator: no band started yet
       for (int b = 0; b < p.nblk; ++b, ++kb) {
         const int acc = kb & 1;
         if (!warp_wait(sbase + p.off_bar + 8 * (B.t_full + acc), (kb >> 1) & 1, abort, p.err)) {
@@ -658,7 +666,7 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
             tc_fence_before();
             warp_arrive(sbase + p.off_bar + 8 * (B.t_empty + acc));
           }
-          if (p.stft_bands) {
+          if constexpr (STFT) {
             // the comparator: |X_k|^2 of DFT bin k into the triangular bands, in bin order
             const float4* fbs = reinterpret_cast<const float4*>(gbase + p.off_fb);
 #pragma unroll
@@ -701,7 +709,7 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
         }
       }
       if (!ok) break;
-      if (p.stft_bands)
+      if constexpr (STFT)
         while (stb.c < p.stft_bands) stft_flush(stb, orow, p.stft_bands, p.eps, valid);
       continue;
     } else {
@@ -735,7 +743,9 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
   }
 }
 
-template <int PREC, int NCH, bool MFCC>
+// STFT: the fused STFT + Mel comparator's epilogue (its own instantiation, so
+// that the log-Mel kernel does not carry its registers)
+template <int PREC, int NCH, bool MFCC, bool STFT = false>
 __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -781,7 +791,7 @@ __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_const
     tmem_alloc(smem_u32(tmem_slot), p.tmem_cols);
     tmem_relinquish();
   }
-  if (p.stft_bands > 0 && warp < kEpiWarps) {  // the comparator's filterbank table
+  if (STFT && warp < kEpiWarps) {  // the comparator's filterbank table
     float4* fbs = reinterpret_cast<float4*>(gbase + p.off_fb);
     for (int i = threadIdx.x; i < p.M; i += kEpiThreads) fbs[i] = p.fb[i];
   }
@@ -813,7 +823,7 @@ __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_const
     __syncwarp();
   } else {
     pdl_wait();
-    role_epilogue<PREC, NCH, MFCC>(p, gbase, sbase, B, tmem_base, abort);
+    role_epilogue<PREC, NCH, MFCC, STFT>(p, gbase, sbase, B, tmem_base, abort);
     __syncwarp();
   }
   tc_fence_before();
@@ -847,14 +857,14 @@ KernelFn pick_kernel(int nch) {
 }
 
 // Defined in melt_tc_plain.cu (log-Mel) and melt_tc_mfcc.cu (MFCC epilogue).
-KernelFn kernel_for_plain(int prec, int nch);
+KernelFn kernel_for_plain(int prec, int nch, bool stft = false);
 KernelFn kernel_for_mfcc(int prec, int nch);
 // Defined in melt_tc2.cu: the CTA-pair kernel (BF16).
-KernelFn kernel_for_pair(bool mfcc, int nch);
+KernelFn kernel_for_pair(bool mfcc, int nch, bool dtc);
 // Defined in melt_tc2_mlp.cu: the CTA-pair kernel with the fused correction MLP.
 KernelFn kernel_for_pair_mlp(int nch);
 // Defined in melt_tc2_fp8.cu: the CTA-pair kernel with FP8 e4m3 operands.
-KernelFn kernel_for_pair_fp8(bool mfcc, int nch);
+KernelFn kernel_for_pair_fp8(bool mfcc, int nch, bool dtc);
 
 }  // namespace tc
 }  // namespace melt

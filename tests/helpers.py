@@ -40,6 +40,21 @@ FORM_TOL_DB = {
 TOL_DEPTHS = (10.0, 30.0, 60.0, 100.0)
 
 
+def dct_rel(precision, n_mels):
+    """Relative bound (against sum_m |L_m D_km|) on the DCT-II step of the MFCC
+    epilogue.  FP32 sums on the CUDA cores (FP32 and BF16x3 forms): n + 2
+    roundings.  The CTA-pair kernels (BF16, FP8) may run the DCT on the
+    tensor cores with both operands split into BF16 hi + lo and the lo*lo
+    term dropped: each product is off by at most 3.02 * 2^-16 of |L D|
+    (hi*e_D + lo*lo + lo*e_D + e_L*D, with |e| <= 2^-16 of the value and
+    |lo| <= 2^-8), and the 3 * MP products accumulate in FP32 (4 gamma_n, the
+    convention used for every tensor-core sum here)."""
+    if precision in ("fp32", "bf16x3"):
+        return (n_mels + 2) * U32
+    mp = -(-n_mels // 16) * 16
+    return 3.1 * 2.0 ** -16 + 4 * 3 * mp * U32 * 1.01
+
+
 def gpu_features(fe, clips, offsets=None, stream=None):
     """Run a Frontend on host clips (packed at 4-float alignment) -> float64 [sum T, n_out]."""
     import torch

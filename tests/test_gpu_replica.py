@@ -17,7 +17,7 @@ import pytest
 
 from oracle import melt_oracle as O
 from paper_2606_01009_gb300 import inputs as G
-from tests.helpers import (acc_rel, db_report, fp32_sum_error, gpu_features, log_error_bound, oracle_features,
+from tests.helpers import (acc_rel, db_report, dct_rel, fp32_sum_error, gpu_features, log_error_bound, oracle_features,
                            rounded_log_bound)
 
 pytestmark = pytest.mark.gpu
@@ -86,8 +86,8 @@ def test_cepstral_configuration(melt, prec):
     D = O.dct2_ortho(40, 128)
     ref = logmel @ D.T
     assert got.shape == ref.shape
-    # the log-Mel bound carried through the DCT, plus the DCT's own FP32 sums
-    bound = lb @ np.abs(D).T + 130 * 2.0 ** -24 * (np.abs(logmel) @ np.abs(D).T)
+    # the log-Mel bound carried through the DCT, plus the DCT's own error
+    bound = lb @ np.abs(D).T + dct_rel(prec, 128) * (np.abs(logmel) @ np.abs(D).T)
     bad = np.abs(got - ref) > bound
     assert not bad.any(), (prec, int(bad.sum()), np.argwhere(bad)[:5])
     exact = O.MelTSpec(periodic=False, n_mfcc=40, **CEPSTRAL)

@@ -12,7 +12,7 @@ import pytest
 
 from oracle import melt_oracle as O
 from paper_2606_01009_gb300 import inputs as G
-from tests.helpers import (acc_rel, check_form_tolerance, db_report, fp32_sum_error, gpu_features,
+from tests.helpers import (acc_rel, check_form_tolerance, dct_rel, db_report, fp32_sum_error, gpu_features,
                            log_error_bound, oracle_features, rounded_log_bound)
 
 pytestmark = pytest.mark.gpu
@@ -100,7 +100,7 @@ def test_mfcc(melt, prec):
     D = O.dct2_ortho(40, 80)
     logmel_r = oracle_features(spec_l, clips, rounded=prec)
     ref = logmel_r @ D.T
-    bound = lb @ np.abs(D).T + 82 * 2 ** -24 * (np.abs(logmel_r) @ np.abs(D).T)
+    bound = lb @ np.abs(D).T + dct_rel(prec, 80) * (np.abs(logmel_r) @ np.abs(D).T)
     assert np.all(np.abs(got - ref) <= bound)
     fe.close()
 
