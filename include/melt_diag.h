@@ -41,6 +41,20 @@ melt_status melt_diag_wait_timeout(melt_basis* basis, void* stream);
 melt_status melt_diag_gelu(const float* h, float* y, int64_t n, void* stream);
 
 /*
+ * melt_diag_log - evaluates, on n device floats x, the natural log that the
+ *   tensor-core kernels' epilogues take of S + eps (Eq. 8): log2(x) from the
+ *   hardware approximation with subnormal inputs flushed to zero, times ln 2.
+ *   The paper has no counterpart; this entry point lets a test check the
+ *   log's error against the exact function over every binade (the parity
+ *   bounds assume absolute error <= 2^-21 for x in [0.5, 2] and <= 4 ulp of
+ *   the result elsewhere).
+ *   x, y    device float[n] (may be the same array); x > 0 normal
+ *   stream  cudaStream_t as void*; asynchronous
+ *   Errors: MELT_ERR_ARG for n < 0 or NULL pointers, MELT_ERR_CUDA if the launch fails.
+ */
+melt_status melt_diag_log(const float* x, float* y, int64_t n, void* stream);
+
+/*
  * melt_diag_alloc_count - number of device allocations (cudaMalloc) and
  *   page-locked host allocations (cudaMallocHost) the library has made in
  *   this process so far, over all devices and threads.  The paper has no

@@ -65,15 +65,16 @@ __host__ __device__ constexpr int pair_epi_warps(bool mlp, bool mfcc = false, in
   return mlp || (mfcc && (dtc || nch <= 5)) ? 8 : 4;
 }
 // Converter warps: 4 (BF16: each sample converted once, short chains), 8 for
-// FP8's log-Mel kernel, whose per-row max makes each chunk one dependent
-// chain per row set (twice the warps, half the chain).  The MFCC kernels keep
-// 4 (their epilogue warps and registers fill the block).
-__host__ __device__ constexpr int pair_cvt_warps(int prec, bool mfcc, int nch) {
-  return prec == MELT_FP8E4M3 && !mfcc ? 8 : 4;
+// FP8's log-Mel kernel and its MFCC kernel with the DCT on the tensor cores,
+// whose per-row max makes each chunk one dependent chain per row set (twice
+// the warps, half the chain).  The MFCC kernels with the DCT on the CUDA
+// cores keep 4 (their epilogue warps and registers fill the block).
+__host__ __device__ constexpr int pair_cvt_warps(int prec, bool mfcc, int nch, bool dtc = false) {
+  return prec == MELT_FP8E4M3 && (!mfcc || dtc) ? 8 : 4;
 }
 __host__ __device__ constexpr int pair_threads(bool mlp, int prec = MELT_BF16, bool mfcc = false, int nch = 1,
                                                bool dtc = false) {
-  return 32 * (pair_epi_warps(mlp, mfcc, nch, dtc) + 3 + pair_cvt_warps(prec, mfcc, nch));
+  return 32 * (pair_epi_warps(mlp, mfcc, nch, dtc) + 3 + pair_cvt_warps(prec, mfcc, nch, dtc));
 }
 constexpr int kPQuads = 8;  // float4s per converter thread per staged chunk (<= 16 KB)
 constexpr uint32_t kSfOne = 0x7F7F7F7Fu;    // four UE8M0 codes of 2^0
@@ -823,9 +824,9 @@ __device__ void pair_epilogue_dct(const TcParams& p, const PairCtx& c, const Pai
             for (int e = 0; e < 8; ++e) {
               // bins past M hold zero basis rows: their log is replaced by 0
               const int m = 16 * cc + 2 * e;
-              const float a = m < p.M ? __logf(fmaf(re[g][2 * e], re[g][2 * e], fmaf(im[g][2 * e], im[g][2 * e], p.eps))) : 0.f;
+              const float a = m < p.M ? fast_ln(fmaf(re[g][2 * e], re[g][2 * e], fmaf(im[g][2 * e], im[g][2 * e], p.eps))) : 0.f;
               const float b = m + 1 < p.M
-                                  ? __logf(fmaf(re[g][2 * e + 1], re[g][2 * e + 1],
+                                  ? fast_ln(fmaf(re[g][2 * e + 1], re[g][2 * e + 1],
                                                 fmaf(im[g][2 * e + 1], im[g][2 * e + 1], p.eps)))
                                   : 0.f;
               wh[e] = pack_bf16(a, b);
@@ -926,7 +927,7 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
               const float r = re[g][e] * sc, i = im[g][e] * sc;
-              re[g][e] = __logf(fmaf(r, r, fmaf(i, i, p.eps)));
+              re[g][e] = fast_ln(fmaf(r, r, fmaf(i, i, p.eps)));
             }
             if (valid) {
               if (vec8 && 16 * cc + 16 <= p.M) {
@@ -956,7 +957,7 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
 #pragma unroll
         for (int e = 0; e < 16; ++e)
           lm[16 * cc + e] =
-              (16 * cc + e < p.M) ? __logf(fmaf(re[e] * sc, re[e] * sc, (im[e] * sc) * (im[e] * sc)) + p.eps) : 0.f;
+              (16 * cc + e < p.M) ? fast_ln(fmaf(re[e] * sc, re[e] * sc, (im[e] * sc) * (im[e] * sc)) + p.eps) : 0.f;
       }
       tc_fence_before();
       warp_arrive_leader(pbar(p, c, B.t_empty + acc));
@@ -1048,7 +1049,7 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
           tmem_ld16(tl + p.MP + 16 * cc, im);
           tmem_ld_wait(re, im);
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[16 * g + e] = __logf(fmaf(re[e], re[e], fmaf(im[e], im[e], p.eps)));
+          for (int e = 0; e < 16; ++e) v[16 * g + e] = fast_ln(fmaf(re[e], re[e], fmaf(im[e], im[e], p.eps)));
           uint32_t w[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
@@ -1135,7 +1136,7 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH, DTC), 1)
     melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
   constexpr int EPW = pair_epi_warps(MLP, MFCC, NCH, DTC);
   constexpr int kPMmaWarp = EPW, kPBWarp = EPW + 1, kPProdWarp = EPW + 2, kPCvtWarp0 = EPW + 3;
-  constexpr int CW = pair_cvt_warps(PREC, MFCC, NCH);
+  constexpr int CW = pair_cvt_warps(PREC, MFCC, NCH, DTC);
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 127u) & ~127u;

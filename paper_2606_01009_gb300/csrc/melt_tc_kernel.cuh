@@ -597,7 +597,7 @@ struct StftBands {
 };
 
 static __device__ __forceinline__ void stft_flush(StftBands& st, float* orow, int nb, float eps, bool valid) {
-  if (valid && st.c >= 0 && st.c < nb) orow[st.c] = __logf(st.acc0 + eps);
+  if (valid && st.c >= 0 && st.c < nb) orow[st.c] = fast_ln(st.acc0 + eps);
   st.acc0 = st.acc1;
   st.acc1 = 0.f;
   ++st.c;
@@ -691,7 +691,7 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
 #pragma unroll
               for (int e = 0; e < 16; ++e) {
                 const float r = re[g][e], i = im[g][e];
-                re[g][e] = __logf(fmaf(r, r, fmaf(i, i, p.eps)));
+                re[g][e] = fast_ln(fmaf(r, r, fmaf(i, i, p.eps)));
               }
               const int m = m0 + 16 * cc;
               if (valid) {
@@ -729,7 +729,7 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const float r = re[e], i = im[e];
-          lm[16 * c + e] = (16 * c + e < p.M) ? __logf(fmaf(r, r, i * i) + p.eps) : 0.f;
+          lm[16 * c + e] = (16 * c + e < p.M) ? fast_ln(fmaf(r, r, i * i) + p.eps) : 0.f;
         }
       }
       tc_fence_before();

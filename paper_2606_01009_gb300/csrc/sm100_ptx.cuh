@@ -19,6 +19,20 @@ static __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// Natural log for the epilogues: ln x = log2(x) ln 2, with log2 from the
+// hardware approximation (lg2.approx, flush-to-zero).  The epilogues take the
+// log of S + eps (eps > 0 by default, so the argument is normal); with eps = 0
+// an S below 2^-126 gives -inf.  Its error against the exact function is
+// checked on the GPU over every binade (melt_diag_log).  The flush-to-zero
+// form issues far fewer instructions than the denormal-handling one; in the
+// MFCC epilogue, where the log sits before the DCT on the critical path, it
+// measured 47 against 67 us per batch.
+static __device__ __forceinline__ float fast_ln(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y * 0.69314718055994531f;
+}
+
 static __device__ __forceinline__ uint64_t globaltimer() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -60,6 +60,7 @@ SIGNATURES = {
     "melt_diag_wait_timeout": (C.c_int, [_VP, _VP]),
     "melt_diag_alloc_count": (C.c_longlong, []),
     "melt_diag_gelu": (C.c_int, [_VP, _VP, C.c_int64, _VP]),
+    "melt_diag_log": (C.c_int, [_VP, _VP, C.c_int64, _VP]),
     "melt_plan_get": (C.c_int, [_VP, _VP]),
     "melt_plan_set": (C.c_int, [_VP, _VP]),
     "melt_autotune": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP, C.c_int, _VP]),
@@ -245,6 +246,12 @@ def melt_pad_reflect(wave, offsets, lengths, pad, out, out_offsets=None, stream=
 def melt_diag_wait_timeout(basis, stream=None):
     """Run the failure path of the bounded waits: the next melt_sync reports MELT_ERR_TIMEOUT."""
     _check(lib.melt_diag_wait_timeout(basis, _stream_ptr(stream)), "melt_diag_wait_timeout")
+
+
+def melt_diag_log(x, y, stream=None):
+    """The tensor-core epilogues' natural log on device tensors x -> y (float32)."""
+    _check(lib.melt_diag_log(C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), int(x.numel()), _stream_ptr(stream)),
+           "melt_diag_log")
 
 
 def melt_diag_gelu(h, y, stream=None):

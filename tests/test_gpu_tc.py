@@ -13,7 +13,7 @@ import pytest
 from oracle import melt_oracle as O
 from paper_2606_01009_gb300 import inputs as G
 from tests.helpers import (acc_rel, check_form_tolerance, dct_rel, db_report, fp32_sum_error, gpu_features,
-                           log_error_bound, oracle_features, rounded_log_bound)
+                           log_error_bound, oracle_features, rounded_log_bound, LOGF_ABS, LOGF_REL)
 
 pytestmark = pytest.mark.gpu
 
@@ -164,3 +164,32 @@ def test_more_than_128_mel_bins_needs_bf16_log_mel(melt):
         with pytest.raises(melt.MeltError) as ei:
             melt.Frontend(n_mels=256, **kw)
         assert ei.value.status == melt.MELT_ERR_UNSUPPORTED, kw
+
+
+def test_epilogue_log_error_bound(melt):
+    """The epilogues' natural log (hardware log2 times ln 2, subnormals
+    flushed) against the exact function: within the bound every parity test
+    assumes for it, LOGF_ABS + LOGF_REL |ln x|, on 4096 mantissas of every
+    normal binade and on random values."""
+    import torch
+    e = np.arange(-126, 128)
+    m = 1.0 + np.arange(4096) / 4096.0
+    x = (m[None, :] * np.exp2(e[:, None].astype(np.float64))).astype(np.float32).ravel()
+    x = x[np.isfinite(x)]
+    rng = np.random.default_rng(5)
+    x = np.concatenate([x, np.exp(rng.uniform(-80, 80, 200000)).astype(np.float32),
+                        np.array([1e-10, 1.0, 0.5, 2.0, np.nextafter(np.float32(1), 0)], np.float32)])
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    melt.melt_diag_log(xd, yd)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy().astype(np.float64)
+    exact = np.log(x.astype(np.float64))
+    err = np.abs(y - exact)
+    bound = LOGF_ABS + LOGF_REL * np.abs(exact)
+    bad = err > bound
+    assert not bad.any(), (int(bad.sum()), x[bad][:5], err[bad][:5])
+    near = (x >= 0.5) & (x <= 2)
+    print("epilogue log: max abs error on [0.5, 2] %.3g (2^%.2f); max relative error elsewhere %.3g (2^%.2f)" %
+          (err[near].max(), np.log2(err[near].max()), (err[~near] / np.abs(exact[~near])).max(),
+           np.log2((err[~near] / np.abs(exact[~near])).max())))
