@@ -360,7 +360,9 @@ def time_form(args, W, precision, steps, warmup, world, want_e2e):
     res = {"precision": precision, "T": T, "n_out": n_out, "copies": copies, "steps": steps,
            "ms_total": ms_total, "ms_per_step": ms_total / steps, "launch_ms": launch_ms,
            "value": value, "clocks": ck, "trials": trial_stats(trial_ms, steps), "step": step,
-           "out_sample": outs[0], "fe": fe}
+           "out_sample": outs[0], "fe": fe,
+           # `step` holds raw pointers into these buffers: they live as long as it does
+           "buffers": (waves, outs)}
 
     if want_e2e:
         # end to end through the public C ABI with pinned HOST buffers:
