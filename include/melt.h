@@ -219,6 +219,30 @@ melt_status melt_autotune_file(melt_basis* basis, const float* wave, const int64
 melt_status melt_forward(melt_basis* basis, const float* wave, const int64_t* offsets,
                          const int64_t* lengths, int batch, float* out, void* stream);
 
+/* Flags of melt_forward_ex. */
+enum { MELT_FWD_INPUT_READY = 1 };
+
+/*
+ * melt_forward_ex - melt_forward with call flags; the features are the same
+ *   (Eq. 8 / Eq. 9), bit for bit.  Every tensor-core launch may start while
+ *   the kernel before it on `stream` is still running (programmatic dependent
+ *   launch); by default each of its roles that reads the waveform waits for
+ *   that kernel to finish first.
+ *   flags  0 or MELT_FWD_INPUT_READY.  With MELT_FWD_INPUT_READY the caller
+ *          states that no kernel enqueued on `stream` since the host last
+ *          synchronised with it writes `wave` (the samples came from copies,
+ *          from work on other streams that `stream` waits for through events,
+ *          or from work already synchronised).  The launch then stages and
+ *          converts samples, and runs its MMAs, while the preceding kernel
+ *          drains; it still stores features only after that kernel has
+ *          finished.  A batch produced by a kernel on `stream` (for example
+ *          melt_pad_reflect) must not use the flag.  The FP32 form and the
+ *          dynamic pair schedule ignore it.
+ *   Other arguments and errors as melt_forward; MELT_ERR_ARG for an unknown flag.
+ */
+melt_status melt_forward_ex(melt_basis* basis, const float* wave, const int64_t* offsets,
+                            const int64_t* lengths, int batch, float* out, void* stream, unsigned flags);
+
 /*
  * melt_forward_noalloc - melt_forward without any allocation at call time.
  *   The paper has no counterpart: this entry point exists for callers that

@@ -285,7 +285,7 @@ melt_status stage_plan(melt_basis* b, const int64_t* offsets, const int64_t* len
 
 melt_status forward_impl(melt_basis* b, const float* wave, const int64_t* offsets,
                          const int64_t* lengths, int batch, float* out, void* stream_v,
-                         int mode) {
+                         int mode, unsigned flags = 0) {
   if (!b || batch < 0 || (batch > 0 && (!lengths || !wave || !out))) return MELT_ERR_ARG;
   if (((uintptr_t)wave & 15) || ((uintptr_t)out & 15)) return MELT_ERR_ARG;
   if (batch == 0) return MELT_OK;
@@ -317,6 +317,7 @@ melt_status forward_impl(melt_basis* b, const float* wave, const int64_t* offset
     L.dct = b->d_dct; L.n_mfcc = b->n_mfcc; L.eps = (float)b->eps; L.err = b->d_err;
     L.sm_count = b->sm_count;
     L.mlp = mode == 0 ? b->correction : nullptr;
+    L.early_inputs = (flags & MELT_FWD_INPUT_READY) != 0;
     L.fused = &fused;
     L.fb = b->d_fb;
     L.stft_bands = b->stft_bands;
@@ -633,6 +634,12 @@ melt_status melt_basis_get_fp64(const melt_basis* b, double* freqs, double* w) {
 melt_status melt_forward(melt_basis* basis, const float* wave, const int64_t* offsets,
                          const int64_t* lengths, int batch, float* out, void* stream) {
   return forward_impl(basis, wave, offsets, lengths, batch, out, stream, 0);
+}
+
+melt_status melt_forward_ex(melt_basis* basis, const float* wave, const int64_t* offsets,
+                            const int64_t* lengths, int batch, float* out, void* stream, unsigned flags) {
+  if (flags & ~(unsigned)MELT_FWD_INPUT_READY) return MELT_ERR_ARG;
+  return forward_impl(basis, wave, offsets, lengths, batch, out, stream, 0, flags);
 }
 
 melt_status melt_forward_components(melt_basis* basis, const float* wave,

@@ -535,6 +535,9 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
   p.n_out = L.stft_bands ? L.stft_bands : L.n_mfcc ? L.n_mfcc : tb->n_mels;
   p.fb = L.fb;
   p.stft_bands = L.stft_bands;
+  // the dynamic pair schedule claims pairs from a counter an earlier launch
+  // resets when it ends, so its waveform producer keeps the wait
+  p.early_inputs = L.early_inputs && L.pdl && !p.dyn ? 1 : 0;
   const bool fused = pair && p.Hd > 0 && L.mlp != nullptr;
   if (pair && p.Hd > 0 && !L.mlp) p.Hd = 0;  // plan made for a correction that is not passed
   KernelFn fn = fused ? kernel_for_pair_mlp(p.MP / 16)

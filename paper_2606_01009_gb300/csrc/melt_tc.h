@@ -57,6 +57,7 @@ struct TcLaunch {
   int* err;
   int sm_count;
   bool pdl = true;    // launch with programmatic stream serialisation
+  bool early_inputs = false;  // MELT_FWD_INPUT_READY: waveform readers need not wait (not with the dynamic schedule)
   const melt_mlp* mlp = nullptr;  // correction attached to the basis (fused when the layout allows)
   const float4* fb = nullptr;     // fused STFT + Mel comparator: per-bin filterbank entries (device)
   int stft_bands = 0;

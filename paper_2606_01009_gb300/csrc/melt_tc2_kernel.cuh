@@ -1234,6 +1234,10 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH, DTC), 1)
   // producer waits before it reads the fused MLP's weight image); the roles
   // that read tiles or the waveform, or write features, wait for the
   // previous kernel of the stream first (programmatic dependent launch).
+  // With early_inputs (the caller stated that no kernel still in flight
+  // writes the waveform) the waveform producer and the converters skip that
+  // wait, so a launch fills and converts its first tiles while the previous
+  // one drains; the epilogue, which stores features, always waits.
   if (warp == kPMmaWarp) {
     if (lane == 0) {
       if (c.rank == 0) pair_mma<MLP, PREC, DTC>(p, gbase, c, B, tmem_base);
@@ -1244,11 +1248,11 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH, DTC), 1)
     if (lane == 0) pair_basis_producer(p, c, B);
     __syncwarp();
   } else if (warp == kPProdWarp) {
-    pdl_wait();
+    if (!p.early_inputs) pdl_wait();
     if (lane == 0) pair_wave_producer(p, c, B);
     __syncwarp();
   } else if (warp >= kPCvtWarp0) {
-    pdl_wait();
+    if (!p.early_inputs) pdl_wait();
     if constexpr (PREC == MELT_FP8E4M3)
       pair_convert_fp8<CW>(p, gbase, c, B, kPCvtWarp0, tmem_base);
     else

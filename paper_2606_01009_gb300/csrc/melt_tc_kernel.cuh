@@ -107,6 +107,10 @@ struct TcParams {
   int stft_bands;
   uint32_t off_fb;
   uint32_t desc_hi;      // high word of every operand descriptor (SBO = 128 B, version)
+  // 1: the caller stated that no kernel still in flight on the stream writes
+  // the waveform (MELT_FWD_INPUT_READY), so the roles that read it start
+  // without waiting for the preceding kernel; the epilogue still waits
+  int early_inputs;
   uint32_t off_a, off_b, off_bar, off_misc, off_tab, off_dct;
   uint32_t smem_total;   // dynamic shared memory bytes (incl. alignment slack)
   // CTA-pair kernel only: FP32 span staging ring and the half-basis layout
@@ -810,7 +814,9 @@ __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_const
   // The MMA issuer and the basis producer touch only this launch's own
   // basis and shared memory, so they start at once; every role that reads
   // the tile list, the waveform or writes features first waits for the
-  // previous kernel of the stream (programmatic dependent launch).
+  // previous kernel of the stream (programmatic dependent launch), except
+  // that the converters skip that wait when the caller stated that the
+  // waveform is not written by a kernel still in flight (early_inputs).
   if (warp == kMmaWarp) {
     if (lane == 0) role_mma<PREC>(p, gbase, sbase, B, tmem_base, abort);
     __syncwarp();
@@ -818,7 +824,7 @@ __global__ void __launch_bounds__(kThreads, 1) melt_tc_kernel(const __grid_const
     if (lane == 0) role_basis_producer(p, sbase, B, abort);
     __syncwarp();
   } else if (warp >= kCvtWarp0) {
-    pdl_wait();
+    if (!p.early_inputs) pdl_wait();
     role_convert_bf16<PREC>(p, sbase, B, abort);
     __syncwarp();
   } else {

@@ -28,6 +28,8 @@ MELT_WIN_HANN_SYMMETRIC = 1
 MELT_MAX_GROUPS = 16
 MELT_GROUP_NO_GRAPH = 1
 
+MELT_FWD_INPUT_READY = 1
+
 MELT_FP32 = 0
 MELT_BF16 = 1
 MELT_BF16X3 = 2
@@ -51,6 +53,7 @@ SIGNATURES = {
     "melt_basis_info": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "melt_basis_get_fp64": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "melt_forward": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
+    "melt_forward_ex": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP, C.c_uint]),
     "melt_stft_create": (C.c_int, [C.c_double, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                    C.c_int, C.c_int, C.c_double, C.POINTER(_VP)]),
     "melt_forward_components": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
@@ -220,6 +223,17 @@ def melt_forward(basis, wave, offsets, lengths, out, stream=None, batch=None):
     outp = out if isinstance(out, int) else out.data_ptr()
     _check(lib.melt_forward(basis, C.c_void_p(wp), op, lp, b, C.c_void_p(outp), _stream_ptr(stream)),
            "melt_forward")
+
+
+def melt_forward_ex(basis, wave, offsets, lengths, out, flags, stream=None):
+    """melt_forward with call flags (MELT_FWD_INPUT_READY: no kernel enqueued on
+    the stream since the last host synchronisation writes ``wave``)."""
+    lens, lp = _i64(lengths)
+    offs, op = _i64(offsets)
+    wp = wave if isinstance(wave, int) else wave.data_ptr()
+    outp = out if isinstance(out, int) else out.data_ptr()
+    _check(lib.melt_forward_ex(basis, C.c_void_p(wp), op, lp, int(lens.shape[0]), C.c_void_p(outp),
+                               _stream_ptr(stream), int(flags)), "melt_forward_ex")
 
 
 def melt_forward_noalloc(basis, wave, offsets, lengths, out, stream=None):
@@ -512,7 +526,10 @@ class Frontend:
     def total_frames(self, lengths) -> int:
         return sum(self.num_frames(int(L)) for L in lengths)
 
-    def __call__(self, wave, offsets, lengths, out=None, stream=None):
+    def __call__(self, wave, offsets, lengths, out=None, stream=None, input_ready=False):
+        """Features of a batch.  input_ready=True passes MELT_FWD_INPUT_READY
+        (no kernel enqueued on the stream since the last host synchronisation
+        writes ``wave``); centred framing pads with a kernel and ignores it."""
         import torch
         if out is None:
             out = torch.empty((self.total_frames(lengths), self.n_out), device=wave.device,
@@ -524,7 +541,10 @@ class Frontend:
             melt_pad_reflect(wave, offsets, lengths, self.pad, self._pad_buf, offs, stream)
             melt_forward(self.handle, self._pad_buf, offs, lens, out, stream)
             return out
-        melt_forward(self.handle, wave, offsets, lengths, out, stream)
+        if input_ready:
+            melt_forward_ex(self.handle, wave, offsets, lengths, out, MELT_FWD_INPUT_READY, stream)
+        else:
+            melt_forward(self.handle, wave, offsets, lengths, out, stream)
         return out
 
     def sync(self, stream=None):
