@@ -309,8 +309,7 @@ melt_status forward_impl(melt_basis* b, const float* wave, const int64_t* offset
     p.n_fft = b->n_fft; p.hop = b->hop; p.n_mels = b->n_mels; p.mp = b->mp;
     p.n_mfcc = b->n_mfcc; p.n_out = b->n_mfcc ? b->n_mfcc : b->n_mels;
     p.eps = (float)b->eps; p.mode = mode;
-    const int grid = std::min(n_tiles, b->sm_count * 1);
-    e = launch_simt(p, b->mj, grid, stream);
+    e = launch_simt(p, b->mj, b->sm_count, stream);
   } else {
     TcLaunch L;
     L.wave = wave; L.tiles = slot->dev; L.n_tiles = n_tiles; L.out = out;
@@ -396,7 +395,7 @@ melt_status launch_forward_tiles(melt_basis* b, const float* wave, const TileDes
     p.n_fft = b->n_fft; p.hop = b->hop; p.n_mels = b->n_mels; p.mp = b->mp;
     p.n_mfcc = b->n_mfcc; p.n_out = b->n_mfcc ? b->n_mfcc : b->n_mels;
     p.eps = (float)b->eps; p.mode = 0;
-    e = launch_simt(p, b->mj, std::min(n_tiles, b->sm_count), stream);
+    e = launch_simt(p, b->mj, b->sm_count, stream);
   } else {
     TcLaunch L;
     L.wave = wave; L.tiles = d_tiles; L.n_tiles = n_tiles; L.out = out;

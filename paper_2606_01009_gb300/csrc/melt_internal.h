@@ -57,7 +57,8 @@ inline cudaError_t host_alloc_pinned(T** p, size_t bytes) {
 }
 
 // Launch the FP32 SIMT kernel for `p` (grid picked by the caller).
-cudaError_t launch_simt(const SimtParams& p, int mj, int grid, cudaStream_t stream);
+// Persistent launch: as many CTAs as fit on sm_count SMs (at most one per tile).
+cudaError_t launch_simt(const SimtParams& p, int mj, int sm_count, cudaStream_t stream);
 int simt_smem_bytes(int mj, int n_mels, int n_mfcc);
 
 }  // namespace melt

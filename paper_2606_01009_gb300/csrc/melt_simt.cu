@@ -9,9 +9,12 @@
 // of 8) x 16 (mel lanes); thread (ty, tx) owns frames 8ty..8ty+7 and mels
 // tx + 16j, j < MJ, for both R and I (16*MJ FP32 accumulators).
 // K loop in chunks of 32 samples: the chunk of the frame matrix is
-// transposed into shared memory (Xs[k][f]) with coalesced loads, the basis
-// chunk (row-major [k][2*mp], R/I interleaved) is copied beside it; the next
-// chunk's loads are in flight while the current one is computed.
+// transposed into shared memory (Xs[k][f]) by asynchronous copies with
+// coalesced reads, the basis chunk (row-major [k][2*mp], R/I interleaved) is
+// copied beside it; the next chunk's copies are in flight while the current
+// one is computed.
+#include <algorithm>
+
 #include "melt_internal.h"
 
 namespace melt {
@@ -23,67 +26,74 @@ constexpr int kKC = 32;          // samples per K chunk
 constexpr int kXPad = 4;         // Xs row padding (keeps float4 alignment)
 constexpr int kThreads = 256;
 
-// K chunks are double-buffered: the global loads of chunk c + 1 are issued
-// into registers before chunk c is computed and stored into the other
-// shared-memory buffer after it, so one barrier per chunk separates them and
-// the loads' latency hides behind the FFMAs.
+// K chunks are double-buffered with asynchronous copies (cp.async): the
+// copies of chunk c + 1 are issued into the other shared-memory buffer before
+// chunk c is computed, so their latency hides behind the FFMAs and no
+// registers hold them in flight.  That leaves room for two CTAs per SM (four
+// warps per scheduler) where the accumulators allow (MJ <= 5).
 template <int MJ>
 struct SimtChunk {
   static constexpr int kXq = kF * kKC / kThreads;        // frame samples per thread (16)
   static constexpr int kWq = (kKC * 2 * 16 * MJ / 4 + kThreads - 1) / kThreads;  // basis float4s per thread
-  float x[kXq];
-  float4 w[kWq];
 };
 
+static __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+
+static __device__ __forceinline__ void cp_async16(float* dst, const float* src, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+
+static __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Waits until at most one group (the newest) of this thread is in flight.
+static __device__ __forceinline__ void cp_async_wait_all_but_newest() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+// Copies of K chunk [k0, k0 + kKC) of a tile: the frame chunk transposed into
+// Xs[k][f] (4-byte copies; lanes take consecutive samples of a frame, so the
+// global reads coalesce), the basis chunk into Ws[k][2 mp] (16-byte copies).
+// Samples past the tile's frames or past N, and basis rows past N, are
+// zero-filled (source size 0; the source address stays inside the buffer).
 template <int MJ>
-static __device__ __forceinline__ void simt_load_chunk(const SimtParams& p, const TileDesc& td, int k0, int tid,
-                                                       SimtChunk<MJ>& c) {
+static __device__ __forceinline__ void simt_copy_chunk(const SimtParams& p, const TileDesc& td, int k0, int tid,
+                                                       float* Xs, float* Ws) {
   const int N = p.n_fft, H = p.hop, W2 = 2 * p.mp, row4 = W2 / 4;
 #pragma unroll
   for (int i = 0; i < SimtChunk<MJ>::kXq; ++i) {
     const int idx = tid + i * kThreads;
     const int k = idx % kKC, f = idx / kKC;
     const int n = k0 + k;
-    c.x[i] = (f < td.n_frames && n < N) ? __ldg(p.wave + td.in_off + (int64_t)f * H + n) : 0.f;
-  }
-#pragma unroll
-  for (int i = 0; i < SimtChunk<MJ>::kWq; ++i) {
-    const int idx = tid + i * kThreads;
-    const int k = idx / row4, c4 = idx - k * row4;
-    c.w[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (idx < kKC * row4 && k0 + k < N) c.w[i] = __ldg(reinterpret_cast<const float4*>(p.w32 + (size_t)(k0 + k) * W2) + c4);
-  }
-}
-
-template <int MJ>
-static __device__ __forceinline__ void simt_store_chunk(const SimtParams& p, int tid, const SimtChunk<MJ>& c,
-                                                        float* Xs, float* Ws) {
-  const int W2 = 2 * p.mp, row4 = W2 / 4;
-#pragma unroll
-  for (int i = 0; i < SimtChunk<MJ>::kXq; ++i) {
-    const int idx = tid + i * kThreads;
-    Xs[(idx % kKC) * (kF + kXPad) + idx / kKC] = c.x[i];
+    const bool ok = f < td.n_frames && n < N;
+    cp_async4(Xs + k * (kF + kXPad) + f, p.wave + (ok ? td.in_off + (int64_t)f * H + n : td.in_off), ok);
   }
 #pragma unroll
   for (int i = 0; i < SimtChunk<MJ>::kWq; ++i) {
     const int idx = tid + i * kThreads;
     if (idx < kKC * row4) {
       const int k = idx / row4, c4 = idx - k * row4;
-      reinterpret_cast<float4*>(Ws + k * W2)[c4] = c.w[i];
+      const bool ok = k0 + k < N;
+      cp_async16(Ws + k * W2 + 4 * c4, p.w32 + (size_t)(ok ? k0 + k : 0) * W2 + 4 * c4, ok);
     }
   }
 }
 
 template <int MJ>
-__global__ void __launch_bounds__(kThreads, 1) melt_simt_kernel(SimtParams p) {
+__global__ void __launch_bounds__(kThreads, MJ <= 5 ? 2 : 1) melt_simt_kernel(SimtParams p) {
   extern __shared__ __align__(16) float smem[];
   constexpr int kXs = kKC * (kF + kXPad);
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int N = p.n_fft, M = p.n_mels, W2 = 2 * p.mp;
   const int kWs = kKC * W2;
-  float* Xbuf[2] = {smem, smem + kXs + kWs};          // [kKC][kF + kXPad], then the basis chunk [kKC][2 mp]
-  float* Wbuf[2] = {smem + kXs, smem + 2 * kXs + kWs};
+  // chunk buffer b: the frame chunk [kKC][kF + kXPad] at smem + b (kXs + kWs),
+  // the basis chunk [kKC][2 mp] after it (addressed arithmetically: an array
+  // of pointers indexed by b would live in local memory)
+  const int kBuf = kXs + kWs;
 
   for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
     const TileDesc td = p.tiles[tile];
@@ -93,17 +103,19 @@ __global__ void __launch_bounds__(kThreads, 1) melt_simt_kernel(SimtParams p) {
 #pragma unroll
       for (int j = 0; j < MJ; ++j) acc[i][j][0] = acc[i][j][1] = 0.f;
 
-    SimtChunk<MJ> nxt;
-    simt_load_chunk<MJ>(p, td, 0, tid, nxt);
     __syncthreads();  // the previous tile's readers of both buffers (and the MFCC staging) are done
-    simt_store_chunk<MJ>(p, tid, nxt, Xbuf[0], Wbuf[0]);
-    __syncthreads();
+    simt_copy_chunk<MJ>(p, td, 0, tid, smem, smem + kXs);
+    cp_async_commit();
     int b = 0;
     for (int k0 = 0; k0 < N; k0 += kKC, b ^= 1) {
-      const bool more = k0 + kKC < N;
-      if (more) simt_load_chunk<MJ>(p, td, k0 + kKC, tid, nxt);
-      const float* Xs = Xbuf[b];
-      const float* Ws = Wbuf[b];
+      // the next chunk's copies go to the other buffer, whose last readers
+      // passed the barrier at the end of the previous chunk
+      if (k0 + kKC < N) simt_copy_chunk<MJ>(p, td, k0 + kKC, tid, smem + (b ^ 1) * kBuf, smem + (b ^ 1) * kBuf + kXs);
+      cp_async_commit();  // (an empty group after the last chunk)
+      cp_async_wait_all_but_newest();
+      __syncthreads();    // every thread's copies of this chunk have landed
+      const float* Xs = smem + b * kBuf;
+      const float* Ws = Xs + kXs;
       const int kn = min(kKC, N - k0);
 #pragma unroll 4
       for (int k = 0; k < kn; ++k) {
@@ -120,10 +132,7 @@ __global__ void __launch_bounds__(kThreads, 1) melt_simt_kernel(SimtParams p) {
           }
         }
       }
-      if (more) {
-        simt_store_chunk<MJ>(p, tid, nxt, Xbuf[b ^ 1], Wbuf[b ^ 1]);  // its last readers finished a chunk ago
-        __syncthreads();
-      }
+      __syncthreads();  // this buffer's readers are done before it is refilled
     }
 
     // ---- epilogue: power (Eq. 7), log (Eq. 8), optional DCT-II (Eq. 9)
@@ -197,25 +206,29 @@ int simt_smem_bytes(int mj, int n_mels, int n_mfcc) {
 }
 
 template <int MJ>
-static cudaError_t launch_mj(const SimtParams& p, int grid, cudaStream_t stream) {
+static cudaError_t launch_mj(const SimtParams& p, int sm_count, cudaStream_t stream) {
   const int smem = simt_smem_bytes(MJ, p.n_mels, p.n_mfcc);
   cudaError_t e = cudaFuncSetAttribute(melt_simt_kernel<MJ>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
+  int per_sm = 1;  // persistent: as many CTAs as can be resident at once
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, melt_simt_kernel<MJ>, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(p.n_tiles, std::max(1, per_sm) * sm_count);
   melt_simt_kernel<MJ><<<grid, kThreads, smem, stream>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_simt(const SimtParams& p, int mj, int grid, cudaStream_t stream) {
+cudaError_t launch_simt(const SimtParams& p, int mj, int sm_count, cudaStream_t stream) {
   switch (mj) {
-    case 1: return launch_mj<1>(p, grid, stream);
-    case 2: return launch_mj<2>(p, grid, stream);
-    case 3: return launch_mj<3>(p, grid, stream);
-    case 4: return launch_mj<4>(p, grid, stream);
-    case 5: return launch_mj<5>(p, grid, stream);
-    case 6: return launch_mj<6>(p, grid, stream);
-    case 7: return launch_mj<7>(p, grid, stream);
-    case 8: return launch_mj<8>(p, grid, stream);
+    case 1: return launch_mj<1>(p, sm_count, stream);
+    case 2: return launch_mj<2>(p, sm_count, stream);
+    case 3: return launch_mj<3>(p, sm_count, stream);
+    case 4: return launch_mj<4>(p, sm_count, stream);
+    case 5: return launch_mj<5>(p, sm_count, stream);
+    case 6: return launch_mj<6>(p, sm_count, stream);
+    case 7: return launch_mj<7>(p, sm_count, stream);
+    case 8: return launch_mj<8>(p, sm_count, stream);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -316,7 +316,10 @@ int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap
     // for it (M = 128, two A buffers, 2 slots: 58 us against 66 us without,
     // and 63 us with one A buffer and more slots), but costs time where the
     // ring is deep enough (M = 80, 5 slots: 42.5 against 42.1 us) and with
-    // the correction fused (167 against 164 us).  FP8 runs in CTA pairs only
+    // the correction fused (167 against 164 us).  When launches overlap
+    // (MELT_FWD_INPUT_READY) the stream pays at M = 80 too (BF16 log-Mel:
+    // 37.4 against 38.1 us; FP8: 52.1 against 51.3 us, so not for FP8).
+    // FP8 runs in CTA pairs only
     // (its converter is the polyphase one with a per-row scale).  The static
     // schedule is the default: the dynamic one measured no gain (42.6 against
     // 42.4 us).
@@ -324,7 +327,8 @@ int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap
       melt_plan pc{1, zb, 0, p.KS, 1, 1, kDefaultSchedule};
       TcParams q = p;
       if (n < cap && try_layout_pair(tb, q, pc, tb->n_mfcc) && q.NS >= 2) {
-        if (q.NS < 4 && !tb->mlp_hd) pc.prefetch_tiles = kDefaultSchedule ? 0 : 1;
+        const bool bf16_logmel = tb->precision == MELT_BF16 && tb->n_mfcc == 0;
+        if ((q.NS < 4 || bf16_logmel) && !tb->mlp_hd) pc.prefetch_tiles = kDefaultSchedule ? 0 : 1;
         out[n++] = pc;
         // the other pair schedule, for melt_autotune (after every default layout)
         melt_plan alt = pc;

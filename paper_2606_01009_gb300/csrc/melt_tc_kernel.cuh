@@ -671,18 +671,23 @@ __device__ void role_epilogue(const TcParams& p, uint8_t* gbase, uint32_t sbase,
             warp_arrive(sbase + p.off_bar + 8 * (B.t_empty + acc));
           }
           if constexpr (STFT) {
-            // the comparator: |X_k|^2 of DFT bin k into the triangular bands, in bin order
+            // the comparator: |X_k|^2 of DFT bin k into the triangular bands, in
+            // bin order.  Every loop over the chunk's registers is fully
+            // unrolled: a runtime index would move re/im to local memory.
             const float4* fbs = reinterpret_cast<const float4*>(gbase + p.off_fb);
+#pragma unroll
+            for (int g = 0; g < kEpiGroup; ++g) {
+#pragma unroll
+              for (int e = 0; e < 16; ++e) re[g][e] = fmaf(re[g][e], re[g][e], im[g][e] * im[g][e]);
+            }
 #pragma unroll
             for (int g = 0; g < kEpiGroup; ++g) {
               const int cc = c0 + g;
               if (cc < nch) {
-#pragma unroll 4
+#pragma unroll
                 for (int e = 0; e < 16; ++e) {
                   const int kbin = m0 + 16 * cc + e;
-                  if (kbin < p.M)
-                    stft_bin(stb, fbs, kbin, fmaf(re[g][e], re[g][e], im[g][e] * im[g][e]), orow, p.stft_bands,
-                             p.eps, valid);
+                  if (kbin < p.M) stft_bin(stb, fbs, kbin, re[g][e], orow, p.stft_bands, p.eps, valid);
                 }
               }
             }
