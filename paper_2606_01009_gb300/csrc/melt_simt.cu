@@ -116,9 +116,11 @@ __global__ void __launch_bounds__(kThreads, MJ <= 5 ? 2 : 1) melt_simt_kernel(Si
       __syncthreads();    // every thread's copies of this chunk have landed
       const float* Xs = smem + b * kBuf;
       const float* Ws = Xs + kXs;
-      const int kn = min(kKC, N - k0);
-#pragma unroll 4
-      for (int k = 0; k < kn; ++k) {
+      // every chunk runs all kKC samples: past N both operands were
+      // zero-filled, so those products add exact zeros (a compile-time
+      // trip count lets every shared-memory offset be an immediate)
+#pragma unroll 8
+      for (int k = 0; k < kKC; ++k) {
         const float4 xa = *reinterpret_cast<const float4*>(Xs + k * (kF + kXPad) + ty * 8);
         const float4 xb = *reinterpret_cast<const float4*>(Xs + k * (kF + kXPad) + ty * 8 + 4);
         const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
