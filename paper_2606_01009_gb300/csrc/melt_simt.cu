@@ -62,7 +62,8 @@ static __device__ __forceinline__ void cp_async_wait_all_but_newest() {
 template <int MJ>
 static __device__ __forceinline__ void simt_copy_chunk(const SimtParams& p, const TileDesc& td, int k0, int tid,
                                                        float* Xs, float* Ws) {
-  const int N = p.n_fft, H = p.hop, W2 = 2 * p.mp, row4 = W2 / 4;
+  const int N = p.n_fft, H = p.hop;
+  constexpr int W2 = 32 * MJ, row4 = W2 / 4;  // 2 mp basis values per sample (mp = 16 MJ)
 #pragma unroll
   for (int i = 0; i < SimtChunk<MJ>::kXq; ++i) {
     const int idx = tid + i * kThreads;
@@ -88,12 +89,15 @@ __global__ void __launch_bounds__(kThreads, MJ <= 5 ? 2 : 1) melt_simt_kernel(Si
   constexpr int kXs = kKC * (kF + kXPad);
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int N = p.n_fft, M = p.n_mels, W2 = 2 * p.mp;
-  const int kWs = kKC * W2;
+  const int N = p.n_fft, M = p.n_mels;
+  // compile-time strides (mp = 16 MJ): every shared-memory offset of the
+  // unrolled K loop is an immediate
+  constexpr int W2 = 32 * MJ;
+  constexpr int kWs = kKC * W2;
   // chunk buffer b: the frame chunk [kKC][kF + kXPad] at smem + b (kXs + kWs),
   // the basis chunk [kKC][2 mp] after it (addressed arithmetically: an array
   // of pointers indexed by b would live in local memory)
-  const int kBuf = kXs + kWs;
+  constexpr int kBuf = kXs + kWs;
 
   for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
     const TileDesc td = p.tiles[tile];

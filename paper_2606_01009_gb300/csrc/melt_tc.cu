@@ -155,30 +155,42 @@ bool try_layout(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) 
 }
 
 // CTA-pair layout (BF16, FP8): A buffers, the waveform staging ring and this
-// CTA's half of the basis (resident), then barriers and tables.  The ring
-// takes every slot that still fits (2..8).
+// CTA's half of the basis (resident, or streamed through NB slots of kps
+// K-steps), then barriers and tables.  The ring takes every slot that still
+// fits (2..8).  A streamed half basis serves the BF16 and split-BF16 log-Mel
+// kernels with the static schedule (no fused MLP, no MFCC); split BF16 runs
+// in pairs only that way (hi + lo halves do not fit resident beside two
+// split A buffers).
 bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_mfcc) {
   const bool fp8 = tb->precision == MELT_FP8E4M3;
-  if (c.cta_pair != 1 || (tb->precision != MELT_BF16 && !fp8) || !tb->d_b2 || p.nblk > 1 || tb->stft_bands > 0)
+  const bool x3 = tb->precision == MELT_BF16X3;
+  if (c.cta_pair != 1 || (tb->precision != MELT_BF16 && !fp8 && !x3) || !tb->d_b2 || p.nblk > 1 ||
+      tb->stft_bands > 0)
     return false;
   // FP8: a converter lane holds at most two quads of a Z row
   if (fp8 && p.H > 256) return false;
-  if (c.basis_resident != 1 || c.a_buffers < 1 || c.a_buffers > 2) return false;
+  if (c.basis_resident < 0 || c.basis_resident > 1 || c.a_buffers < 1 || c.a_buffers > 2) return false;
   if (c.prefetch_tiles < 0 || c.prefetch_tiles > kMaxPrefetch) return false;
   if (c.schedule != 0 && c.schedule != 1) return false;
+  const bool streamed = c.basis_resident == 0;
+  if (streamed && (fp8 || c.schedule != 0 || n_mfcc != 0 || tb->mlp_hd > 0 || c.basis_slots < 2 ||
+                   c.basis_slots > 8 || c.ksteps_per_slot < 1 || c.ksteps_per_slot > 16))
+    return false;
+  if (x3 && (!streamed || n_mfcc != 0)) return false;
   p.dyn = c.schedule;
-  p.b_resident = 1;
+  p.b_resident = streamed ? 0 : 1;
   p.blk_step = p.blk_step_last = 0;
   p.ZB = c.a_buffers;
   p.pf = c.schedule ? 0 : c.prefetch_tiles;  // L2 prefetch stream of the waveform producer (static schedule)
-  p.kps = 1;
-  p.NB = p.KS;
-  p.step_bytes = p.kstep_bytes / 2;  // one K-step block of this CTA's N/2 basis rows
-  p.bslot_bytes = p.step_bytes;
+  // one K-step block of this CTA's N/2 basis rows (split BF16: hi, then lo)
+  p.step_bytes = p.kstep_bytes / 2 * (x3 ? 2 : 1);
+  p.kps = streamed ? std::min(c.ksteps_per_slot, p.KS) : 1;
+  p.NB = streamed ? c.basis_slots : p.KS;
+  p.bslot_bytes = p.step_bytes * (uint32_t)p.kps;
   p.b_lbo = (uint32_t)(p.NC / 2) * 16;
   // fused correction MLP: its weight half in shared memory, one projection
   // accumulator in TMEM and the MLP's operands beside it
-  p.Hd = fp8 ? 0 : tb->mlp_hd;
+  p.Hd = fp8 || x3 || streamed ? 0 : tb->mlp_hd;
   // TMEM: two projection accumulators 256 columns apart when room is left
   // beside the first for FP8's scale-factor columns (sfg groups of four per A
   // buffer, then kSfBCols for the basis scale), else one
@@ -247,6 +259,9 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
     const int max_rows = kPQuads * kPCvtThreads * 4 / p.H;
     if (ch > max_rows) ch = std::max(1, max_rows);
     chs[nch_c++] = ch;
+    // smaller chunks where the 16 KB ones leave no room for a ring of two
+    // (split BF16's two A parts, long frames)
+    for (int c2 = ch / 2; c2 >= 4 && nch_c < 3; c2 /= 2) chs[nch_c++] = c2;
   }
   p.codes_stride = fp8 ? align_up((uint32_t)p.zrows + 3, 16) : 0u;
   for (int ci = 0; ci < nch_c; ++ci) {
@@ -255,14 +270,14 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
     p.NCHUNK = (p.zrows + ch - 1) / ch;
     p.st_bytes = row_bytes * ch;
     for (int ns = 8; ns >= 2; --ns) {
-      const PairBars B(ns, p.ZB, p.KS);
+      const PairBars B(ns, p.ZB, p.KS, streamed ? p.NB : 0);
       uint32_t off = 0;
       p.off_a = off;
       off += align_up(p.abuf_bytes * p.ZB, 128);
       p.off_st = off;
       off += align_up(p.st_bytes * ns, 128);
       p.off_b = off;
-      off += align_up(p.step_bytes * p.KS, 128);
+      off += align_up(streamed ? p.bslot_bytes * p.NB : p.step_bytes * p.KS, 128);
       p.off_mlp = off;
       off += p.Hd > 0 ? align_up(p.mlp_half, 128) : 0u;
       p.off_bar = off;
@@ -349,6 +364,27 @@ int candidate_list(const TcBasis* tb, const TcParams& p, melt_plan* out, int cap
   add(1, 1, 2, p.KS, 1);
   for (int kps = kps_hi; kps >= 1; --kps) add(0, 1, 2, 2, kps);
   for (int nb = 24; nb >= 2; nb -= 2) add(0, 1, 2, nb, 1);
+  if ((tb->precision == MELT_BF16 || tb->precision == MELT_BF16X3) && tb->d_b2 && tb->n_mfcc == 0 &&
+      !tb->mlp_hd) {
+    // CTA pairs with each CTA's half basis streamed through slots (split
+    // BF16, long frames): a 2-SM MMA shares every basis block between two
+    // tiles, so each tile reads half the basis a single-CTA layout streams.
+    // Measured no faster than the single-CTA streamed layouts (64 x 30 s
+    // split BF16: 86.6 against 83.4 us; 64 x 20 s at 22.05 kHz, N = 1024:
+    // 51.2 against 51.1 us): each slot's turnaround (copy from L2, the odd
+    // CTA's signal, the MMAs' release) is the limit, not L2 traffic.  So
+    // they come after the single-CTA layouts, for melt_autotune.
+    const int shapes[][2] = {{4, 4}, {4, 2}, {3, 4}, {2, 8}, {3, 2}, {2, 4}, {2, 2}, {2, 1}};
+    for (int zb = 2; zb >= 1; --zb)
+      for (const auto& sh : shapes) {
+        melt_plan pc{0, zb, 0, sh[0], sh[1], 1, 0};
+        TcParams q = p;
+        if (n < cap && try_layout_pair(tb, q, pc, 0) && q.NS >= 2) {
+          if (q.NS < 4) pc.prefetch_tiles = 1;
+          out[n++] = pc;
+        }
+      }
+  }
   for (int i = 0; i < n_alt && n < cap; ++i) out[n++] = alts[i];
   return n;
 }
@@ -440,18 +476,22 @@ melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64) {
     if (cudaMemcpy(tb->d_b, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
       return MELT_ERR_CUDA;
   }
-  if ((P == MELT_BF16 || P == MELT_FP8E4M3) && nblk == 1) {
+  if ((P == MELT_BF16 || P == MELT_FP8E4M3 || P == MELT_BF16X3) && nblk == 1) {
     // CTA-pair image: the K-step blocks of basis rows [0, MP) (W_r), then those
     // of rows [MP, 2 MP) (W_i); each block is 2 core columns x MP rows x 16 B
+    // per part (split BF16: the hi part, then the lo part)
     const size_t half_step = (size_t)MP * 32;
-    std::vector<uint8_t> img2((size_t)2 * KS * half_step, 0);
+    std::vector<uint8_t> img2((size_t)2 * KS * parts * half_step, 0);
     for (int h = 0; h < 2; ++h)
       for (int s = 0; s < KS; ++s)
-        for (int cc = 0; cc < 2; ++cc)
-          for (int r = 0; r < MP; ++r)
-            std::memcpy(img2.data() + ((size_t)h * KS + s) * half_step + (size_t)cc * MP * 16 + (size_t)r * 16,
-                        img.data() + (size_t)s * kstep_bytes + (size_t)cc * NC * 16 + (size_t)(h * MP + r) * 16,
-                        16);
+        for (int pt = 0; pt < parts; ++pt)
+          for (int cc = 0; cc < 2; ++cc)
+            for (int r = 0; r < MP; ++r)
+              std::memcpy(img2.data() + (((size_t)h * KS + s) * parts + pt) * half_step + (size_t)cc * MP * 16 +
+                              (size_t)r * 16,
+                          img.data() + ((size_t)s * parts + pt) * kstep_bytes + (size_t)cc * NC * 16 +
+                              (size_t)(h * MP + r) * 16,
+                          16);
     if (melt::dev_alloc(&tb->d_b2, img2.size()) != cudaSuccess) return MELT_ERR_OOM;
     if (cudaMemcpy(tb->d_b2, img2.data(), img2.size(), cudaMemcpyHostToDevice) != cudaSuccess)
       return MELT_ERR_CUDA;
@@ -545,8 +585,9 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
   const bool fused = pair && p.Hd > 0 && L.mlp != nullptr;
   if (pair && p.Hd > 0 && !L.mlp) p.Hd = 0;  // plan made for a correction that is not passed
   KernelFn fn = fused ? kernel_for_pair_mlp(p.MP / 16)
-                : pair ? (tb->precision == MELT_FP8E4M3 ? kernel_for_pair_fp8(L.n_mfcc > 0, p.MP / 16, p.dct_tc)
-                                                        : kernel_for_pair(L.n_mfcc > 0, p.MP / 16, p.dct_tc))
+                : pair ? (tb->precision == MELT_FP8E4M3   ? kernel_for_pair_fp8(L.n_mfcc > 0, p.MP / 16, p.dct_tc)
+                          : tb->precision == MELT_BF16X3 ? kernel_for_pair_x3()
+                                                         : kernel_for_pair(L.n_mfcc > 0, p.MP / 16, p.dct_tc))
                        : (L.n_mfcc ? kernel_for_mfcc(tb->precision, p.MP / 16)
                                    : kernel_for_plain(tb->precision, p.MP / 16, L.stft_bands > 0));
   if (!fn) return cudaErrorInvalidValue;

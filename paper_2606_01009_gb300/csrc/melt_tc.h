@@ -23,7 +23,7 @@ struct TcBasis {
   int n_cols = 0;       // UMMA N = 2M rounded up to a multiple of 16
   size_t kstep_bytes = 0;  // bytes of one K-step block of the B operand
   void* d_b = nullptr;     // B operand blocks, one per K-step (BF16x3: hi and lo parts)
-  void* d_b2 = nullptr;    // BF16 CTA-pair image: W_r rows' blocks, then W_i rows' blocks
+  void* d_b2 = nullptr;    // CTA-pair image: W_r rows' blocks, then W_i rows' blocks (BF16x3: hi, lo per block)
   int n_mfcc = 0;
   int stft_bands = 0;      // fused STFT + Mel comparator: bands per frame (its table sits in shared memory)
   int pair_clusters = -1;  // co-resident 2-CTA clusters of the pair kernel (-1: not queried)

@@ -83,8 +83,9 @@ constexpr int kSfBCols = 16;                // TMEM columns holding the basis sc
 
 struct PairBars {
   int s_full, s_empty, z_full, z_empty, b_full, peer_b, t_full, t_empty, h_full, a2_full, y_full,
-      drain, sched_full, sched_empty, total;
-  __host__ __device__ PairBars(int NS, int ZB, int KS) {
+      drain, sched_full, sched_empty, bs_full, bs_peer, bs_empty, total;
+  // NB: basis slots of a streamed half basis (0 when it is resident)
+  __host__ __device__ PairBars(int NS, int ZB, int KS, int NB = 0) {
     s_full = 0;
     s_empty = s_full + NS;
     z_full = s_empty + NS;
@@ -99,7 +100,10 @@ struct PairBars {
     drain = y_full + 1;
     sched_full = drain + 1;              // dynamic schedule: ring entry published (per CTA)
     sched_empty = sched_full + kSchedRing;  //               ring entry read by both epilogues
-    total = sched_empty + kSchedRing;
+    bs_full = sched_empty + kSchedRing;  // streamed basis: this CTA's slot filled (transaction bytes)
+    bs_peer = bs_full + NB;              //                 the odd CTA's slot filled (even CTA only)
+    bs_empty = bs_peer + NB;             //                 the slot's MMAs completed (both CTAs)
+    total = bs_empty + NB;
   }
 };
 
@@ -285,7 +289,51 @@ static __device__ void pair_wave_producer(const TcParams& p, const PairCtx& c, c
     drain_wait(pbar(p, c, B.s_full + k % p.NS), (k / p.NS) & 1, p.err);
 }
 
+// Streamed half basis (b_resident == 0; static schedule, log-Mel only): for
+// every pair of the cluster, this CTA's half of the basis flows through NB
+// slots of kps K-steps.  Fill g uses slot g % NB; the even CTA's MMAs of a
+// slot release it in both CTAs (multicast commit on bs_empty).
+static __device__ void pair_basis_stream(const TcParams& p, const PairCtx& c, const PairBars& B) {
+  const uint64_t pol = policy_evict_last();
+  const uint32_t total = p.step_bytes * (uint32_t)p.KS;
+  const uint8_t* src = p.bimg + (size_t)c.rank * total;  // this CTA's half
+  int g = 0;
+  bool ok = true;
+  for (int q = c.cluster; ok && q < p.n_pairs; q += c.n_clusters) {
+    for (int s0 = 0; s0 < p.KS; s0 += p.kps, ++g) {
+      const int slot = g % p.NB;
+      if (!mbar_wait(pbar(p, c, B.bs_empty + slot), ((g / p.NB) & 1) ^ 1, c.abort, p.err, kErrTimeout)) {
+        ok = false;
+        break;
+      }
+      const uint32_t bytes = p.step_bytes * (uint32_t)min(p.kps, p.KS - s0);
+      const uint32_t full = pbar(p, c, B.bs_full + slot);
+      mbar_arrive_expect_tx(full, bytes);
+      bulk_g2s_hint(c.sbase + p.off_b + slot * p.bslot_bytes, src + (size_t)s0 * p.step_bytes, bytes, full, pol);
+    }
+  }
+  // every issued copy has landed before the CTA can exit
+  for (int k = max(0, g - p.NB); k < g; ++k) drain_wait(pbar(p, c, B.bs_full + k % p.NB), (k / p.NB) & 1, p.err);
+}
+
+// Streamed half basis, odd CTA (its idle MMA warp): as each of its slots
+// fills, one arrival on the even CTA's bs_peer barrier of that slot, which
+// the even CTA's MMA thread waits on beside its own bs_full.
+static __device__ void pair_basis_signal(const TcParams& p, const PairCtx& c, const PairBars& B) {
+  int g = 0;
+  for (int q = c.cluster; q < p.n_pairs; q += c.n_clusters)
+    for (int s0 = 0; s0 < p.KS; s0 += p.kps, ++g) {
+      const int slot = g % p.NB;
+      if (!mbar_wait(pbar(p, c, B.bs_full + slot), (g / p.NB) & 1, c.abort, p.err, kErrTimeout)) return;
+      mbar_arrive_cluster(mapa_shared(pbar(p, c, B.bs_peer + slot), 0));
+    }
+}
+
 static __device__ void pair_basis_producer(const TcParams& p, const PairCtx& c, const PairBars& B) {
+  if (!p.b_resident) {
+    pair_basis_stream(p, c, B);
+    return;
+  }
   const uint64_t pol = policy_evict_last();
   const uint32_t total = p.step_bytes * (uint32_t)p.KS;
   const uint8_t* src = p.bimg + (size_t)c.rank * total;  // this CTA's half
@@ -394,6 +442,13 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
   const uint32_t abuf16 = p.abuf_bytes >> 4;
   const int nacc = MLP ? 1 : p.nacc;  // the fused MLP's TMEM leaves room for one accumulator
   const uint32_t sfb = tmem_base + p.sf_col + (uint32_t)(4 * p.sfg * p.ZB);  // FP8: basis scale 2^-8
+  // split BF16: the lo part of an A buffer follows its hi part; the lo part
+  // of a K-step block of this CTA's basis half follows its hi part
+  const uint32_t apart16 = p.a_bytes >> 4, bpart16 = (p.step_bytes / 2) >> 4;
+  // streamed half basis: slot descriptors (low word) and the fill count
+  const uint32_t bslot0 = ((c.sbase + p.off_b) >> 4) | ((p.b_lbo >> 4) << 16);
+  const uint32_t bslot16 = p.bslot_bytes >> 4, step16 = p.step_bytes >> 4;
+  int g = 0;
   int k = 0;
   bool ok = true;
   for (;; ++k) {
@@ -411,7 +466,7 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
     }
     ok = ok && mbar_wait_cluster(pbar(p, c, B.z_full + zb), (p.ZB == 2 ? (k >> 1) : k) & 1, c.abort,
                                  p.err, kErrTimeout);
-    if (ok && k == 0)
+    if (ok && k == 0 && p.b_resident)
       ok = mbar_wait(pbar(p, c, B.b_full), 0, c.abort, p.err, kErrTimeout) &&
            mbar_wait_cluster(pbar(p, c, B.peer_b), 0, c.abort, p.err, kErrTimeout);
     if (!ok) break;
@@ -419,6 +474,37 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
     const uint32_t d = tmem_base + acc * p.acc_stride;
     const uint32_t alo = a_lo0 + zb * abuf16;
     const uint32_t tab_s = smem_u32(tab);
+    if constexpr (PREC != MELT_FP8E4M3 && !MLP && !DTC) {  // (the host plans a streamed basis for these only)
+      if (!p.b_resident) {
+        // streamed half basis: slot by slot, each once both CTAs' halves are in
+        for (int s0 = 0; s0 < p.KS; s0 += p.kps, ++g) {
+          const int slot = g % p.NB;
+          const uint32_t ph = (g / p.NB) & 1;
+          if (!mbar_wait(pbar(p, c, B.bs_full + slot), ph, c.abort, p.err, kErrTimeout) ||
+              !mbar_wait(pbar(p, c, B.bs_peer + slot), ph, c.abort, p.err, kErrTimeout)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int n = min(p.kps, p.KS - s0);
+          for (int u = 0; u < n; ++u) {
+            uint32_t tx, ty;
+            asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(tx), "=r"(ty) : "r"(tab_s + 8u * (s0 + u)));
+            const uint32_t bl = bslot0 + slot * bslot16 + u * step16;
+            mma_f16_pair(d, hi | (alo + tx), hi | bl, p.idesc, s0 + u > 0);
+            if constexpr (PREC == MELT_BF16X3) {
+              mma_f16_pair(d, hi | (alo + tx), hi | (bl + bpart16), p.idesc, true);
+              mma_f16_pair(d, hi | (alo + tx + apart16), hi | bl, p.idesc, true);
+            }
+          }
+          mma_commit_pair_mc(pbar(p, c, B.bs_empty + slot), 3);
+        }
+        if (!ok) break;
+        mma_commit_pair_mc(pbar(p, c, B.z_empty + zb), 3);
+        mma_commit_pair_mc(pbar(p, c, B.t_full + acc), 3);
+        continue;
+      }
+    }
 #pragma unroll 1
     for (int s0 = 0; s0 < p.KS; s0 += 8) {
       uint32_t tx[8], ty[8];
@@ -439,6 +525,11 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
                            s0 + u > 0);
           } else {
             mma_f16_pair(d, hi | (alo + tx[u]), hi | ty[u], p.idesc, s0 + u > 0);
+            if constexpr (PREC == MELT_BF16X3) {
+              // hi*lo and lo*hi, in the order of the single-CTA kernel (bit-identical sums)
+              mma_f16_pair(d, hi | (alo + tx[u]), hi | (ty[u] + bpart16), p.idesc, true);
+              mma_f16_pair(d, hi | (alo + tx[u] + apart16), hi | ty[u], p.idesc, true);
+            }
           }
         }
     }
@@ -489,6 +580,7 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
 // (lanes read consecutive quads: conflict-free); quad hq is the low or high
 // half (hq & 1) of the Z row segment (row ul, 8-sample group kc) with
 // 8 * (hq >> 1) = (ul - ch*CH) H + 8 kc.
+template <bool SPLIT>
 static __device__ void pair_convert(const TcParams& p, const PairCtx& c, const PairBars& B, int cvt0) {
   const int ct = threadIdx.x - 32 * cvt0;
   const int H8 = p.H >> 3;
@@ -544,6 +636,12 @@ static __device__ void pair_convert(const TcParams& p, const PairCtx& c, const P
         if (qrow[q] < rows) {
           const uint32_t h0 = pack_bf16(x[q].x, x[q].y), h1 = pack_bf16(x[q].z, x[q].w);
           asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(zrow0 + qoff[q]), "r"(h0), "r"(h1));
+          if constexpr (SPLIT) {
+            // split BF16: lo = rn(x - hi), the second part p.a_bytes further
+            const uint32_t l0 = pack_bf16(x[q].x - __uint_as_float(h0 << 16), x[q].y - __uint_as_float(h0 & 0xffff0000u));
+            const uint32_t l1 = pack_bf16(x[q].z - __uint_as_float(h1 << 16), x[q].w - __uint_as_float(h1 & 0xffff0000u));
+            asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(zrow0 + qoff[q] + p.a_bytes), "r"(l0), "r"(l1));
+          }
         }
       }
       warp_arrive(pbar(p, c, B.s_empty + slot));
@@ -1142,7 +1240,7 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH, DTC), 1)
   const uint32_t sbase = (raw + 127u) & ~127u;
   uint8_t* gbase = smem_raw + (sbase - raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const PairBars B(p.NS, p.ZB, p.KS);
+  const PairBars B(p.NS, p.ZB, p.KS, p.b_resident ? 0 : p.NB);
   PairCtx c;
   c.sbase = sbase;
   c.rank = cluster_ctarank();
@@ -1174,6 +1272,11 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH, DTC), 1)
     for (int i = 0; i < kSchedRing; ++i) {
       mbar_init(bar(B.sched_full + i), 1);           // the even CTA's producer (here or remote)
       mbar_init(bar(B.sched_empty + i), 2 * EPW);    // epilogues of both CTAs (even CTA's copy is used)
+    }
+    for (int i = 0; i < (p.b_resident ? 0 : p.NB); ++i) {
+      mbar_init(bar(B.bs_full + i), 1);   // this CTA's producer (expect_tx)
+      mbar_init(bar(B.bs_peer + i), 1);   // the odd CTA's signal (even CTA's copy is used)
+      mbar_init(bar(B.bs_empty + i), 1);  // the even CTA's multicast commit
     }
     *c.abort = 0;
     fence_mbar_init();
@@ -1241,6 +1344,7 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH, DTC), 1)
   if (warp == kPMmaWarp) {
     if (lane == 0) {
       if (c.rank == 0) pair_mma<MLP, PREC, DTC>(p, gbase, c, B, tmem_base);
+      else if (!p.b_resident) pair_basis_signal(p, c, B);  // the odd CTA's slots, to the even CTA
       drain_wait(pbar(p, c, B.drain), 0, p.err);
     }
     __syncwarp();
@@ -1256,7 +1360,7 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH, DTC), 1)
     if constexpr (PREC == MELT_FP8E4M3)
       pair_convert_fp8<CW>(p, gbase, c, B, kPCvtWarp0, tmem_base);
     else
-      pair_convert(p, c, B, kPCvtWarp0);
+      pair_convert<PREC == MELT_BF16X3>(p, c, B, kPCvtWarp0);
     __syncwarp();
   } else {
     pdl_wait();
@@ -1326,6 +1430,12 @@ KernelFn pick_pair_fp8_kernel(bool mfcc, int nch, bool dtc = false) {
     case 8: return melt_tc_pair_kernel<8, true, false, MELT_FP8E4M3>;
     default: return nullptr;
   }
+}
+
+// Split-BF16 (BF16x3) instantiation: log-Mel only.
+template <int = 0>
+KernelFn pick_pair_x3_kernel() {
+  return melt_tc_pair_kernel<1, false, false, MELT_BF16X3>;
 }
 
 // Fused-MLP instantiations: log-Mel rows of 16 * nch bands (the fused TMEM

@@ -876,6 +876,8 @@ KernelFn kernel_for_pair(bool mfcc, int nch, bool dtc);
 KernelFn kernel_for_pair_mlp(int nch);
 // Defined in melt_tc2_fp8.cu: the CTA-pair kernel with FP8 e4m3 operands.
 KernelFn kernel_for_pair_fp8(bool mfcc, int nch, bool dtc);
+// Defined in melt_tc2_x3.cu: the CTA-pair kernel with split-BF16 operands.
+KernelFn kernel_for_pair_x3();
 
 }  // namespace tc
 }  // namespace melt

@@ -36,6 +36,10 @@ def _plans():
         # or dynamic pair schedule
         out.append(dict(basis_resident=1, a_buffers=zb, prefetch_tiles=pf, basis_slots=0, ksteps_per_slot=1,
                         cta_pair=1, schedule=sched))
+    for zb, pf, nb, kps in ((2, 0, 4, 4), (2, 1, 2, 1), (1, 0, 3, 8), (2, 2, 4, 2), (1, 1, 2, 16)):
+        # CTA pairs with each CTA's half basis streamed through slots (BF16, split BF16)
+        out.append(dict(basis_resident=0, a_buffers=zb, prefetch_tiles=pf, basis_slots=nb, ksteps_per_slot=kps,
+                        cta_pair=1, schedule=0))
     return out
 
 
@@ -85,7 +89,8 @@ def test_plan_round_trip_and_rejections(melt):
     for bad in [dict(pl, a_buffers=3), dict(pl, prefetch_tiles=-1), dict(pl, prefetch_tiles=5),
                 dict(pl, basis_slots=1), dict(pl, ksteps_per_slot=0),
                 dict(pl, basis_slots=32, ksteps_per_slot=40), dict(pl, cta_pair=2),
-                dict(pl, cta_pair=1),           # a pair plan needs the resident basis
+                dict(pl, cta_pair=1, schedule=1),   # a streamed half basis needs the static schedule
+                dict(pl, cta_pair=1, basis_slots=9),  # at most 8 slots
                 dict(pl, schedule=1),           # the dynamic schedule is for CTA pairs only
                 dict(pair, schedule=2), dict(pair, schedule=-1)]:
         with pytest.raises(melt.MeltError) as ei:
