@@ -940,7 +940,8 @@ def sweeps(args, dev):
         row = {"batch": b, "frames": fes["bf16"].total_frames(pk.lengths)}
         for p, fe in fes.items():
             out = torch.empty((row["frames"], 80), device=dev)
-            ms = time_launches(lambda i: fe(wave, pk.offsets, pk.lengths, out=out), dev, 10 if p == "bf16" else 3)
+            ms = time_launches(lambda i: fe(wave, pk.offsets, pk.lengths, out=out, input_ready=True), dev,
+                               10 if p == "bf16" else 3)
             row[f"melt_{p}_us"] = ms * 1e3
         x = torch.from_numpy(np.stack([c for c in clips[:b]]))
         row["torch_stft_us"] = time_stft_batch(x, base, dev, steps=10)["ms_per_step"] * 1e3
@@ -958,8 +959,8 @@ def sweeps(args, dev):
             fe = melt.Frontend(precision=p, n_mels=M)
             T = fe.total_frames(pk.lengths)
             out = torch.empty((T, M), device=dev)
-            row[f"melt_{p}_us"] = time_launches(lambda i: fe(wave, pk.offsets, pk.lengths, out=out), dev,
-                                                10 if p == "bf16" else 3) * 1e3
+            row[f"melt_{p}_us"] = time_launches(lambda i: fe(wave, pk.offsets, pk.lengths, out=out, input_ready=True),
+                                                dev, 10 if p == "bf16" else 3) * 1e3
             fe.close()
         row["frames"] = T
         row["torch_stft_us"] = time_stft_batch(torch.from_numpy(clip[None, :].copy()), cfg, dev, steps=10)["ms_per_step"] * 1e3
