@@ -213,6 +213,15 @@ int64_t frames_of(const melt_basis* b, int64_t len) {
   return (len - b->n_fft) / b->hop + 1;
 }
 
+// The FP32 kernel's CTAs take tiles in list order, round by round, and a
+// tile costs it in proportion to its frames (warps past the tile's end
+// idle); with the longest tiles first, the last, partly filled round holds
+// the short tiles that end clips.  Tiles are independent (each writes its
+// own rows), so the order changes no result.
+void order_longest_first(TileDesc* t, long long n) {
+  std::stable_sort(t, t + n, [](const TileDesc& a, const TileDesc& b) { return a.n_frames > b.n_frames; });
+}
+
 // Build the tile list of a batch; returns MELT_ERR_ARG on bad offsets/lengths.
 melt_status plan_tiles(melt_basis* b, const int64_t* offsets, const int64_t* lengths, int batch) {
   b->plan.clear();
@@ -237,6 +246,7 @@ melt_status plan_tiles(melt_basis* b, const int64_t* offsets, const int64_t* len
     row += T;
   }
   b->plan_rows = row;
+  if (b->precision == MELT_FP32) order_longest_first(b->plan.data(), (long long)b->plan.size());
   return MELT_OK;
 }
 
@@ -381,6 +391,7 @@ long long plan_tiles_into(const melt_basis* b, const int64_t* offsets, const int
     n += k;
     row += frames_of(b, L);
   }
+  if (b->precision == MELT_FP32) order_longest_first(dst, n);
   return n;
 }
 

@@ -22,6 +22,7 @@
 // the call refuses to run while its stream is being captured.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "melt_internal.h"
@@ -66,8 +67,8 @@ extern "C" melt_status melt_forward_noalloc(melt_basis* basis, const float* wave
   const long long n = plan_tiles_into(basis, offsets, lengths, batch, g_host_tiles, kMaxTiles);
   if (n < 0) return MELT_ERR_ARG;  // -1: bad offset/length; -2: more than kMaxTiles tiles
   if (n == 0) return MELT_OK;
-  const TileDesc& last = g_host_tiles[n - 1];  // planned in output-row order
-  const int64_t rows = last.out_row + last.n_frames;
+  int64_t rows = 0;  // the tiles need not be in output-row order
+  for (long long i = 0; i < n; ++i) rows = std::max<int64_t>(rows, g_host_tiles[i].out_row + g_host_tiles[i].n_frames);
   // Every field of the n descriptors is written here; nothing in the array
   // has to start at zero.
   if (cudaMemcpyAsync(g_dev_tiles[dev], g_host_tiles, (size_t)n * sizeof(TileDesc),

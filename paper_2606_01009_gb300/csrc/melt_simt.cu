@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(kThreads, MJ <= 5 ? 2 : 1) melt_simt_kernel(Si
 
   for (int tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) {
     const TileDesc td = p.tiles[tile];
+    const bool busy = (tid >> 5) * 16 < td.n_frames;  // warp w owns frames 16 w .. 16 w + 15
     float acc[8][MJ][2];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -122,9 +123,12 @@ __global__ void __launch_bounds__(kThreads, MJ <= 5 ? 2 : 1) melt_simt_kernel(Si
       const float* Ws = Xs + kXs;
       // every chunk runs all kKC samples: past N both operands were
       // zero-filled, so those products add exact zeros (a compile-time
-      // trip count lets every shared-memory offset be an immediate)
+      // trip count lets every shared-memory offset be an immediate).  A warp
+      // whose 16 frames all lie past the tile's end skips the FFMAs (it
+      // still copies and meets the barriers), leaving its issue slots to
+      // the SM's other warps.
 #pragma unroll 8
-      for (int k = 0; k < kKC; ++k) {
+      for (int k = 0; k < (busy ? kKC : 0); ++k) {
         const float4 xa = *reinterpret_cast<const float4*>(Xs + k * (kF + kXPad) + ty * 8);
         const float4 xb = *reinterpret_cast<const float4*>(Xs + k * (kF + kXPad) + ty * 8 + 4);
         const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
