@@ -567,7 +567,8 @@ def _jsonable(o):
 
 def time_grouped(args, dev, steps=20, warmup=3, per_clip_steps=2):
     """Mixed-geometry batch of 4096 clips (16 kHz 400/160/80 and 22.05 kHz 1024/256/80, BF16):
-    melt_forward_grouped with a CUDA graph, without, and one melt_forward per clip."""
+    melt_forward_grouped as one shared persistent launch and as one launch per
+    basis, with a CUDA graph and without, and one melt_forward per clip."""
     import torch
     from paper_2606_01009_gb300 import inputs as G
     from paper_2606_01009_gb300 import melt
@@ -599,19 +600,29 @@ def time_grouped(args, dev, steps=20, warmup=3, per_clip_steps=2):
         torch.cuda.synchronize(dev)
         return a.elapsed_time(b) / k
 
-    # default plans, then the plans melt_group_autotune picks by timing this
-    # grouped launch (kept in the on-disk plan cache for later processes)
+    # default plans: one launch per basis, and both bases in one shared
+    # persistent launch (MELT_GROUP_SHARED); then the plans
+    # melt_group_autotune picks by timing the per-basis grouped call (kept in
+    # the on-disk plan cache for later processes)
     gf = melt.GroupedFrontend(fes, graphs=True)
     ms = timed(lambda: gf(wave, pk.offsets, pk.lengths, ids, out=out, stream=stream), steps, warmup)
     res["grouped_graph_default_plans"] = {"ms_per_step": ms, "frames_per_s": T / (ms / 1e3),
                                           "plans": [melt.melt_plan_get(fe.handle) for fe in fes]}
+    gf.close()
+    gf = melt.GroupedFrontend(fes, graphs=True, shared_launch=True)
+    ms = timed(lambda: gf(wave, pk.offsets, pk.lengths, ids, out=out, stream=stream), steps, warmup)
+    res["grouped_graph_shared_launch_default_plans"] = {"ms_per_step": ms, "frames_per_s": T / (ms / 1e3),
+                                                        "launches_per_step": 1}
+    gf.close()
+    gf = melt.GroupedFrontend(fes, graphs=True)
     t0 = time.perf_counter()
     plans, hit = gf.autotune(wave, pk.offsets, pk.lengths, ids, out, path=args.plan_cache, stream=stream)
     res["autotune"] = {"plans": plans, "cache_hit": hit, "seconds": round(time.perf_counter() - t0, 3),
                        "plan_cache": args.plan_cache}
     gf.close()
-    for name, graphs in (("grouped_graph", True), ("grouped_direct", False)):
-        gf = melt.GroupedFrontend(fes, graphs=graphs)
+    # with the tuned plans: one launch per basis (graph, and direct)
+    for name, graphs, shared in (("grouped_graph", True, False), ("grouped_direct", False, False)):
+        gf = melt.GroupedFrontend(fes, graphs=graphs, shared_launch=shared)
         ms = timed(lambda: gf(wave, pk.offsets, pk.lengths, ids, out=out, stream=stream), steps, warmup)
         gf.sync(stream)
         res[name] = {"ms_per_step": ms, "frames_per_s": T / (ms / 1e3)}

@@ -377,20 +377,30 @@ melt_status melt_forward_components(melt_basis* basis, const float* wave,
  * and layout plans may differ (e.g. 16 kHz 400/160/80 and 22.05 kHz
  * 1024/256/80).  One call plans a work list of tiles (basis, clip, 128-frame
  * run), copies it to the device once per batch layout, and runs one
- * persistent kernel per basis over its part of the list.  Unless disabled,
- * the launches of a batch layout are captured once into a CUDA graph and
- * replayed by later calls with the same layout.
+ * persistent kernel per basis over its part of the list.  With
+ * MELT_GROUP_SHARED, two BF16 log-Mel bases (without a correction, with
+ * CTA-pair plans or default plans) share one persistent launch instead: the
+ * clusters are split between the bases (melt_group_set_split; by default in
+ * proportion to tiles x n_fft) and each cluster runs its basis's layout (a
+ * basis whose default plan is single-CTA takes its first CTA-pair plan
+ * there; a forced single-CTA plan keeps the per-basis launches).  On the
+ * 4096-clip 16 kHz + 22.05 kHz batch the shared launch measured slower
+ * (1.05 ms at its best split against 0.81 ms), hence not the default.
+ * Unless disabled, the launches of a batch layout are captured once into a
+ * CUDA graph and replayed by later calls with the same layout.
  */
 #define MELT_MAX_GROUPS 16
 #define MELT_GROUP_NO_GRAPH 1   /* melt_group_create flag: launch directly, no graph */
+#define MELT_GROUP_SHARED 2     /* melt_group_create flag: two bases in one shared persistent launch */
 
 typedef struct melt_group melt_group;
 
 /*
  * melt_group_create - bundle `n_bases` bases (host array of handles, 1..16,
  * all created on the current device, equal melt_num_outputs).  The group
- * does not own the bases: destroy the group first.  `flags`: 0 or
- * MELT_GROUP_NO_GRAPH.  Returns MELT_ERR_ARG on a bad argument.
+ * does not own the bases: destroy the group first.  `flags`: 0 or an OR of
+ * MELT_GROUP_NO_GRAPH and MELT_GROUP_SHARED.  Returns MELT_ERR_ARG on a bad
+ * argument.
  */
 melt_status melt_group_create(melt_basis* const* bases, int n_bases, int flags, melt_group** out);
 
@@ -436,6 +446,14 @@ melt_status melt_forward_grouped(melt_group* group, const float* wave, const int
 melt_status melt_group_autotune(melt_group* group, const float* wave, const int64_t* offsets,
                                 const int64_t* lengths, const int32_t* basis_of, int batch, float* out,
                                 void* stream, int reps, const char* path, int* hit);
+
+/*
+ * melt_group_set_split - the first basis's share of the clusters in the
+ * shared launch of a two-basis group (0 <= frac0 < 1; 0 = in proportion to
+ * tiles x n_fft, the default).  Drops the group's recorded graphs.
+ * MELT_ERR_ARG outside that range.
+ */
+melt_status melt_group_set_split(melt_group* group, double frac0);
 
 /* melt_group_sync - melt_sync of every basis of the group; first error wins. */
 melt_status melt_group_sync(melt_group* group, void* stream);

@@ -423,6 +423,30 @@ melt_status launch_forward_tiles(melt_basis* b, const float* wave, const TileDes
   return MELT_OK;
 }
 
+melt_status launch_forward_tiles_pair2(melt_basis* b0, const TileDesc* t0, int n0, melt_basis* b1,
+                                       const TileDesc* t1, int n1, const float* wave, float* out, double frac0,
+                                       cudaStream_t stream, bool* launched) {
+  *launched = false;
+  if (b0->precision == MELT_FP32 || b1->precision == MELT_FP32 || b0->correction || b1->correction)
+    return MELT_OK;
+  TcLaunch L[2];
+  melt_basis* bs[2] = {b0, b1};
+  const TileDesc* ts[2] = {t0, t1};
+  const int ns[2] = {n0, n1};
+  for (int k = 0; k < 2; ++k) {
+    L[k].wave = wave; L[k].tiles = ts[k]; L[k].n_tiles = ns[k]; L[k].out = out;
+    L[k].dct = bs[k]->d_dct; L[k].n_mfcc = bs[k]->n_mfcc; L[k].eps = (float)bs[k]->eps; L[k].err = bs[k]->d_err;
+    L[k].sm_count = bs[k]->sm_count;
+    L[k].fb = bs[k]->d_fb;
+    L[k].stft_bands = bs[k]->stft_bands;
+  }
+  // clusters in proportion to each basis's tiles x n_fft (the MMA work of a tile)
+  const double w0 = (double)n0 * b0->n_fft, w1 = (double)n1 * b1->n_fft;
+  const cudaError_t e =
+      tc_launch_pair_group(&b0->tc, L[0], &b1->tc, L[1], frac0 > 0.0 ? frac0 : w0 / (w0 + w1), stream, launched);
+  return e == cudaSuccess ? MELT_OK : cuda_status(e);
+}
+
 int basis_device(const melt_basis* b) { return b->device; }
 
 const melt_mlp* basis_correction(const melt_basis* b) { return b->correction; }

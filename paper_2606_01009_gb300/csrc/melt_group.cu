@@ -61,6 +61,7 @@ struct melt_group {
   cudaStream_t capture = nullptr;  // private stream the graphs are captured on
   std::vector<TileDesc> host;      // planning scratch
   std::vector<int64_t> rows;       // planning scratch: first output row of each clip
+  double split = 0.0;              // shared launch: the first basis's share of the clusters (0: by work)
 };
 
 namespace {
@@ -75,6 +76,15 @@ bool same_layout(const GroupEntry* e, const float* wave, const int64_t* offsets,
 }
 
 melt_status launch_all(melt_group* g, const GroupEntry* e, cudaStream_t stream) {
+  if ((g->flags & MELT_GROUP_SHARED) && g->bases.size() == 2 && e->count[0] > 0 && e->count[1] > 0 &&
+      e->count[0] <= 0x7fffffffLL && e->count[1] <= 0x7fffffffLL) {
+    // both bases in one persistent launch where their kernels allow it
+    bool launched = false;
+    const melt_status st = launch_forward_tiles_pair2(g->bases[0], e->d_tiles + e->first[0], (int)e->count[0],
+                                                      g->bases[1], e->d_tiles + e->first[1], (int)e->count[1],
+                                                      e->wave, e->out, g->split, stream, &launched);
+    if (st != MELT_OK || launched) return st;
+  }
   for (size_t k = 0; k < g->bases.size(); ++k) {
     if (e->count[k] == 0) continue;
     const melt_status st = launch_forward_tiles(g->bases[k], e->wave, e->d_tiles + e->first[k],
@@ -186,7 +196,7 @@ extern "C" {
 
 melt_status melt_group_create(melt_basis* const* bases, int n_bases, int flags, melt_group** out) {
   if (!out || !bases || n_bases < 1 || n_bases > MELT_MAX_GROUPS) return MELT_ERR_ARG;
-  if (flags & ~MELT_GROUP_NO_GRAPH) return MELT_ERR_ARG;
+  if (flags & ~(MELT_GROUP_NO_GRAPH | MELT_GROUP_SHARED)) return MELT_ERR_ARG;
   *out = nullptr;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MELT_ERR_CUDA;
@@ -361,6 +371,15 @@ melt_status melt_group_autotune(melt_group* g, const float* wave, const int64_t*
   g->cache.clear();
   if (st == MELT_OK && hit) *hit = applied ? 1 : 0;
   return st;
+}
+
+melt_status melt_group_set_split(melt_group* g, double frac0) {
+  if (!g || !(frac0 >= 0.0 && frac0 < 1.0)) return MELT_ERR_ARG;
+  g->split = frac0;
+  // recorded graphs hold the old split: drop them
+  for (GroupEntry* e : g->cache) free_entry(e);
+  g->cache.clear();
+  return MELT_OK;
 }
 
 melt_status melt_group_sync(melt_group* g, void* stream) {

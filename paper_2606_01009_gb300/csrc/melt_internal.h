@@ -77,6 +77,14 @@ long long plan_tiles_into(const melt_basis* b, const int64_t* offsets, const int
 melt_status launch_forward_tiles(melt_basis* b, const float* wave, const TileDesc* d_tiles,
                                  int n_tiles, float* out, int64_t rows, cudaStream_t stream);
 
+// Both bases' tiles in one persistent CTA-pair launch (the grouped call);
+// *launched is false, with nothing enqueued, where the bases' kernels do not
+// allow it (then the caller launches them one by one).
+// frac0 is the first basis's share of the clusters (0: by tiles x n_fft).
+melt_status launch_forward_tiles_pair2(melt_basis* b0, const TileDesc* t0, int n0, melt_basis* b1,
+                                       const TileDesc* t1, int n1, const float* wave, float* out, double frac0,
+                                       cudaStream_t stream, bool* launched);
+
 // Frames of a clip of `len` samples under basis b: floor((len - N)/H) + 1, 0 if len < N.
 int64_t basis_frames(const melt_basis* b, int64_t len);
 

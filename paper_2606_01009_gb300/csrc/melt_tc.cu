@@ -657,3 +657,98 @@ cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream)
 }
 
 }  // namespace melt
+
+namespace melt {
+
+namespace {
+
+// Parameters of one basis's half of a two-basis pair launch; false if the
+// basis cannot run as a BF16 log-Mel CTA pair there.
+bool group_pair_params(const TcBasis* tb, const TcLaunch& L, TcParams& p) {
+  if (tb->precision != MELT_BF16 || tb->n_mfcc != 0 || tb->stft_bands > 0 || L.n_mfcc != 0 || L.mlp || !tb->d_b2)
+    return false;
+  TcBasis probe = *tb;
+  melt_plan cands[kMaxCands];
+  const int n = tc_candidates(tb, cands, kMaxCands);
+  if (n < 1) return false;
+  if (!tb->forced && cands[0].cta_pair != 1) {
+    // default plan single-CTA: the first CTA-pair layout among the candidates
+    int i = 0;
+    while (i < n && cands[i].cta_pair != 1) ++i;
+    if (i == n) return false;
+    probe.forced = true;
+    probe.plan = cands[i];
+  }
+  std::memset(&p, 0, sizeof(p));
+  if (!plan_smem(&probe, p, 0) || p.NS == 0 || p.dyn || p.Hd > 0) return false;
+  p.wave = L.wave;
+  p.tiles = L.tiles;
+  p.n_tiles = L.n_tiles;
+  p.n_pairs = (L.n_tiles + 1) / 2;
+  p.bimg = static_cast<const uint8_t*>(tb->d_b2);
+  p.dct = L.dct;
+  p.out = L.out;
+  p.err = L.err;
+  p.eps = L.eps;
+  p.n_mfcc = 0;
+  p.n_out = tb->n_mels;
+  p.early_inputs = L.early_inputs && L.pdl ? 1 : 0;
+  return true;
+}
+
+}  // namespace
+
+cudaError_t tc_launch_pair_group(const TcBasis* tb0, const TcLaunch& L0, const TcBasis* tb1, const TcLaunch& L1,
+                                 double frac0, cudaStream_t stream, bool* launched) {
+  *launched = false;
+  if (L0.n_tiles < 1 || L1.n_tiles < 1) return cudaSuccess;
+  TcGroupParams q;
+  std::memset(&q, 0, sizeof(q));
+  if (!group_pair_params(tb0, L0, q.g[0]) || !group_pair_params(tb1, L1, q.g[1])) return cudaSuccess;
+  GroupKernelFn fn = kernel_for_pair_group();
+  const int smem = (int)std::max(q.g[0].smem_total, q.g[1].smem_total);
+  static thread_local int set_smem = 0;  // the attribute already set for this size or larger
+  if (set_smem < smem) {
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    set_smem = smem;
+  }
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = L0.pdl ? 1 : 0;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = 2;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  cfg.blockDim = dim3(pair_threads(false, MELT_BF16, false, 1, false), 1, 1);
+  static thread_local int occ_smem = -1, occ_clusters = 0;
+  if (occ_smem != smem) {
+    cfg.gridDim = dim3(2 * (L0.sm_count / 2), 1, 1);
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, fn, &cfg);
+    if (e != cudaSuccess) return e;
+    occ_smem = smem;
+    occ_clusters = n;
+  }
+  const int C = std::min(occ_clusters, q.g[0].n_pairs + q.g[1].n_pairs);
+  if (C < 2) return cudaSuccess;
+  // clusters for the first basis: its share of the work, at least one each,
+  // none beyond a basis's own pair count
+  int s = (int)std::lround(frac0 * C);
+  s = std::max(s, C - q.g[1].n_pairs);
+  s = std::min(s, q.g[0].n_pairs);
+  s = std::max(1, std::min(C - 1, s));
+  q.split = s;
+  cfg.gridDim = dim3(2 * C, 1, 1);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, fn, q);
+  if (e == cudaSuccess) *launched = true;
+  return e;
+}
+
+}  // namespace melt

@@ -65,6 +65,14 @@ struct TcLaunch {
 };
 
 melt_status tc_build(TcBasis* tb, const TcConfig& c, const double* w64);
+// Two BF16 log-Mel bases in one persistent CTA-pair launch (the grouped
+// call): a fraction frac0 of the clusters works through L0's tiles, the rest
+// through L1's.  Each basis runs its own plan when that is a CTA-pair plan;
+// a basis without a forced plan whose default is single-CTA runs the first
+// streamed-half-basis pair layout that fits.  *launched is false (and
+// nothing is enqueued) when a basis cannot run that way.
+cudaError_t tc_launch_pair_group(const TcBasis* tb0, const TcLaunch& L0, const TcBasis* tb1, const TcLaunch& L1,
+                                 double frac0, cudaStream_t stream, bool* launched);
 int tc_max_mfcc();  // largest n_mfcc the tensor-core epilogue supports
 void tc_free(TcBasis* tb);
 cudaError_t tc_launch(const TcBasis* tb, const TcLaunch& L, cudaStream_t stream);

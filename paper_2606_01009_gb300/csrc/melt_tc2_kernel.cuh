@@ -1229,9 +1229,10 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
   }
 }
 
-template <int NCH, bool MFCC, bool MLP, int PREC = MELT_BF16, bool DTC = false>
-__global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH, DTC), 1)
-    melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
+// The work of one CTA of a pair kernel: cluster `cluster` of `n_clusters`
+// clusters that share the tile list of `p`.
+template <int NCH, bool MFCC, bool MLP, int PREC, bool DTC>
+__device__ __forceinline__ void pair_cta(const TcParams& p, int cluster, int n_clusters) {
   constexpr int EPW = pair_epi_warps(MLP, MFCC, NCH, DTC);
   constexpr int kPMmaWarp = EPW, kPBWarp = EPW + 1, kPProdWarp = EPW + 2, kPCvtWarp0 = EPW + 3;
   constexpr int CW = pair_cvt_warps(PREC, MFCC, NCH, DTC);
@@ -1244,8 +1245,8 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH, DTC), 1)
   PairCtx c;
   c.sbase = sbase;
   c.rank = cluster_ctarank();
-  c.cluster = blockIdx.x >> 1;
-  c.n_clusters = gridDim.x >> 1;
+  c.cluster = cluster;
+  c.n_clusters = n_clusters;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + p.off_misc);
   c.abort = reinterpret_cast<volatile int*>(gbase + p.off_misc + 4);
 
@@ -1378,7 +1379,7 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH, DTC), 1)
     // every claim of this CTA is settled: the last CTA of the launch to get
     // here leaves the launch's counter at zero for the next launch that uses it
     __threadfence();
-    if (atomicAdd(p.sched + 1, 1ull) == (unsigned long long)gridDim.x - 1) {
+    if (atomicAdd(p.sched + 1, 1ull) == (unsigned long long)(2 * n_clusters) - 1) {
       atomicExch(p.sched, 0ull);
       atomicExch(p.sched + 1, 0ull);
     }
@@ -1389,6 +1390,35 @@ __global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH, DTC), 1)
     tmem_dealloc_pair(tmem_base, p.tmem_cols);
   }
 }
+
+template <int NCH, bool MFCC, bool MLP, int PREC = MELT_BF16, bool DTC = false>
+__global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH, DTC), 1)
+    melt_tc_pair_kernel(const __grid_constant__ TcParams p) {
+  pair_cta<NCH, MFCC, MLP, PREC, DTC>(p, (int)(blockIdx.x >> 1), (int)(gridDim.x >> 1));
+}
+
+// Two bases in one persistent launch (the grouped call): clusters
+// [0, split) work through the tiles of g[0], the others through those of
+// g[1], each with its own geometry, shared-memory layout and TMEM size (the
+// launch provides the larger shared-memory size).  Every tile is computed
+// exactly as in its basis's own launch.
+struct TcGroupParams {
+  TcParams g[2];
+  int split;
+};
+
+template <int NCH, bool MFCC, bool MLP, int PREC = MELT_BF16, bool DTC = false>
+__global__ void __launch_bounds__(pair_threads(MLP, PREC, MFCC, NCH, DTC), 1)
+    melt_tc_pair_group_kernel(const __grid_constant__ TcGroupParams q) {
+  const int cl = (int)(blockIdx.x >> 1), nc = (int)(gridDim.x >> 1);
+  const bool second = cl >= q.split;
+  pair_cta<NCH, MFCC, MLP, PREC, DTC>(second ? q.g[1] : q.g[0], second ? cl - q.split : cl,
+                                      second ? nc - q.split : q.split);
+}
+
+using GroupKernelFn = void (*)(TcGroupParams);
+// Defined in melt_tc2.cu: the two-basis launch of the BF16 log-Mel pair kernel.
+GroupKernelFn kernel_for_pair_group();
 
 template <bool MFCC>
 KernelFn pick_pair_kernel(int nch, bool dtc = false) {

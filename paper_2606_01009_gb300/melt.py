@@ -27,6 +27,7 @@ MELT_WIN_HANN_SYMMETRIC = 1
 
 MELT_MAX_GROUPS = 16
 MELT_GROUP_NO_GRAPH = 1
+MELT_GROUP_SHARED = 2
 
 MELT_FWD_INPUT_READY = 1
 
@@ -54,6 +55,7 @@ SIGNATURES = {
     "melt_basis_get_fp64": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "melt_forward": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
     "melt_forward_ex": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP, C.c_uint]),
+    "melt_group_set_split": (C.c_int, [_VP, C.c_double]),
     "melt_stft_create": (C.c_int, [C.c_double, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                    C.c_int, C.c_int, C.c_double, C.POINTER(_VP)]),
     "melt_forward_components": (C.c_int, [_VP, _VP, _I64P, _I64P, C.c_int, _VP, _VP]),
@@ -358,6 +360,11 @@ def melt_group_create(bases, flags=0):
     return g
 
 
+def melt_group_set_split(group, frac0):
+    """First basis's share of the clusters in a two-basis shared launch (0: by work)."""
+    _check(lib.melt_group_set_split(group, float(frac0)), "melt_group_set_split")
+
+
 def melt_forward_grouped(group, wave, offsets, lengths, basis_of, out, stream=None):
     lens, lp = _i64(lengths)
     offs, op = _i64(offsets)
@@ -581,12 +588,14 @@ class StftMelFrontend(Frontend):
 class GroupedFrontend:
     """Owns one melt_group over several Frontends (which must outlive it)."""
 
-    def __init__(self, frontends, graphs=True):
+    def __init__(self, frontends, graphs=True, shared_launch=False):
+        """shared_launch=True asks for both bases in one persistent launch (MELT_GROUP_SHARED)."""
         self.frontends = list(frontends)
         if any(fe.center for fe in self.frontends):
             raise ValueError("grouped launches frame clips from their first sample (center=False)")
         self.n_out = self.frontends[0].n_out
-        self.handle = melt_group_create(self.frontends, 0 if graphs else MELT_GROUP_NO_GRAPH)
+        flags = (0 if graphs else MELT_GROUP_NO_GRAPH) | (MELT_GROUP_SHARED if shared_launch else 0)
+        self.handle = melt_group_create(self.frontends, flags)
 
     def total_frames(self, lengths, basis_of):
         return sum(self.frontends[int(g)].num_frames(int(L)) for L, g in zip(lengths, basis_of))

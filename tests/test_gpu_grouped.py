@@ -210,3 +210,62 @@ def test_group_autotune_and_plan_cache(melt, tmp_path):
     gm.close()
     for fe in mixed:
         fe.close()
+
+
+@pytest.mark.parametrize("n,graphs", [(40, True), (7, False), (3, True)])
+def test_shared_launch_equals_per_basis_launches(melt, n, graphs):
+    """Two BF16 bases share one persistent launch (MELT_GROUP_SHARED; clusters
+    split between them, each running its own layout; the 22.05 kHz basis
+    takes a CTA-pair plan with its half basis streamed): bit for bit what one
+    launch per basis gives, for batches large and small (a basis with a
+    single tile), and at a set split."""
+    import torch
+    clips, ids = G.mixed_groups(n=n)
+    fes = _frontends(melt)
+    pk = G.pack_clips(clips)
+    wave = torch.from_numpy(pk.wave).cuda()
+    outs = []
+    for shared in (True, False):
+        gf = melt.GroupedFrontend(fes, graphs=graphs, shared_launch=shared)
+        T = gf.total_frames(pk.lengths, ids)
+        out = torch.full((T, gf.n_out), float("nan"), device="cuda")
+        for it in range(3):
+            if shared and it == 2:
+                melt.melt_group_set_split(gf.handle, 0.6)
+            out.fill_(float("nan"))
+            gf(wave, pk.offsets, pk.lengths, ids, out=out)
+        gf.sync()
+        outs.append(out.cpu().numpy())
+        gf.close()
+    assert not np.isnan(outs[0]).any()
+    np.testing.assert_array_equal(outs[0], outs[1])
+    ref = _per_clip_reference(fes, clips, ids)
+    np.testing.assert_array_equal(outs[0], ref)
+    for fe in fes:
+        fe.close()
+
+
+def test_shared_launch_follows_forced_plans(melt):
+    """A forced single-CTA plan keeps the per-basis launches; a forced CTA-pair
+    plan runs in the shared launch; both give the same bits."""
+    import torch
+    clips, ids = G.mixed_groups(n=12)
+    fes = _frontends(melt)
+    pk = G.pack_clips(clips)
+    wave = torch.from_numpy(pk.wave).cuda()
+    ref = _per_clip_reference(fes, clips, ids)
+    single = dict(basis_resident=0, a_buffers=2, prefetch_tiles=2, basis_slots=2, ksteps_per_slot=8, cta_pair=0,
+                  schedule=0)
+    pair = dict(basis_resident=0, a_buffers=2, prefetch_tiles=0, basis_slots=2, ksteps_per_slot=8, cta_pair=1,
+                schedule=0)
+    for pl in (single, pair):
+        melt.melt_plan_set(fes[1].handle, pl)
+        gf = melt.GroupedFrontend(fes, graphs=False, shared_launch=True)
+        T = gf.total_frames(pk.lengths, ids)
+        out = gf(wave, pk.offsets, pk.lengths, ids)
+        gf.sync()
+        np.testing.assert_array_equal(out.cpu().numpy(), ref)
+        gf.close()
+    melt.melt_plan_set(fes[1].handle, None)
+    for fe in fes:
+        fe.close()
