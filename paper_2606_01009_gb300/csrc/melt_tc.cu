@@ -707,7 +707,19 @@ cudaError_t tc_launch_pair_group(const TcBasis* tb0, const TcLaunch& L0, const T
   if (!group_pair_params(tb0, L0, q.g[0]) || !group_pair_params(tb1, L1, q.g[1])) return cudaSuccess;
   GroupKernelFn fn = kernel_for_pair_group();
   const int smem = (int)std::max(q.g[0].smem_total, q.g[1].smem_total);
-  static thread_local int set_smem = 0;  // the attribute already set for this size or larger
+  int dev = 0;
+  {
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+  }
+  // per thread: the device, the shared-memory size the attribute was set
+  // for, and the co-resident cluster count at that size
+  static thread_local int last_dev = -1, set_smem = 0, occ_smem = -1, occ_clusters = 0;
+  if (last_dev != dev) {
+    last_dev = dev;
+    set_smem = 0;
+    occ_smem = -1;
+  }
   if (set_smem < smem) {
     const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -727,7 +739,6 @@ cudaError_t tc_launch_pair_group(const TcBasis* tb0, const TcLaunch& L0, const T
   cfg.attrs = attr;
   cfg.numAttrs = 2;
   cfg.blockDim = dim3(pair_threads(false, MELT_BF16, false, 1, false), 1, 1);
-  static thread_local int occ_smem = -1, occ_clusters = 0;
   if (occ_smem != smem) {
     cfg.gridDim = dim3(2 * (L0.sm_count / 2), 1, 1);
     int n = 0;
