@@ -935,9 +935,9 @@ def time_fused_stft(W, dev, peaks):
 
 def sweeps(args, dev):
     """Paper's scaling figures on synthetic clips: the batch sweep (1..256 clips
-    of 4 s) and the Mel-count sweep (one 160 s clip, M = 40..512), MelT (BF16;
-    FP32 up to M = 128) against the torch.stft context pipeline on the same
-    GPU."""
+    of 4 s) and the Mel-count sweep (one 160 s clip, M = 40..512, and the
+    whole 64 x 30 s batch), MelT (BF16; FP32 up to M = 128 on the 160 s clip)
+    against the torch.stft context pipeline on the same GPU."""
     import torch
     from paper_2606_01009_gb300 import inputs as G
     from paper_2606_01009_gb300 import melt
@@ -977,6 +977,26 @@ def sweeps(args, dev):
         row["torch_stft_us"] = time_stft_batch(torch.from_numpy(clip[None, :].copy()), cfg, dev, steps=10)["ms_per_step"] * 1e3
         row["speedup_bf16_vs_stft"] = row["torch_stft_us"] / row["melt_bf16_us"]
         res["mels_160s"].append(row)
+    # the same Mel counts on the whole 64 x 30 s batch, where neither side is
+    # launch-bound: inputs rotate over two device copies (246 MB > L2)
+    res["mels_64x30s"] = []
+    clips64, _ = G.workload("rich_64x30s")
+    pk = G.pack_clips(clips64)
+    waves = [torch.from_numpy(pk.wave).to(dev) for _ in range(2)]
+    x64 = torch.from_numpy(np.stack(clips64))
+    for M in (40, 80, 128, 256, 512):
+        cfg = dict(base, n_mels=M)
+        fe = melt.Frontend(precision="bf16", n_mels=M)
+        T = fe.total_frames(pk.lengths)
+        outs = [torch.empty((T, M), device=dev) for _ in range(2)]
+        us = time_launches(lambda i: fe(waves[i % 2], pk.offsets, pk.lengths, out=outs[i % 2], input_ready=True),
+                           dev, 10) * 1e3
+        fe.close()
+        del outs
+        row = {"n_mels": M, "frames": T, "melt_bf16_us": us,
+               "torch_stft_us": time_stft_batch(x64, cfg, dev, steps=5)["ms_per_step"] * 1e3}
+        row["speedup_bf16_vs_stft"] = row["torch_stft_us"] / row["melt_bf16_us"]
+        res["mels_64x30s"].append(row)
     return res
 
 
