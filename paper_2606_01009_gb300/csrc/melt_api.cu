@@ -546,6 +546,7 @@ std::vector<float4> stft_filterbank(double sr, int n_fft, int n_bands, double fm
   }
   const int K = n_fft / 2 + 1;
   std::vector<float4> fb(K);
+  int prev = -1;  // band c of the epilogue's walk before bin k (the last in-range bin's b0)
   for (int k = 0; k < K; ++k) {
     const double f = (double)k * sr / n_fft;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -565,7 +566,12 @@ std::vector<float4> stft_filterbank(double sr, int n_fft, int n_bands, double fm
       v.y = i < n_bands ? (float)wrise : 0.f;
       b0 = i - 1;
     }
+    // bands completed before this bin's power is added (the walk moves from
+    // band prev to b0); bins outside every triangle add zero and complete none
+    const int nf = b0 >= -1 ? b0 - prev : 0;
+    if (b0 >= -1) prev = b0;
     std::memcpy(&v.z, &b0, sizeof(float));  // the band index's int bits
+    std::memcpy(&v.w, &nf, sizeof(float));
     fb[k] = v;
   }
   return fb;

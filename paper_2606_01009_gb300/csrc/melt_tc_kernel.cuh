@@ -594,7 +594,11 @@ static __device__ __forceinline__ void fill_dct(const TcParams& p, float* dct, i
 // order; acc0 holds band c, acc1 band c + 1.  A bin k adds w0 |X_k|^2 to band
 // b0(k) and w1 |X_k|^2 to band b0(k) + 1 (b0 is the same for every frame, so
 // the control flow is uniform); bands below b0(k) are complete and are
-// written (log(E + eps)) as c moves up to b0(k).
+// written (log(E + eps)) as c moves up to b0(k).  The host table gives, per
+// bin, how many bands complete before it (nf = b0(k) minus the previous
+// in-range bin's b0; 0 or 1 almost everywhere), so the walk takes no
+// comparison per bin: one flush on a uniform branch, a loop only for the
+// rare larger steps of narrow low-frequency bands.
 struct StftBands {
   float acc0, acc1;
   int c;
@@ -610,9 +614,12 @@ static __device__ __forceinline__ void stft_flush(StftBands& st, float* orow, in
 static __device__ __forceinline__ void stft_bin(StftBands& st, const float4* fbs, int k, float s2, float* orow,
                                                 int nb, float eps, bool valid) {
   const float4 f = fbs[k];
-  const int b0 = __float_as_int(f.z);
-  if (b0 < -1) return;  // outside every triangle
-  while (st.c < b0) stft_flush(st, orow, nb, eps, valid);
+  const int nf = __float_as_int(f.w);
+  if (nf > 0) {
+    stft_flush(st, orow, nb, eps, valid);
+    for (int i = 1; i < nf; ++i) stft_flush(st, orow, nb, eps, valid);
+  }
+  // bins outside every triangle carry zero weights
   st.acc0 = fmaf(f.x, s2, st.acc0);
   st.acc1 = fmaf(f.y, s2, st.acc1);
 }
