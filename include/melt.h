@@ -258,8 +258,9 @@ melt_status melt_forward_ex(melt_basis* basis, const float* wave, const int64_t*
  *     library until the process exits.  A batch that needs more tiles is
  *     rejected with MELT_ERR_ARG before anything is launched.
  *   The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current.  The basis must
- *     belong to the current device.
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     outside any stream capture.  The basis must belong to the current
+ *     device.
  *   All calls share the array, which keeps the previous call's descriptors;
  *     each call rewrites every entry it uses, so nothing needs clearing.
  *     Calls whose work overlaps on the GPU (different streams without
