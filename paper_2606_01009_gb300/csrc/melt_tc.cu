@@ -236,9 +236,10 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
     p.w2_step = (uint32_t)(p.MP / 2) * 32;
     p.mlp_w2_off = (uint32_t)(p.MP / 16) * p.w1_step;
     p.mlp_vec_off = p.mlp_w2_off + (uint32_t)(p.Hd / 16) * p.w2_step;
-    // TMEM: accumulator [0, NC), Y [160, 160 + MP) (over x-hat [192, 192 + MP/2),
-    // which GEMM1 has consumed by then), H and, in place, GELU(H) [256, 256 + Hd)
-    p.a1_col = 192;
+    // TMEM: accumulator [0, NC), Y [160, 160 + MP) with x-hat's band chunk c
+    // at 160 + 16 c (GEMM1 consumes it before Y is written), H and, in place,
+    // GELU(H) [256, 256 + Hd)
+    p.a1_col = 160;
     p.h_col = 256;
     p.y_col = 160;
     p.idesc1 = idesc_f32acc(1u, 2 * kF, (uint32_t)p.Hd);

@@ -20,10 +20,10 @@
 // Z row t + j, selected by the scale-factor byte j) and 2^-8 to the basis,
 // which is stored as e4m3(W 2^8).  The accumulator holds R and I directly.
 //
-// Warp roles per CTA (11 warps; 15 with the fused MLP):
+// Warp roles per CTA (11 warps; 19 with the fused MLP):
 //   warps 0-3   epilogue: TMEM -> registers, R^2 + I^2, log, (DCT), store (with
-//               the fused MLP, warps 0-7: warps e and e+4 read the same 32 TMEM
-//               lanes (frames) and split the columns, bands and hidden units)
+//               the fused MLP, warps 0-11: warps e, e+4 and e+8 read the same
+//               32 TMEM lanes (frames) and split the bands and hidden units)
 //   next warp   TMEM allocation for the pair; in the even CTA, the MMA issuer
 //   next warp   basis producer: this CTA's half of the basis, once
 //   next warp   waveform producer: bulk copies of the tile's FP32 span into a ring
@@ -34,11 +34,13 @@
 // epilogue writes x-hat = (x - mu)/sd as BF16 into TMEM and the even CTA
 // issues two more 2-SM MMAs with the A operand in TMEM: H = x-hat W1^T (W1
 // rows split between the CTAs like the basis) and, after the epilogue has
-// written GELU(H + b1) in BF16 over H, Y = GELU(H) W2^T.  The epilogue stores
-// x + Y + b2.  TMEM per CTA: the projection accumulator (one, columns
-// [0, NC)), Y at y_col over x-hat at a1_col (consumed by then), H and GELU(H)
-// at h_col.  The next tile's projection MMAs
-// run while the epilogue works through the MLP of this one.
+// written GELU(H + b1) in BF16 over H and x + b2 into the output columns,
+// Y = x + b2 + GELU(H) W2^T, which the epilogue stores.  TMEM per CTA: the
+// projection accumulator (one, columns [0, NC)), the output at y_col with
+// x-hat's band chunk c in the first half of the output's chunk c (consumed
+// by GEMM1 before anything is written there; each epilogue warp writes only
+// chunks it has read back itself), H and GELU(H) at h_col.  The next tile's
+// projection MMAs run while the epilogue works through the MLP of this one.
 //
 // Synchronisation.  Barriers that gate the pair's MMAs live in the even CTA
 // and count arrivals from both CTAs (the odd CTA arrives through its
@@ -57,12 +59,20 @@ namespace tc {
 // converters epw+3 .. epw+6.
 constexpr int kPCvtWarps = 4;
 constexpr int kPCvtThreads = 32 * kPCvtWarps;  // 128
-// Epilogue warps: 8 (two per TMEM lane quarter) with the fused MLP, for the
-// MFCC epilogue with the DCT on the tensor cores, and for the MFCC epilogue
-// with the DCT on the CUDA cores where M <= 80 (the two split the
-// coefficients); 4 otherwise.
+// Epilogue warps: 12 (three per TMEM lane quarter) with the fused MLP,
+// whose GELU of every hidden unit is the longest step of a tile; 8 (two per
+// quarter) for the MFCC epilogue with the DCT on the tensor cores and for the
+// MFCC epilogue with the DCT on the CUDA cores where M <= 80 (the two split
+// the coefficients); 4 otherwise.
+constexpr int kMlpParts = 2;  // fused MLP: epilogue warps per lane quarter
 __host__ __device__ constexpr int pair_epi_warps(bool mlp, bool mfcc = false, int nch = 1, bool dtc = false) {
-  return mlp || (mfcc && (dtc || nch <= 5)) ? 8 : 4;
+  return mlp ? 4 * kMlpParts : (mfcc && (dtc || nch <= 5)) ? 8 : 4;
+}
+
+// Part j of `parts` near-equal runs of n chunks, the larger runs first:
+// chunks [lo, hi).
+__host__ __device__ constexpr int part_lo(int n, int parts, int j) {
+  return j * (n / parts) + (j < n % parts ? j : n % parts);
 }
 // Converter warps: 4 (BF16: each sample converted once, short chains), 8 for
 // FP8's log-Mel kernel and its MFCC kernel with the DCT on the tensor cores,
@@ -353,40 +363,51 @@ static __device__ void pair_basis_producer(const TcParams& p, const PairCtx& c, 
 }
 
 // TMEM column of the packed GELU(H) of hidden chunk cc (16 units) in the
-// fused MLP.  GELU(H) is written over H itself: the two epilogue warps of a
-// lane quarter take hidden chunks [0, F) and [F, nH) (F = ceil(nH/2)), in
-// order, and each stores chunk cc only into H columns it has already read:
-// 8 cc for the first warp, 8 cc + 8 F for the second.
+// fused MLP.  GELU(H) is written over H itself: the kMlpParts epilogue warps
+// of a lane quarter take runs [lo_j, lo_{j+1}) of the hidden chunks
+// (part_lo), in order, and each stores chunk cc only into H columns it has
+// already read: 8 cc + 8 lo_j, inside its own run's columns [16 lo_j, 16 cc + 16).
 static __device__ __forceinline__ uint32_t gelu_col(const TcParams& p, int cc) {
-  const int nh = p.Hd / 16, first = (nh + 1) / 2;
-  return p.h_col + 8u * cc + (cc >= first ? 8u * first : 0u);
+  const int nh = p.Hd / 16;
+  int lo = 0;
+#pragma unroll
+  for (int j = 1; j < kMlpParts; ++j)
+    if (cc >= part_lo(nh, kMlpParts, j)) lo = part_lo(nh, kMlpParts, j);
+  return p.h_col + 8u * (uint32_t)(cc + lo);
 }
 
-// Fused MLP (even CTA's MMA thread), hidden layer: H = x-hat W1^T.  The
-// caller has seen the epilogues' release of the tile's accumulator, which
-// follows the x-hat stores.
+// Fused MLP (even CTA's MMA thread), hidden layer: H = x-hat W1^T, K-step s
+// reading x-hat's band chunk s at a1_col + 16 s.  The caller has seen the
+// epilogues' release of the tile's accumulator, which follows the x-hat
+// stores.
 static __device__ void pair_mlp_gemm1(const TcParams& p, const PairCtx& c, const PairBars& B,
                                       uint32_t tmem_base) {
   const uint64_t hi = (uint64_t)p.desc_hi << 32;
   const uint32_t w1 = ((c.sbase + p.off_mlp) >> 4) | ((((uint32_t)p.Hd / 2 * 16) >> 4) << 16);
   tc_fence_after();
   for (int s = 0; s < p.MP / 16; ++s)
-    mma_f16_pair_ts(tmem_base + p.h_col, tmem_base + p.a1_col + 8 * s, hi | (w1 + s * (p.w1_step >> 4)),
+    mma_f16_pair_ts(tmem_base + p.h_col, tmem_base + p.a1_col + 16 * s, hi | (w1 + s * (p.w1_step >> 4)),
                     p.idesc1, s > 0);
   mma_commit_pair_mc(pbar(p, c, B.h_full), 3);
 }
 
 // Fused MLP, output layer of the tile with ordinal j: once both CTAs'
-// epilogues have written GELU(H + b1) back, Y = GELU(H) W2^T.
+// epilogues have written GELU(H + b1) back and x + b2 into the output
+// columns, Y = x + b2 + GELU(H) W2^T (every K-step accumulates).
 static __device__ bool pair_mlp_gemm2(const TcParams& p, const PairCtx& c, const PairBars& B,
                                       uint32_t tmem_base, int j) {
   const uint64_t hi = (uint64_t)p.desc_hi << 32;
   const uint32_t w2 = ((c.sbase + p.off_mlp + p.mlp_w2_off) >> 4) | ((((uint32_t)p.MP / 2 * 16) >> 4) << 16);
+  // the K-steps' A columns before the wait, so that the MMAs issue back to back
+  const int nh = p.Hd / 16;  // <= 16
+  uint32_t ta[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) ta[s] = tmem_base + gelu_col(p, s < nh ? s : 0);
   if (!mbar_wait_cluster(pbar(p, c, B.a2_full), j & 1, c.abort, p.err, kErrTimeout)) return false;
   tc_fence_after();
-  for (int s = 0; s < p.Hd / 16; ++s)
-    mma_f16_pair_ts(tmem_base + p.y_col, tmem_base + gelu_col(p, s), hi | (w2 + s * (p.w2_step >> 4)),
-                    p.idesc2, s > 0);
+#pragma unroll
+  for (int s = 0; s < 16; ++s)
+    if (s < nh) mma_f16_pair_ts(tmem_base + p.y_col, ta[s], hi | (w2 + s * (p.w2_step >> 4)), p.idesc2, true);
   mma_commit_pair_mc(pbar(p, c, B.y_full), 3);
   return true;
 }
@@ -1102,17 +1123,61 @@ static __device__ __forceinline__ float gelu_poly(float h) {
   return fmaxf(h, 0.f) - t * e * r;
 }
 
-// Epilogue with the fused correction MLP: log-Mel of the row (kept in
-// registers), x-hat to TMEM, GELU of the hidden layer over H, then
-// y = x + Y + b2 stored.  The two warps of a lane quarter split the bands and
-// the hidden units.  Every step is taken for an empty tile too (without
-// loads or stores) so that both CTAs keep the barrier phases in step.
+// GELU(H + b1) of hidden chunk cc (16 units, in h) to BF16 over H at TMEM
+// address `to` (gelu_col: the chunk's warp starts its run at lo, to = lanes +
+// h_col + 8 (cc + lo)).
+static __device__ __forceinline__ void gelu_chunk(uint32_t to, const float* b1, int cc, const float (&h)[16]) {
+  const float4* b4 = reinterpret_cast<const float4*>(b1 + 16 * cc);  // 16-byte aligned
+  float bb[16];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const float4 q = b4[v];
+    bb[4 * v] = q.x;
+    bb[4 * v + 1] = q.y;
+    bb[4 * v + 2] = q.z;
+    bb[4 * v + 3] = q.w;
+  }
+  uint32_t w[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e)
+    w[e] = pack_bf16(gelu_poly(h[2 * e] + bb[2 * e]), gelu_poly(h[2 * e + 1] + bb[2 * e + 1]));
+  tmem_st8(to, w);
+}
+
+// The fused-MLP epilogue's log-Mel (Eq. 8) of this warp's band chunks of
+// the row, from the projection accumulator into v (one chunk per wait).
+template <int NV>
+static __device__ __forceinline__ void mlp_logmel(const TcParams& p, uint32_t tl, int c_lo, int c_hi,
+                                                  float (&v)[16 * NV]) {
+#pragma unroll
+  for (int g = 0; g < NV; ++g) {
+    if (c_lo + g < c_hi) {
+      const int cc = c_lo + g;
+      float re[16], im[16];
+      tmem_ld16(tl + 16 * cc, re);
+      tmem_ld16(tl + p.MP + 16 * cc, im);
+      tmem_ld_wait(re, im);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) v[16 * g + e] = fast_ln(fmaf(re[e], re[e], fmaf(im[e], im[e], p.eps)));
+    }
+  }
+}
+
+// Epilogue with the fused correction MLP.  Per pair step k: x-hat of the
+// row (BF16) into TMEM and the accumulator released; once the hidden layer
+// is in, x + b2 into the output columns (over x-hat) and GELU(H + b1) over
+// H; while the output layer runs, the log-Mel of step k + 1 from its
+// accumulator into registers; then the output layer's sum
+// x + b2 + GELU(H) W2^T stored.  The kMlpParts warps of a lane quarter
+// split the bands and the hidden units (part_lo).  Every step is taken for an empty tile too
+// (without loads or stores) so that both CTAs keep the barrier phases in
+// step.
 template <int NCH>
 __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairCtx& c, const PairBars& B,
                                   uint32_t tmem_base) {
-  constexpr int NV = (NCH + 1) / 2;  // band chunks of the larger half
+  constexpr int NV = (NCH + kMlpParts - 1) / kMlpParts;  // band chunks of the largest part
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int quarter = warp & 3, half = warp >> 2;
+  const int quarter = warp & 3, part = warp >> 2;
   const int row = 32 * quarter + lane;
   const float* vec = reinterpret_cast<const float*>(gbase + p.off_mlp + p.mlp_vec_off);
   const float* b1 = vec;                 // [Hd]
@@ -1121,85 +1186,97 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
   const float* isd = mu + p.MP;          // [MP]
   const bool vec8 = ((p.n_out & 7) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 31) == 0);
   const uint32_t tl = tmem_base + ((uint32_t)(32 * quarter) << 16);  // this warp's lanes
-  int c_lo, c_hi, h_lo, h_hi;
-  half_chunks(NCH, 2, half, c_lo, c_hi);
-  half_chunks(p.Hd / 16, 2, half, h_lo, h_hi);
+  const int c_lo = part_lo(NCH, kMlpParts, part), c_hi = part_lo(NCH, kMlpParts, part + 1);
+  const int h_lo = part_lo(p.Hd / 16, kMlpParts, part), h_hi = part_lo(p.Hd / 16, kMlpParts, part + 1);
+  if (c.cluster >= p.n_pairs) return;
+  TileDesc td = pair_tile(p, c, c.cluster);
+  if (!warp_wait_cl(pbar(p, c, B.t_full), 0, c.abort, p.err)) return;
+  tc_fence_after();
+  bool live = td.n_frames > 0;
+  float v[16 * NV];
+  if (live) mlp_logmel<NV>(p, tl, c_lo, c_hi, v);
   for (int k = 0;; ++k) {
-    bool okq = true;
-    const int q = k == 0 ? c.cluster : pair_next_warp(p, c, B, k, okq);
-    if (!okq || q >= p.n_pairs) break;
-    const TileDesc td = pair_tile(p, c, q);
-    const bool live = td.n_frames > 0;
     const bool valid = row < td.n_frames;
     float* orow = p.out + (size_t)(td.out_row + row) * p.n_out;
-    // 1. log-Mel (Eq. 8) of this half of the row, and its x-hat in BF16 into TMEM
-    if (!warp_wait_cl(pbar(p, c, B.t_full), k & 1, c.abort, p.err)) break;
-    sched_release(p, c, B, k);
-    tc_fence_after();
-    float v[16 * NV];
+    // 1. x-hat in BF16 into TMEM (chunk cc over the first half of the
+    // output's chunk cc, which this warp has read back); the accumulator
+    // released
     if (live) {
 #pragma unroll
       for (int g = 0; g < NV; ++g) {
-        if (c_lo + g < c_hi) {  // one chunk per wait: the row's log values stay in registers
-          const int cc = c_lo + g;
-          float re[16], im[16];
-          tmem_ld16(tl + 16 * cc, re);
-          tmem_ld16(tl + p.MP + 16 * cc, im);
-          tmem_ld_wait(re, im);
-#pragma unroll
-          for (int e = 0; e < 16; ++e) v[16 * g + e] = fast_ln(fmaf(re[e], re[e], fmaf(im[e], im[e], p.eps)));
+        const int cc = c_lo + g;
+        if (cc < c_hi) {
           uint32_t w[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int m = 16 * cc + 2 * e;
             w[e] = pack_bf16((v[16 * g + 2 * e] - mu[m]) * isd[m], (v[16 * g + 2 * e + 1] - mu[m + 1]) * isd[m + 1]);
           }
-          tmem_st8(tl + p.a1_col + 8 * cc, w);
+          tmem_st8(tl + p.a1_col + 16 * cc, w);
         }
       }
       tmem_st_wait();
     }
     tc_fence_before();
     warp_arrive_leader(pbar(p, c, B.t_empty));
-    // 2. hidden layer: GELU(H + b1) in BF16, written over H (see gelu_col), two chunks per wait
+    // 2. once H is in (x-hat consumed): x + b2 into the output columns, then
+    // GELU(H + b1) in BF16 over H (see gelu_col), the next chunk's load in
+    // flight while one chunk is evaluated
     if (!warp_wait_cl(pbar(p, c, B.h_full), k & 1, c.abort, p.err)) break;
     tc_fence_after();
     if (live) {
-#pragma unroll 1
-      for (int c0 = h_lo; c0 < h_hi; c0 += 2) {
-        float h[2][16];
 #pragma unroll
-        for (int t = 0; t < 2; ++t)
-          if (c0 + t < h_hi) tmem_ld16(tl + p.h_col + 16 * (c0 + t), h[t]);
-        tmem_ld_wait();
+      for (int g = 0; g < NV; ++g) {
+        const int cc = c_lo + g;
+        if (cc < c_hi) {
+          uint32_t r0[8], r1[8];
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          reg_fence16(h[t]);
-          const int cc = c0 + t;
-          if (cc < h_hi) {
-            const float4* b4 = reinterpret_cast<const float4*>(b1 + 16 * cc);  // 16-byte aligned
-            float bb[16];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              const float4 q = b4[v];
-              bb[4 * v] = q.x;
-              bb[4 * v + 1] = q.y;
-              bb[4 * v + 2] = q.z;
-              bb[4 * v + 3] = q.w;
-            }
-            uint32_t w[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-              w[e] = pack_bf16(gelu_poly(h[t][2 * e] + bb[2 * e]), gelu_poly(h[t][2 * e + 1] + bb[2 * e + 1]));
-            tmem_st8(tl + gelu_col(p, cc), w);
+          for (int e = 0; e < 8; ++e) {
+            r0[e] = __float_as_uint(v[16 * g + e] + b2[16 * cc + e]);
+            r1[e] = __float_as_uint(v[16 * g + 8 + e] + b2[16 * cc + 8 + e]);
           }
+          tmem_st8(tl + p.y_col + 16 * cc, r0);
+          tmem_st8(tl + p.y_col + 16 * cc + 8, r1);
         }
+      }
+      float ha[16], hb[16];
+      tmem_ld16(tl + p.h_col + 16 * h_lo, ha);  // (every part has hidden chunks: Hd >= 160)
+      tmem_ld_wait();
+      reg_fence16(ha);
+#pragma unroll 1
+      for (int cc = h_lo; cc < h_hi; cc += 2) {
+        // chunk cc in ha; chunk cc + 1 loads into hb meanwhile
+        if (cc + 1 < h_hi) tmem_ld16(tl + p.h_col + 16 * (cc + 1), hb);
+        gelu_chunk(tl + p.h_col + 8u * (uint32_t)(cc + h_lo), b1, cc, ha);
+        if (cc + 1 >= h_hi) break;
+        tmem_ld_wait();
+        reg_fence16(hb);
+        // chunk cc + 1 in hb; chunk cc + 2 loads into ha meanwhile
+        if (cc + 2 < h_hi) tmem_ld16(tl + p.h_col + 16 * (cc + 2), ha);
+        gelu_chunk(tl + p.h_col + 8u * (uint32_t)(cc + 1 + h_lo), b1, cc + 1, hb);
+        tmem_ld_wait();
+        reg_fence16(ha);
       }
       tmem_st_wait();
     }
     tc_fence_before();
     warp_arrive_leader(pbar(p, c, B.a2_full));
-    // 3. y = x + Y + b2 for this half's bands
+    // 3. while the output layer runs: the next step's pair, and its log-Mel
+    // (its projection was queued right after this step's hidden layer)
+    bool okq = true;
+    const int qn = pair_next_warp(p, c, B, k + 1, okq);
+    const bool more = okq && qn < p.n_pairs;
+    TileDesc tn = td;
+    bool live_n = false;
+    if (more) {
+      tn = pair_tile(p, c, qn);
+      if (!warp_wait_cl(pbar(p, c, B.t_full), (k + 1) & 1, c.abort, p.err)) break;
+      sched_release(p, c, B, k + 1);
+      tc_fence_after();
+      live_n = tn.n_frames > 0;
+      if (live_n) mlp_logmel<NV>(p, tl, c_lo, c_hi, v);  // (this step's v is in TMEM as x + b2)
+    }
+    // 4. the output layer's sum for this warp's bands
     if (!warp_wait_cl(pbar(p, c, B.y_full), k & 1, c.abort, p.err)) break;
     tc_fence_after();
     if (live) {
@@ -1211,8 +1288,6 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
           tmem_ld16(tl + p.y_col + 16 * cc, y);
           tmem_ld_wait();
           reg_fence16(y);
-#pragma unroll
-          for (int e = 0; e < 16; ++e) y[e] = v[16 * g + e] + y[e] + b2[16 * cc + e];
           if (valid) {
             if (vec8 && 16 * cc + 16 <= p.M) {
               stg256(orow + 16 * cc, y);
@@ -1226,6 +1301,9 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
         }
       }
     }
+    if (!more) break;
+    td = tn;
+    live = live_n;
   }
 }
 

@@ -139,7 +139,7 @@ struct TcParams {
   uint32_t mlp_w2_off, mlp_vec_off;  // W2 blocks and FP32 vectors within a half
   uint32_t w1_step, w2_step;         // bytes per K-step block of this CTA's W1 / W2 rows
   uint32_t idesc1, idesc2;           // the two MLP GEMMs (M = 256, N = Hd / MP)
-  uint32_t a1_col, h_col, y_col;     // TMEM columns of x-hat, the hidden layer, the output
+  uint32_t a1_col, h_col, y_col;     // TMEM columns of x-hat (chunk c at a1_col + 16 c), the hidden layer, the output
   // CTA-pair kernel, MFCC with the DCT-II on the tensor cores (dct_tc = 1):
   // the log-Mel row goes to TMEM as a split-BF16 A operand (hi and lo parts,
   // MP/2 columns each, at dct_ahi / dct_alo), the DCT matrix sits in shared
