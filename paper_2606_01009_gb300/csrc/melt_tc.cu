@@ -257,7 +257,7 @@ bool try_layout_pair(const TcBasis* tb, TcParams& p, const melt_plan& c, int n_m
   } else {
     const int nchunk = (int)((span_bytes + 16383) / 16384);
     int ch = (p.zrows + nchunk - 1) / nchunk;
-    const int max_rows = kPQuads * kPCvtThreads * 4 / p.H;
+    const int max_rows = kPQuads * (p.Hd > 0 ? 32 * kMlpCvtWarps : kPCvtThreads) * 4 / p.H;
     if (ch > max_rows) ch = std::max(1, max_rows);
     chs[nch_c++] = ch;
     // smaller chunks where the 16 KB ones leave no room for a ring of two

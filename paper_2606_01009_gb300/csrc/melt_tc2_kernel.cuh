@@ -20,15 +20,17 @@
 // Z row t + j, selected by the scale-factor byte j) and 2^-8 to the basis,
 // which is stored as e4m3(W 2^8).  The accumulator holds R and I directly.
 //
-// Warp roles per CTA (11 warps; 19 with the fused MLP):
+// Warp roles per CTA (11 warps; 16 with the fused MLP):
 //   warps 0-3   epilogue: TMEM -> registers, R^2 + I^2, log, (DCT), store (with
 //               the fused MLP, warps 0-11: warps e, e+4 and e+8 read the same
 //               32 TMEM lanes (frames) and split the bands and hidden units)
 //   next warp   TMEM allocation for the pair; in the even CTA, the MMA issuer
-//   next warp   basis producer: this CTA's half of the basis, once
+//   next warp   basis producer: this CTA's half of the basis, once (with the
+//               fused MLP, lane 1 of the MMA warp instead)
 //   next warp   waveform producer: bulk copies of the tile's FP32 span into a ring
 //   last four   converters: staged FP32 samples -> polyphase Z rows (BF16, or
-//               e4m3 with per-row scales written to TMEM)
+//               e4m3 with per-row scales written to TMEM; two warps with the
+//               fused MLP)
 //
 // Fused correction MLP (template flag MLP).  After the log-Mel of a tile the
 // epilogue writes x-hat = (x - mu)/sd as BF16 into TMEM and the even CTA
@@ -54,17 +56,21 @@
 namespace melt {
 namespace tc {
 
-// Warp layout of a pair kernel with `epw` epilogue warps (4, or 8 with the
-// fused MLP): epilogue 0..epw-1, MMA epw, basis epw+1, waveform epw+2,
-// converters epw+3 .. epw+6.
+// Warp layout of a pair kernel with `epw` epilogue warps: epilogue
+// 0..epw-1, MMA epw, basis epw+1, waveform epw+2, then the converters.  With
+// the fused MLP the basis producer runs on lane 1 of the MMA warp instead
+// (its work is a few copies at the start), so the block is 16 warps: 12
+// epilogue, MMA + basis, waveform, 2 converters, and keeps 128 registers a
+// thread.
 constexpr int kPCvtWarps = 4;
 constexpr int kPCvtThreads = 32 * kPCvtWarps;  // 128
+constexpr int kMlpCvtWarps = 2;                // converter warps with the fused MLP
 // Epilogue warps: 12 (three per TMEM lane quarter) with the fused MLP,
 // whose GELU of every hidden unit is the longest step of a tile; 8 (two per
 // quarter) for the MFCC epilogue with the DCT on the tensor cores and for the
 // MFCC epilogue with the DCT on the CUDA cores where M <= 80 (the two split
 // the coefficients); 4 otherwise.
-constexpr int kMlpParts = 2;  // fused MLP: epilogue warps per lane quarter
+constexpr int kMlpParts = 3;  // fused MLP: epilogue warps per lane quarter
 __host__ __device__ constexpr int pair_epi_warps(bool mlp, bool mfcc = false, int nch = 1, bool dtc = false) {
   return mlp ? 4 * kMlpParts : (mfcc && (dtc || nch <= 5)) ? 8 : 4;
 }
@@ -78,13 +84,15 @@ __host__ __device__ constexpr int part_lo(int n, int parts, int j) {
 // FP8's log-Mel kernel and its MFCC kernel with the DCT on the tensor cores,
 // whose per-row max makes each chunk one dependent chain per row set (twice
 // the warps, half the chain).  The MFCC kernels with the DCT on the CUDA
-// cores keep 4 (their epilogue warps and registers fill the block).
-__host__ __device__ constexpr int pair_cvt_warps(int prec, bool mfcc, int nch, bool dtc = false) {
-  return prec == MELT_FP8E4M3 && (!mfcc || dtc) ? 8 : 4;
+// cores keep 4 (their epilogue warps and registers fill the block).  With
+// the fused MLP, 2: a tile takes several microseconds there, and the warps
+// go to the epilogue.
+__host__ __device__ constexpr int pair_cvt_warps(int prec, bool mfcc, int nch, bool dtc = false, bool mlp = false) {
+  return mlp ? kMlpCvtWarps : prec == MELT_FP8E4M3 && (!mfcc || dtc) ? 8 : 4;
 }
 __host__ __device__ constexpr int pair_threads(bool mlp, int prec = MELT_BF16, bool mfcc = false, int nch = 1,
                                                bool dtc = false) {
-  return 32 * (pair_epi_warps(mlp, mfcc, nch, dtc) + 3 + pair_cvt_warps(prec, mfcc, nch, dtc));
+  return 32 * (pair_epi_warps(mlp, mfcc, nch, dtc) + (mlp ? 2 : 3) + pair_cvt_warps(prec, mfcc, nch, dtc, mlp));
 }
 constexpr int kPQuads = 8;  // float4s per converter thread per staged chunk (<= 16 KB)
 constexpr uint32_t kSfOne = 0x7F7F7F7Fu;    // four UE8M0 codes of 2^0
@@ -601,7 +609,7 @@ static __device__ void pair_mma(const TcParams& p, uint8_t* gbase, const PairCtx
 // (lanes read consecutive quads: conflict-free); quad hq is the low or high
 // half (hq & 1) of the Z row segment (row ul, 8-sample group kc) with
 // 8 * (hq >> 1) = (ul - ch*CH) H + 8 kc.
-template <bool SPLIT>
+template <bool SPLIT, int CT = kPCvtThreads>
 static __device__ void pair_convert(const TcParams& p, const PairCtx& c, const PairBars& B, int cvt0) {
   const int ct = threadIdx.x - 32 * cvt0;
   const int H8 = p.H >> 3;
@@ -610,7 +618,7 @@ static __device__ void pair_convert(const TcParams& p, const PairCtx& c, const P
   int qrow[kPQuads];
 #pragma unroll
   for (int q = 0; q < kPQuads; ++q) {
-    const int hq = ct + q * kPCvtThreads;
+    const int hq = ct + q * CT;
     const int il = hq >> 1;
     const int ull = il / H8;
     const int kc = il - ull * H8;
@@ -647,10 +655,10 @@ static __device__ void pair_convert(const TcParams& p, const PairCtx& c, const P
       for (int q = 0; q < kPQuads; ++q)
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                      : "=f"(x[q].x), "=f"(x[q].y), "=f"(x[q].z), "=f"(x[q].w)
-                     : "r"(st + 16u * min(ct + q * kPCvtThreads, nq_full - 1)));
+                     : "r"(st + 16u * min(ct + q * CT, nq_full - 1)));
       if (tail) {
 #pragma unroll
-        for (int q = 0; q < kPQuads; ++q) clip_quad(x[q], s_base + 4 * (ct + q * kPCvtThreads), nsamp);
+        for (int q = 0; q < kPQuads; ++q) clip_quad(x[q], s_base + 4 * (ct + q * CT), nsamp);
       }
 #pragma unroll
       for (int q = 0; q < kPQuads; ++q) {
@@ -1312,8 +1320,9 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
 template <int NCH, bool MFCC, bool MLP, int PREC, bool DTC>
 __device__ __forceinline__ void pair_cta(const TcParams& p, int cluster, int n_clusters) {
   constexpr int EPW = pair_epi_warps(MLP, MFCC, NCH, DTC);
-  constexpr int kPMmaWarp = EPW, kPBWarp = EPW + 1, kPProdWarp = EPW + 2, kPCvtWarp0 = EPW + 3;
-  constexpr int CW = pair_cvt_warps(PREC, MFCC, NCH, DTC);
+  // (fused MLP: the basis producer on lane 1 of the MMA warp)
+  constexpr int kPMmaWarp = EPW, kPBWarp = MLP ? EPW : EPW + 1, kPProdWarp = kPBWarp + 1, kPCvtWarp0 = kPProdWarp + 1;
+  constexpr int CW = pair_cvt_warps(PREC, MFCC, NCH, DTC, MLP);
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 127u) & ~127u;
@@ -1425,6 +1434,8 @@ __device__ __forceinline__ void pair_cta(const TcParams& p, int cluster, int n_c
       if (c.rank == 0) pair_mma<MLP, PREC, DTC>(p, gbase, c, B, tmem_base);
       else if (!p.b_resident) pair_basis_signal(p, c, B);  // the odd CTA's slots, to the even CTA
       drain_wait(pbar(p, c, B.drain), 0, p.err);
+    } else if (MLP && lane == 1) {
+      pair_basis_producer(p, c, B);
     }
     __syncwarp();
   } else if (warp == kPBWarp) {
@@ -1439,7 +1450,7 @@ __device__ __forceinline__ void pair_cta(const TcParams& p, int cluster, int n_c
     if constexpr (PREC == MELT_FP8E4M3)
       pair_convert_fp8<CW>(p, gbase, c, B, kPCvtWarp0, tmem_base);
     else
-      pair_convert<PREC == MELT_BF16X3>(p, c, B, kPCvtWarp0);
+      pair_convert<PREC == MELT_BF16X3, 32 * CW>(p, c, B, kPCvtWarp0);
     __syncwarp();
   } else {
     pdl_wait();
