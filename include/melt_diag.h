@@ -29,9 +29,9 @@ melt_status melt_diag_wait_timeout(melt_basis* basis, void* stream);
  * melt_diag_gelu - evaluates, on n device floats h, the GELU that the CTA-pair
  *   kernel's fused correction epilogue applies to the hidden layer: GELU(h) =
  *   h Phi(h) (the exact-erf form the model is trained with), computed as
- *   max(h, 0) - |h| phi(|h|) R(|h|) with a polynomial R for the Mills ratio of
- *   the normal tail.  Stated accuracy against the exact function: relative
- *   error <= 7e-5 for |h| <= 5, absolute error <= 5e-6 everywhere.  The paper
+ *   max(h, 0) - |h| Q(|h|), the normal tail Q(t) = 2^(S(t) - t^2 log2(e) / 2)
+ *   with a polynomial S.  Stated accuracy against the exact function:
+ *   relative error <= 2e-5 for |h| <= 5, absolute error <= 3e-6 everywhere.  The paper
  *   has no counterpart (it evaluates no correction layer); this entry point
  *   lets a test check that bound.
  *   h, y    device float[n] (may be the same array)

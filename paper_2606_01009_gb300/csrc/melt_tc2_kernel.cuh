@@ -1102,33 +1102,31 @@ __device__ void pair_epilogue(const TcParams& p, uint8_t* gbase, const PairCtx& 
 // GELU(h) = h Phi(h), the exact-erf form the model is trained with, for the
 // fused epilogue, whose result is rounded to BF16 (8 significant bits).
 // With t = |h| and Q(t) = 1 - Phi(t) the upper normal tail,
-//     GELU(h) = max(h, 0) - t Q(t),   Q(t) = phi(t) R(t),
-// phi the standard normal density and R = Q / phi the Mills ratio, which is
-// smooth and slowly varying on [0, 5].  R / sqrt(2 pi) is a degree-9
-// polynomial in u = 0.4 t - 1, the Chebyshev least-squares fit on [0, 5]
-// (4000 Chebyshev nodes) rounded to float32; phi(t) sqrt(2 pi) =
-// 2^(-t^2 log2(e) / 2) comes from the hardware base-2 exponential.  Against
-// the exact function (float64, a 1e-5 grid) the float32 evaluation has a
-// relative error <= 7e-5 for |h| <= 5 (2^-14, far below half a BF16 ulp) and
-// an absolute error <= 5e-6 everywhere (R is taken at min(t, 5): the tail
-// beyond is below 1.5e-6 in magnitude).  About 17 FP32 operations and one
-// multi-function-unit operation, against several times that for erff.
+//     GELU(h) = max(h, 0) - t Q(t),   log2 Q(t) = -t^2 log2(e) / 2 + S(t),
+// where S (log2 of the Mills ratio over sqrt(2 pi)) is smooth on [0, 5],
+// from -1 at t = 0 to about -3.7 at t = 5.  S is a degree-6 polynomial in
+// u = 0.4 t - 1: the Chebyshev fit on [0, 5] refined towards minimax by
+// Lawson reweighting (30 passes on a 4e5-point grid), in the power basis
+// rounded to float32; Q = 2^(S - t^2 log2(e) / 2) from the hardware base-2
+// exponential.  Against the exact function (float64) the float32 evaluation
+// has a relative error <= 2e-5 for |h| <= 5 (about 2^-16, far below half a
+// BF16 ulp) and an absolute error <= 3e-6 everywhere (S is taken at
+// min(t, 5): beyond, the tail is below 1.5e-6 in magnitude).  About a dozen
+// FP32 operations and one multi-function-unit operation (the degree-9 fit of
+// the Mills ratio it replaces took 17).
 static __device__ __forceinline__ float gelu_poly(float h) {
   const float t = fabsf(h);
   const float u = fmaf(0.4f, fminf(t, 5.f), -1.f);
-  float r = -5.916386843e-03f;
-  r = fmaf(r, u, 1.064418070e-02f);
-  r = fmaf(r, u, -5.160273518e-03f);
-  r = fmaf(r, u, 9.528063238e-03f);
-  r = fmaf(r, u, -2.687160671e-02f);
-  r = fmaf(r, u, 4.192553833e-02f);
-  r = fmaf(r, u, -5.953888968e-02f);
-  r = fmaf(r, u, 8.501806855e-02f);
-  r = fmaf(r, u, -1.140514612e-01f);
-  r = fmaf(r, u, 1.413371563e-01f);
-  float e;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(t * t * -0.72134752044448170f));  // 2^(-t^2 log2(e) / 2)
-  return fmaxf(h, 0.f) - t * e * r;
+  float r = 7.192788180e-03f;
+  r = fmaf(r, u, -2.606392093e-02f);
+  r = fmaf(r, u, 6.437100470e-02f);
+  r = fmaf(r, u, -1.599922627e-01f);
+  r = fmaf(r, u, 4.010236561e-01f);
+  r = fmaf(r, u, -1.164181113e+00f);
+  r = fmaf(r, u, -2.822842598e+00f);
+  float q;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(q) : "f"(fmaf(t * -0.72134752044448170f, t, r)));  // Q(t)
+  return fmaf(-t, q, fmaxf(h, 0.f));
 }
 
 // GELU(H + b1) of hidden chunk cc (16 units, in h) to BF16 over H at TMEM

@@ -289,8 +289,8 @@ def _fused_case(melt, seed, lens, Hd=256):
 
 def test_fused_gelu_error_bound(melt):
     """The fused epilogue's GELU against the exact h Phi(h) (FP64) on a fine grid
-    over [-12, 12] and on random values: relative error <= 7e-5 for |h| <= 5,
-    absolute error <= 5e-6 everywhere (the stated bound)."""
+    over [-12, 12] and on random values: relative error <= 2e-5 for |h| <= 5,
+    absolute error <= 3e-6 everywhere (the stated bound)."""
     import torch
     g = np.random.default_rng(17)
     h = np.concatenate([np.linspace(-12, 12, 2_400_001), g.standard_normal(200000) * 3,
@@ -302,10 +302,10 @@ def test_fused_gelu_error_bound(melt):
     got = y.cpu().numpy().astype(np.float64)
     exact = P.gelu(h.astype(np.float64))
     err = np.abs(got - exact)
-    assert err.max() <= 5e-6, float(err.max())
+    assert err.max() <= 3e-6, float(err.max())
     inner = (np.abs(h) <= 5) & (exact != 0)
     rel = err[inner] / np.abs(exact[inner])
-    assert rel.max() <= 7e-5, float(rel.max())
+    assert rel.max() <= 2e-5, float(rel.max())
     print(f"fused GELU: max abs {err.max():.2e}, max rel (|h| <= 5) {rel.max():.2e}")
 
 
@@ -325,9 +325,9 @@ def _fused_bound(params, x, mu, sd):
     u = 2.0 ** -24
     s1 = np.abs(xh_b) @ np.abs(W1_b).T
     dh = 2.0 ** -8 * s1 + 100 * u * s1 + u * np.abs(np.asarray(params[1], np.float64))
-    # GELU(h + b1) itself: the epilogue's polynomial form (relative error <= 7e-5
-    # for |h| <= 5, absolute <= 5e-6) before its BF16 rounding
-    da = 1.13 * dh + (2.0 ** -8 + 7e-5) * np.abs(a_b) + 5e-6
+    # GELU(h + b1) itself: the epilogue's polynomial form (relative error <= 2e-5
+    # for |h| <= 5, absolute <= 3e-6) before its BF16 rounding
+    da = 1.13 * dh + (2.0 ** -8 + 2e-5) * np.abs(a_b) + 3e-6
     s2 = np.abs(a_b) @ np.abs(W2_b).T
     bound = da @ np.abs(W2_b).T + 300 * u * (np.abs(x) + s2 + np.abs(np.asarray(params[3], np.float64)))
     return y, bound
