@@ -75,10 +75,15 @@ __host__ __device__ constexpr int pair_epi_warps(bool mlp, bool mfcc = false, in
   return mlp ? 4 * kMlpParts : (mfcc && (dtc || nch <= 5)) ? 8 : 4;
 }
 
-// Part j of `parts` near-equal runs of n chunks, the larger runs first:
-// chunks [lo, hi).
+// Part j of `parts` near-equal runs of n chunks: chunks [lo_j, lo_{j+1}),
+// the larger runs first (part_lo) or last (part_lo_tail).  The fused MLP's
+// epilogue splits the bands with the first and the hidden units with the
+// second, so that its warps' shares of the two even out.
 __host__ __device__ constexpr int part_lo(int n, int parts, int j) {
   return j * (n / parts) + (j < n % parts ? j : n % parts);
+}
+__host__ __device__ constexpr int part_lo_tail(int n, int parts, int j) {
+  return j * (n / parts) + (j > parts - n % parts ? j - (parts - n % parts) : 0);
 }
 // Converter warps: 4 (BF16: each sample converted once, short chains), 8 for
 // FP8's log-Mel kernel and its MFCC kernel with the DCT on the tensor cores,
@@ -373,14 +378,15 @@ static __device__ void pair_basis_producer(const TcParams& p, const PairCtx& c, 
 // TMEM column of the packed GELU(H) of hidden chunk cc (16 units) in the
 // fused MLP.  GELU(H) is written over H itself: the kMlpParts epilogue warps
 // of a lane quarter take runs [lo_j, lo_{j+1}) of the hidden chunks
-// (part_lo), in order, and each stores chunk cc only into H columns it has
-// already read: 8 cc + 8 lo_j, inside its own run's columns [16 lo_j, 16 cc + 16).
+// (part_lo_tail), in order, and each stores chunk cc only into H columns it
+// has already read: 8 cc + 8 lo_j, inside its own run's columns
+// [16 lo_j, 16 cc + 16).
 static __device__ __forceinline__ uint32_t gelu_col(const TcParams& p, int cc) {
   const int nh = p.Hd / 16;
   int lo = 0;
 #pragma unroll
   for (int j = 1; j < kMlpParts; ++j)
-    if (cc >= part_lo(nh, kMlpParts, j)) lo = part_lo(nh, kMlpParts, j);
+    if (cc >= part_lo_tail(nh, kMlpParts, j)) lo = part_lo_tail(nh, kMlpParts, j);
   return p.h_col + 8u * (uint32_t)(cc + lo);
 }
 
@@ -1175,7 +1181,7 @@ static __device__ __forceinline__ void mlp_logmel(const TcParams& p, uint32_t tl
 // H; while the output layer runs, the log-Mel of step k + 1 from its
 // accumulator into registers; then the output layer's sum
 // x + b2 + GELU(H) W2^T stored.  The kMlpParts warps of a lane quarter
-// split the bands and the hidden units (part_lo).  Every step is taken for an empty tile too
+// split the bands (part_lo) and the hidden units (part_lo_tail).  Every step is taken for an empty tile too
 // (without loads or stores) so that both CTAs keep the barrier phases in
 // step.
 template <int NCH>
@@ -1193,7 +1199,7 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
   const bool vec8 = ((p.n_out & 7) == 0) && ((reinterpret_cast<uintptr_t>(p.out) & 31) == 0);
   const uint32_t tl = tmem_base + ((uint32_t)(32 * quarter) << 16);  // this warp's lanes
   const int c_lo = part_lo(NCH, kMlpParts, part), c_hi = part_lo(NCH, kMlpParts, part + 1);
-  const int h_lo = part_lo(p.Hd / 16, kMlpParts, part), h_hi = part_lo(p.Hd / 16, kMlpParts, part + 1);
+  const int h_lo = part_lo_tail(p.Hd / 16, kMlpParts, part), h_hi = part_lo_tail(p.Hd / 16, kMlpParts, part + 1);
   if (c.cluster >= p.n_pairs) return;
   TileDesc td = pair_tile(p, c, c.cluster);
   if (!warp_wait_cl(pbar(p, c, B.t_full), 0, c.abort, p.err)) return;
@@ -1205,48 +1211,47 @@ __device__ void pair_epilogue_mlp(const TcParams& p, uint8_t* gbase, const PairC
     const bool valid = row < td.n_frames;
     float* orow = p.out + (size_t)(td.out_row + row) * p.n_out;
     // 1. x-hat in BF16 into TMEM (chunk cc over the first half of the
-    // output's chunk cc, which this warp has read back); the accumulator
-    // released
+    // output's chunk cc, which this warp has read back) and x + b2 of the
+    // chunk's upper 8 bands into its second half (GEMM1 reads only the
+    // first); the accumulator released
     if (live) {
 #pragma unroll
       for (int g = 0; g < NV; ++g) {
         const int cc = c_lo + g;
         if (cc < c_hi) {
-          uint32_t w[8];
+          uint32_t w[8], r1[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int m = 16 * cc + 2 * e;
             w[e] = pack_bf16((v[16 * g + 2 * e] - mu[m]) * isd[m], (v[16 * g + 2 * e + 1] - mu[m + 1]) * isd[m + 1]);
+            r1[e] = __float_as_uint(v[16 * g + 8 + e] + b2[16 * cc + 8 + e]);
           }
           tmem_st8(tl + p.a1_col + 16 * cc, w);
+          tmem_st8(tl + p.y_col + 16 * cc + 8, r1);
         }
       }
       tmem_st_wait();
     }
     tc_fence_before();
     warp_arrive_leader(pbar(p, c, B.t_empty));
-    // 2. once H is in (x-hat consumed): x + b2 into the output columns, then
-    // GELU(H + b1) in BF16 over H (see gelu_col), the next chunk's load in
-    // flight while one chunk is evaluated
+    // 2. once H is in (x-hat consumed): x + b2 of the lower 8 bands into the
+    // output columns (over x-hat), then GELU(H + b1) in BF16 over H (see
+    // gelu_col), the next chunk's load in flight while one chunk is evaluated
     if (!warp_wait_cl(pbar(p, c, B.h_full), k & 1, c.abort, p.err)) break;
     tc_fence_after();
     if (live) {
+      float ha[16], hb[16];
+      tmem_ld16(tl + p.h_col + 16 * h_lo, ha);  // (every part has hidden chunks)
 #pragma unroll
       for (int g = 0; g < NV; ++g) {
         const int cc = c_lo + g;
         if (cc < c_hi) {
-          uint32_t r0[8], r1[8];
+          uint32_t r0[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            r0[e] = __float_as_uint(v[16 * g + e] + b2[16 * cc + e]);
-            r1[e] = __float_as_uint(v[16 * g + 8 + e] + b2[16 * cc + 8 + e]);
-          }
+          for (int e = 0; e < 8; ++e) r0[e] = __float_as_uint(v[16 * g + e] + b2[16 * cc + e]);
           tmem_st8(tl + p.y_col + 16 * cc, r0);
-          tmem_st8(tl + p.y_col + 16 * cc + 8, r1);
         }
       }
-      float ha[16], hb[16];
-      tmem_ld16(tl + p.h_col + 16 * h_lo, ha);  // (every part has hidden chunks: Hd >= 160)
       tmem_ld_wait();
       reg_fence16(ha);
 #pragma unroll 1
