@@ -268,13 +268,12 @@ def test_learned_correction_synthetic_config(melt):
     melt.melt_mlp_destroy(mlp)
 
 
-def _fused_case(melt, seed, lens, Hd=256):
+def _fused_case(melt, seed, lens, Hd=256, M=80):
     import torch
     clips = [G.rich_clip(seed, i, L) for i, L in enumerate(lens)]
     pk = G.pack_clips(clips)
     wave = torch.from_numpy(pk.wave).cuda()
-    M = 80
-    fe = melt.Frontend(precision="bf16")
+    fe = melt.Frontend(precision="bf16", n_mels=M)
     x = fe(wave, pk.offsets, pk.lengths)
     fe.sync()
     x = x.cpu().numpy().astype(np.float64)
@@ -396,3 +395,25 @@ def test_fused_correction_follows_training_and_hidden_sizes(melt):
         assert np.all(err <= bound), (Hd, float(err.max()))
         fe.close()
         melt.melt_mlp_destroy(mlp)
+
+
+@pytest.mark.parametrize("M,Hd", [(16, 64), (40, 192), (64, 128)])
+def test_fused_correction_other_band_and_hidden_counts(melt, M, Hd):
+    """Band and hidden-unit counts whose runs over the three epilogue warps of a lane
+    quarter are uneven or empty: M = 16 (one band chunk: two warps have no bands), 40
+    (three chunks) and 64 (four), with 4, 12 and 8 hidden chunks; the fused epilogue
+    against the FP64 oracle with the same BF16 operand rounding, element by element."""
+    fe, mlp, pk, wave, x, params, mu, sd = _fused_case(melt, 95, [16000 * 2 + 321, 16000 * 3, 400], Hd=Hd, M=M)
+    melt.melt_basis_set_correction(fe.handle, mlp)
+    assert melt.melt_plan_get(fe.handle)["cta_pair"] == 1
+    got = fe(wave, pk.offsets, pk.lengths)
+    fe.sync()
+    got = got.cpu().numpy()
+    assert got.shape == x.shape
+    y_ref, bound = _fused_bound(params, x, mu, sd)
+    err = np.abs(got - y_ref)
+    assert np.all(err <= bound), (M, Hd, float(err.max()), int((err > bound).sum()))
+    assert float(np.abs(y_ref - x).mean()) > 50 * float(np.sqrt(np.mean(err ** 2)))
+    melt.melt_basis_set_correction(fe.handle, None)
+    fe.close()
+    melt.melt_mlp_destroy(mlp)
