@@ -30,7 +30,7 @@ def _gelu_constants():
     body = m.group(1)
     first = re.search(r"float r = " + _NUM + ";", body)
     rest = re.findall(r"r = fmaf\(r, u, " + _NUM + r"\);", body)
-    expo = re.search(r"t \* " + _NUM + ", t, r\)", body)
+    expo = re.search(r"t \* " + _NUM + r", t, r\)", body)
     clamp = re.search(r"fmaf\(" + _NUM + r", fminf\(t, " + r"(\d+(?:\.\d*)?)f\), " + _NUM + r"\)", body)
     assert first and rest and expo and clamp, "unexpected gelu_poly form"
     coeffs = [float(first.group(1))] + [float(x) for x in rest]
