@@ -375,19 +375,20 @@ static __device__ void pair_basis_producer(const TcParams& p, const PairCtx& c, 
   if (c.rank == 1) mbar_arrive_cluster(mapa_shared(pbar(p, c, B.peer_b), 0));
 }
 
-// TMEM column of the packed GELU(H) of hidden chunk cc (16 units) in the
-// fused MLP.  GELU(H) is written over H itself: the kMlpParts epilogue warps
-// of a lane quarter take runs [lo_j, lo_{j+1}) of the hidden chunks
-// (part_lo_tail), in order, and each stores chunk cc only into H columns it
-// has already read: 8 cc + 8 lo_j, inside its own run's columns
-// [16 lo_j, 16 cc + 16).
-static __device__ __forceinline__ uint32_t gelu_col(const TcParams& p, int cc) {
-  const int nh = p.Hd / 16;
+// Column of the packed GELU(H) of hidden chunk cc (16 units) in the fused
+// MLP, relative to H's first column (nh = Hd/16 chunks).  GELU(H) is written
+// over H itself: the kMlpParts epilogue warps of a lane quarter take runs
+// [lo_j, lo_{j+1}) of the hidden chunks (part_lo_tail), in order, and each
+// stores chunk cc only into H columns it has already read: 8 cc + 8 lo_j,
+// inside its own run's columns [16 lo_j, 16 cc + 16).
+__host__ __device__ constexpr uint32_t mlp_gelu_off(int nh, int cc) {
   int lo = 0;
-#pragma unroll
   for (int j = 1; j < kMlpParts; ++j)
     if (cc >= part_lo_tail(nh, kMlpParts, j)) lo = part_lo_tail(nh, kMlpParts, j);
-  return p.h_col + 8u * (uint32_t)(cc + lo);
+  return 8u * (uint32_t)(cc + lo);
+}
+static __device__ __forceinline__ uint32_t gelu_col(const TcParams& p, int cc) {
+  return p.h_col + mlp_gelu_off(p.Hd / 16, cc);
 }
 
 // Fused MLP (even CTA's MMA thread), hidden layer: H = x-hat W1^T, K-step s
